@@ -1,0 +1,14 @@
+"""Seeded synthetic inputs for the adaptive box-spline filter.
+
+This module holds none of the filter's arithmetic: it only draws images and
+raw per-pixel scale fields (paper scales a_k, or ellipse parameters).  Both the
+oracle and the CUDA path consume its output; each applies the scale readings
+itself.
+"""
+from .workloads import (smooth_field, edge_field, image_c1, image_c2, image_c3,
+                        image_f32_grid, scales_a4, ellipse_field, workload,
+                        batch_workload, SEED_BASE)
+
+__all__ = ["smooth_field", "edge_field", "image_c1", "image_c2", "image_c3",
+           "image_f32_grid", "scales_a4", "ellipse_field", "workload",
+           "batch_workload", "SEED_BASE"]
