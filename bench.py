@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Throughput of the adaptive box-spline filter on GB300.
+
+One step = one pass of the whole path over one image: the non-adaptive step
+(abf_integrate: row scan + look-back line scans) and the adaptive step
+(abf_filter: per-pixel mesh), exact form, inputs resident in HBM.
+
+Workload (default): 2048x2048 float32 image on the 2^-16 grid (smooth field +
+edges), order n = 2, per-pixel ellipse fields (sigma in [1, 24], elongation in
+[1, 6], orientation uniform) mapped to the four steps by the moment rule,
+Q = 8.  Synthetic, seeded.
+
+Multi-GPU: images are independent, so N ranks run N replicas (each its own
+image, no collective on the data path); value = pixels of all ranks / max time.
+
+--impl reference: the exact CPU oracle as it stands, timed on this host on a
+bounded sample of the same workload (per-pixel evaluation).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s adaptive filter, chosen vs FP64 form at stated error; p50/p99 latency"
+UNIT = "Mpixel/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(name, rank):
+    import synthetic
+    return synthetic.workload(name, seed_offset=rank)
+
+
+def _algorithmic_macs(n):
+    """Non-zero ZP^{*n} stencil MACs per pixel: (n+1)^4 taps x 7 n^2 (the area
+    of the support octagon of ZP^{*n}, i.e. its average count of non-zero
+    lattice weights)."""
+    return (n + 1) ** 4 * 7 * n * n
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_0908_3861_gb300 import _abf, AdaptiveFilter
+    import __graft_entry__
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    w = _workload(args.workload, rank)
+    img, sc = w["image"], w["scales"]
+    H, W = img.shape
+    n = w["n"]
+    f_t = torch.from_numpy(img).to(dev)
+    s_t = torch.from_numpy(sc.astype(np.float32)).to(dev)
+    d = _abf.abf_desc()
+    d.width, d.height, d.order_n = W, H, n
+    d.scale_kind = _abf.SCALE_KINDS[w["scale_kind"]]
+    d.q_bits, d.max_scale = w["q_bits"], w["cmax"]
+    _, max_prod = _abf.abf_measure_scales(d, s_t, W * 16)
+    tin = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64,
+           np.dtype(np.uint8): torch.uint8}[img.dtype]
+    filt = AdaptiveFilter(W, H, n, tin, scale_kind=w["scale_kind"], q_bits=w["q_bits"], frac_bits=w["frac_bits"],
+                          max_scale=w["cmax"], out="f32", value_bound=w["value_bound"],
+                          max_scale_product=max_prod, device=dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        filt.integrate(f_t)
+        filt.filter(s_t, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert filt.device_status() == 0
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            filt.integrate(f_t)
+            ev[i][1].record(stream)
+            filt.filter(s_t, out)
+            ev[i][2].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    integ_ms = sum(a.elapsed_time(b) for a, b, c in ev) / K
+    mesh_ms = sum(b.elapsed_time(c) for a, b, c in ev) / K
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    assert filt.device_status() == 0
+
+    # End to end through the public API with host buffers (pinned), H2D + D2H inside.
+    f_h = torch.from_numpy(img).pin_memory()
+    s_h = torch.from_numpy(sc.astype(np.float32)).pin_memory()
+    o_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    f_d = torch.empty_like(f_t)
+    s_d = torch.empty_like(s_t)
+    for _ in range(max(1, args.warmup // 2)):
+        f_d.copy_(f_h, non_blocking=True)
+        s_d.copy_(s_h, non_blocking=True)
+        filt.integrate(f_d)
+        filt.filter(s_d, out)
+        o_h.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        f_d.copy_(f_h, non_blocking=True)
+        s_d.copy_(s_h, non_blocking=True)
+        filt.integrate(f_d)
+        filt.filter(s_d, out)
+        o_h.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    pix = float(H * W)
+    value = pix * K * world / (total_ms * 1e-3) / 1e6
+    e2e_value = pix * K * world / (e2e_ms * 1e-3) / 1e6
+    peaks = _peaks()
+    L = filt.limbs
+    macs = _algorithmic_macs(n) * pix
+    # peak: 152 SMs x 64 INT32 multiply lanes / clock x clock, divided by the
+    # 32-bit multiplies one L-limb x 64-bit MAC needs.
+    imad_per_mac = {1: 3, 2: 7, 3: 11, 4: 15}[L] * (2 if n == 3 else 1)
+    clk = clk.summary()
+    sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    peak_macs = 152 * 64 * sm_mhz * 1e6 / imad_per_mac
+    achieved = macs / (mesh_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64x%d" % L, "data": "synthetic",
+        "config": {"workload": "2048x2048 f32 (2^-16 grid), order n=2, per-pixel ellipse (sigma 1-24, "
+                               "elongation 1-6), Q=8, exact form (%d-limb wrap-around integers)" % L,
+                   "image": [H, W], "order_n": n, "form": "exact", "limbs": L,
+                   "l2": "inputs larger than L2 (integrated image %.0f MB + scales %.0f MB)" % (
+                       filt.info["integrated_bytes"] / 1e6, H * W * 16 / 1e6),
+                   "parallelism": "replicas x%d" % world},
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(f_h.numel() * f_h.element_size() + s_h.numel() * 4),
+                "d2h_bytes_per_step": int(o_h.numel() * 4)},
+        "gpu_launches": int(K * (1 + 3 * n + 1)),
+        "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_macs / 1e12,
+                     "unit": "T MAC/s (%d-limb integer)" % L, "frac": achieved / peak_macs,
+                     "traffic": None, "kernel": "mesh_exact_kernel",
+                     "peak_note": "derived: 152 SM x 64 INT32 mul lanes x median SM clock / %d 32-bit "
+                                  "multiplies per MAC" % imad_per_mac},
+        "clocks": clk,
+    }
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    filt.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, seconds=15.0, sample=None):
+    """The oracle (exact, per-pixel windows) on a bounded sample of the workload."""
+    from oracle import paper, scales as osc
+    img, sc = w["image"], w["scales"]
+    H, W = img.shape
+    fi = (img.astype(np.float64) * float(1 << w["frac_bits"])).astype(np.int64)
+    rng = np.random.default_rng(7)
+    C = osc.scales_to_C(w["scale_kind"], sc, w["n"], w["q_bits"], w["cmax"])
+    done, t0 = 0, time.perf_counter()
+    pts = []
+    while time.perf_counter() - t0 < seconds and (sample is None or done < sample):
+        p = (int(rng.integers(0, W)), int(rng.integers(0, H)))
+        paper.filter_pixels(fi, C, w["n"], w["q_bits"], w["frac_bits"], [p])
+        pts.append(p)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": done / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d random pixels of the same workload, exact per-pixel evaluation, %.1f s" % (done, el)}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    w = _workload(args.workload, 0)
+    K = args.steps
+    for _ in range(args.warmup):
+        cpu_baseline(w, seconds=0.0, sample=1)
+    t0 = time.perf_counter()
+    res = None
+    per = max(1.0, min(20.0, 150.0 / max(K, 1)))
+    tot_pix = 0
+    for _ in range(K):
+        r = cpu_baseline(w, seconds=per)
+        tot_pix += int(r["sample"].split()[0])
+        res = r
+    el = time.perf_counter() - t0
+    value = tot_pix / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "exact (python int)", "data": "synthetic",
+            "config": {"workload": "2048x2048 f32 (2^-16 grid), order n=2, per-pixel ellipse, Q=8"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d random pixels per step, exact per-pixel evaluation" % (tot_pix // K)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * abf.h -- adaptive box-spline filtering on one GPU (GB300, sm_103a).
+ *
+ * The operation (Chaudhury, Munoz-Barrutia, Unser, "Fast adaptive elliptical
+ * filtering using box splines"):
+ *
+ *   Sec. 6:  s[m] = < f, beta^4_{a(m)}( . - m) >  for every pixel m, where
+ *            beta^4_a is the four-direction box spline of Sec. 4 Eq. (def)
+ *            (N = 4, theta_k = (k-1) pi/4) and f is the image with phi = delta
+ *            (Sec. 7 (1)).
+ *   Sec. 7:  computed as a global pre-integration (four running-sum recursions,
+ *            Eq. (RS)) followed, per pixel, by the affine finite-difference mesh
+ *            of Eq. (final_eqn) / Table "Mesh Vertices" with ZP interpolation.
+ *
+ * Order n (1..3) applies every directional box n times (the n-fold running sum
+ * Delta_b^{-n} of Sec. 2 and the FD filter d^n_a of Eq. (FD)); the mesh then has
+ * (n+1)^4 vertices and the interpolation kernel is ZP^{*n}.  n = 1 is Sec. 7.
+ *
+ * Units.  Scales enter as lattice steps c_k: the k-th box is the segment c_k v_k
+ * with v = (1,0), (1,1), (0,1), (-1,1); c1 = a1, c3 = a3, c2 = a2/sqrt2,
+ * c4 = a4/sqrt2 in the paper's scales (its a'_j).  Steps are rounded to the
+ * 2^-Q grid: C_k = rint(c_k 2^Q), ties to even.
+ *
+ * Boundary.  The image is zero outside [0, W) x [0, H) (zero padding).
+ *
+ * Conventions for every entry point below:
+ *   - pointers named d_* are DEVICE pointers allocated and owned by the caller;
+ *     the library never frees them.  Images are row-major, row pitch in BYTES.
+ *   - calls are asynchronous on the given cudaStream_t (0 = legacy default);
+ *     the returned status covers argument checks and launch errors.  Errors
+ *     found on the device (invalid scales, range overflow, a bounded wait
+ *     that ran out) set a status word that abf_last_device_status() reads.
+ *   - no exceptions cross the ABI; no call aborts the process.
+ *   - there is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns ABF_ERR_CUDA.
+ */
+#ifndef ABF_H
+#define ABF_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ABF_OK = 0,
+  ABF_ERR_INVALID = 1,      /* bad argument or descriptor                         */
+  ABF_ERR_OOM = 2,          /* device or host allocation failed                   */
+  ABF_ERR_CUDA = 3,         /* CUDA runtime error (no device, launch failure)     */
+  ABF_ERR_UNSUPPORTED = 4,  /* valid request this build does not serve            */
+  ABF_ERR_RANGE = 5,        /* exact form: numerator would exceed 64*limbs bits   */
+  ABF_ERR_TIMEOUT = 6,      /* a bounded device or host wait ran out              */
+  ABF_ERR_BUSY = 7          /* serving: admission refused (over the HBM budget)   */
+} abf_status;
+
+typedef enum { ABF_U8 = 0, ABF_U16 = 1, ABF_F32 = 2, ABF_F64 = 3 } abf_dtype;
+
+typedef enum {
+  /* Exact: running sums in wrap-around integers modulo 2^(64 L) (L limbs),
+   * integer ZP^{*n} weights, integer numerator S; one binary64 division at the
+   * end.  Bit-exact numerator.  Input must be integer after scaling by 2^F.  */
+  ABF_FORM_EXACT = 0,
+  /* Plain: binary64 running sums restarted on a window around each output tile
+   * (the window holds every read of the tile's mesh), binary64 weights.      */
+  ABF_FORM_PLAIN_F64 = 1,
+  /* Fast: as PLAIN_F64 but binary32 arithmetic, window-local re-centring.    */
+  ABF_FORM_TILE_F32 = 2
+} abf_form;
+
+typedef enum {
+  ABF_SCALES_C4 = 0,      /* float32 x4 per pixel: lattice steps c1..c4              */
+  ABF_SCALES_A4 = 1,      /* float32 x4 per pixel: paper scales a1..a4 (Sec. 7)      */
+  ABF_SCALES_ELLIPSE = 2  /* float32 x4 per pixel: sigma, elongation, cos t, sin t   */
+} abf_scale_kind;
+
+/* Descriptor of one filtering problem (image size, order, types, form). */
+typedef struct {
+  int32_t width, height;      /* image size in pixels (>= 1)                          */
+  int32_t order_n;            /* n in {1, 2, 3}                                       */
+  int32_t in_dtype;           /* abf_dtype of f                                       */
+  int32_t out_dtype;          /* ABF_F32 or ABF_F64                                   */
+  int32_t form;               /* abf_form                                             */
+  int32_t scale_kind;         /* abf_scale_kind                                       */
+  int32_t q_bits;             /* Q: steps on the 2^-Q grid (1..9; 1..8 for n = 3)     */
+  int32_t in_frac_bits;       /* F: f 2^F is an integer (exact form); 0 for u8/u16    */
+  int32_t flags;              /* reserved, 0                                          */
+  double max_scale;           /* upper bound on every step c_k (lattice units)        */
+  double min_scale;           /* lower bound on c1 and c3 (>= 2^-Q); 0 means 1.0      */
+  double value_bound;         /* upper bound on |f|; 0 means the dtype's range        */
+  double max_scale_product;   /* upper bound on c1 c2 c3 c4; 0 means max_scale^4      */
+} abf_desc;
+
+typedef struct abf_plan_s* abf_plan;
+
+/* Create a plan (host work + one upload of the ZP^{*n} weight table, which is
+ * shared by all plans with the same n and grid).  The plan fixes the lattice
+ * box of the integrated image: [-left, W + right) x [0, H + above) in image
+ * coordinates (rows below the image are all zero and are not stored).
+ * Errors: ABF_ERR_INVALID (descriptor), ABF_ERR_RANGE (exact form: the
+ * numerator bound needs more than 4 limbs), ABF_ERR_CUDA / ABF_ERR_OOM.      */
+abf_status abf_plan_create(const abf_desc* desc, abf_plan* out);
+abf_status abf_plan_destroy(abf_plan plan);
+
+/* Sizes the caller allocates: the integrated image (exact form; 0 otherwise)
+ * and the scratch workspace; the margins (left, right, below, above) of the
+ * integrated lattice box; the number of 64-bit limbs L (exact form) and the
+ * row pitch of the integrated image in elements (each element L * 8 bytes).
+ * Any output pointer may be NULL.                                            */
+abf_status abf_plan_query(abf_plan plan, size_t* integrated_bytes, size_t* workspace_bytes,
+                          int32_t* halo_lrbt, int32_t* limbs, int64_t* g_pitch_elems);
+
+/* Non-adaptive step (Sec. 7 (1), Eq. (RS)) of the exact form: the four
+ * running-sum recursions, each n times, in the paper's order (0, pi/4, pi/2,
+ * 3pi/4), unit weights (the paper's sqrt2 factors are folded into the
+ * normaliser), modulo 2^(64 L).
+ *   d_f   : H rows of W elements of desc.in_dtype, row pitch f_pitch bytes.
+ *   d_g   : integrated image, abf_plan_query() bytes, layout
+ *           g[(k2) * pitch + (k1 + left)][limb] (uint64 limbs, little-endian),
+ *           k2 in [0, H + above).  Equal to the exact running sums wherever the
+ *           3pi/4 recursion's backward ray leaves the box through its bottom
+ *           row; elsewhere it differs from them by a polynomial of degree < n
+ *           along each 3pi/4 line, which the mesh annihilates.
+ *   d_ws  : workspace of abf_plan_query() bytes (scan carries and flags).    */
+abf_status abf_integrate(abf_plan plan, const void* d_f, size_t f_pitch, void* d_g,
+                         void* d_ws, cudaStream_t stream);
+
+/* Adaptive step (Eq. (final_eqn)) for every pixel.
+ *   exact form:      d_src = the integrated image from abf_integrate().
+ *   PLAIN_F64 / TILE_F32: d_src = the image f itself (pitch f_pitch bytes);
+ *                    the running sums are restarted per output tile.
+ *   d_scales : H rows of W float4 (desc.scale_kind), row pitch in bytes.
+ *   d_s      : H rows of W desc.out_dtype, row pitch in bytes.
+ * Pixels whose scales are invalid (non-finite, c_k <= 0, c_k > max_scale,
+ * c1 or c3 < min_scale) or whose numerator bound exceeds the limbs get NaN and
+ * set the device status.                                                     */
+abf_status abf_filter(abf_plan plan, const void* d_src, size_t src_pitch, const void* d_scales,
+                      size_t scale_pitch, void* d_s, size_t s_pitch, void* d_ws,
+                      cudaStream_t stream);
+
+/* Exact form only: the integer numerators S[m] = D sum_j w_j g_I(y_j)
+ * (L uint64 limbs per pixel, two's complement modulo 2^(64 L)), row pitch in
+ * bytes.  s[m] = S[m] 2^(4 Q n) / (D (C1 C2 C3 C4)^n 2^F).                    */
+abf_status abf_filter_numerator(abf_plan plan, const void* d_g, const void* d_scales,
+                                size_t scale_pitch, void* d_num, size_t num_pitch, void* d_ws,
+                                cudaStream_t stream);
+
+/* The per-pixel integer steps C_k = rint(c_k 2^Q) (int32 x4 per pixel) that
+ * abf_filter uses, for inspection and reuse.                                 */
+abf_status abf_prepare_scales(abf_plan plan, const void* d_scales, size_t scale_pitch,
+                              void* d_C, size_t C_pitch, cudaStream_t stream);
+
+/* Measure a scale field before planning: the largest step max_k c_k and the
+ * largest product c1 c2 c3 c4 over the image, after rounding to the 2^-Q grid
+ * (desc supplies width, height, order_n, scale_kind, q_bits and max_scale, the
+ * clamp of the ellipse rule).  Synchronises `stream`.  Returns
+ * ABF_ERR_INVALID if some pixel's scales are invalid.  Allocates 24 bytes of
+ * device memory for the duration of the call.                               */
+abf_status abf_measure_scales(const abf_desc* desc, const void* d_scales, size_t scale_pitch,
+                              double* max_step, double* max_product, cudaStream_t stream);
+
+/* The common denominator D of the integer ZP^{*n} weights of this plan, as
+ * four 32-bit words (little-endian, D < 2^128).                              */
+abf_status abf_plan_denominator(abf_plan plan, uint32_t* d_words4);
+
+/* Read and clear the plan's device status word (synchronises the device).
+ * code = 0 or an OR of ABF_DEV_* bits.                                        */
+#define ABF_DEV_BAD_SCALE   1   /* a scale was non-finite, non-positive or out of bounds */
+#define ABF_DEV_RANGE       2   /* a pixel's numerator bound exceeded 64 L - 1 bits       */
+#define ABF_DEV_TIMEOUT     4   /* a bounded wait (scan look-back) ran out                 */
+#define ABF_DEV_BAD_INPUT   8   /* f 2^F not an integer within value_bound (exact form)   */
+abf_status abf_last_device_status(abf_plan plan, int32_t* code);
+
+const char* abf_status_str(abf_status s);
+
+/* Host-only: generate the ZP^{*n} weight table for order n and grid 2^-Q (the
+ * table abf_plan_create uploads) into a caller buffer, without touching a
+ * device.  Layout: (2^P)^2 rows (row index ry 2^P + rx, P = Q for even n,
+ * Q + 1 for odd n), each (3n)^2 weights D ZP^{*n}(r - d) ordered [dy][dx],
+ * d from d_min = -3n/2 + 1 (n even) or -(3n - 1)/2 (n odd); r = rx 2^-P
+ * (minus 1/2 for odd n).  Little-endian words of *wbytes bytes (4, 8 or 16).
+ * With out = NULL only *needed_bytes, *wbytes and D are returned.            */
+abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t out_bytes,
+                                 size_t* needed_bytes, int32_t* wbytes, uint32_t* D_words4);
+
+/* Library version, for the bindings. */
+int32_t abf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABF_H */

@@ -1,0 +1,19 @@
+"""GB300-native adaptive elliptical filtering with box splines.
+
+The filter of Chaudhury, Munoz-Barrutia and Unser (four-direction box splines,
+Sec. 4-7): a global pre-integration by running sums and a per-pixel affine
+finite-difference mesh, as hand-written CUDA kernels for sm_103a behind the C
+ABI of include/abf.h (libabf.so).  ``_abf`` binds that ABI one to one;
+``AdaptiveFilter`` adds buffer allocation with PyTorch.
+"""
+from . import _abf
+from ._abf import AbfError
+
+__all__ = ["_abf", "AbfError", "AdaptiveFilter"]
+
+
+def __getattr__(name):
+    if name == "AdaptiveFilter":
+        from .filter import AdaptiveFilter
+        return AdaptiveFilter
+    raise AttributeError(name)

@@ -1,0 +1,174 @@
+"""ctypes binding of libabf (include/abf.h): the same entry points, argument
+marshalling only.  Every step of the filter runs in the library's CUDA
+kernels; there is no Python or CPU implementation behind these functions.
+
+Loading fails loudly when libabf.so has not been built (``build()`` in
+``paper_0908_3861_gb300.build`` or ``__graft_entry__.build()``).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libabf.so")
+
+ABF_OK = 0
+STATUS_NAMES = {0: "ABF_OK", 1: "ABF_ERR_INVALID", 2: "ABF_ERR_OOM", 3: "ABF_ERR_CUDA",
+                4: "ABF_ERR_UNSUPPORTED", 5: "ABF_ERR_RANGE", 6: "ABF_ERR_TIMEOUT", 7: "ABF_ERR_BUSY"}
+ABF_U8, ABF_U16, ABF_F32, ABF_F64 = 0, 1, 2, 3
+ABF_FORM_EXACT, ABF_FORM_PLAIN_F64, ABF_FORM_TILE_F32 = 0, 1, 2
+ABF_SCALES_C4, ABF_SCALES_A4, ABF_SCALES_ELLIPSE = 0, 1, 2
+ABF_DEV_BAD_SCALE, ABF_DEV_RANGE, ABF_DEV_TIMEOUT, ABF_DEV_BAD_INPUT = 1, 2, 4, 8
+
+SCALE_KINDS = {"c4": ABF_SCALES_C4, "a4": ABF_SCALES_A4, "ellipse": ABF_SCALES_ELLIPSE}
+FORMS = {"exact": ABF_FORM_EXACT, "plain_f64": ABF_FORM_PLAIN_F64, "tile_f32": ABF_FORM_TILE_F32}
+
+
+class AbfError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s" % (where, STATUS_NAMES.get(status, status)))
+
+
+class abf_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("order_n", ctypes.c_int32),
+                ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("scale_kind", ctypes.c_int32), ("q_bits", ctypes.c_int32),
+                ("in_frac_bits", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("max_scale", ctypes.c_double), ("min_scale", ctypes.c_double),
+                ("value_bound", ctypes.c_double), ("max_scale_product", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libabf (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libabf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, sz, i32, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int
+    P = ctypes.POINTER
+    sigs = {
+        "abf_plan_create": ([P(abf_desc), P(vp)], st),
+        "abf_plan_destroy": ([vp], st),
+        "abf_plan_query": ([vp, P(sz), P(sz), P(i32), P(i32), P(ctypes.c_int64)], st),
+        "abf_integrate": ([vp, vp, sz, vp, vp, vp], st),
+        "abf_filter": ([vp, vp, sz, vp, sz, vp, sz, vp, vp], st),
+        "abf_filter_numerator": ([vp, vp, vp, sz, vp, sz, vp, vp], st),
+        "abf_prepare_scales": ([vp, vp, sz, vp, sz, vp], st),
+        "abf_plan_denominator": ([vp, P(ctypes.c_uint32)], st),
+        "abf_last_device_status": ([vp, P(i32)], st),
+        "abf_measure_scales": ([P(abf_desc), vp, sz, P(ctypes.c_double), P(ctypes.c_double), vp], st),
+        "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
+        "abf_status_str": ([st], ctypes.c_char_p),
+        "abf_version": ([], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != ABF_OK:
+        raise AbfError(status, where)
+
+
+def _stream(stream):
+    """cudaStream_t of a torch stream (None: torch's current stream)."""
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+# ----------------------------------------------------------- entry points
+
+def abf_plan_create(desc):
+    h = ctypes.c_void_p()
+    _check(lib().abf_plan_create(ctypes.byref(desc), ctypes.byref(h)), "abf_plan_create")
+    return h
+
+
+def abf_plan_destroy(plan):
+    _check(lib().abf_plan_destroy(plan), "abf_plan_destroy")
+
+
+def abf_plan_query(plan):
+    gb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+    halo = (ctypes.c_int32 * 4)()
+    limbs = ctypes.c_int32()
+    pitch = ctypes.c_int64()
+    _check(lib().abf_plan_query(plan, ctypes.byref(gb), ctypes.byref(wb), halo, ctypes.byref(limbs),
+                                ctypes.byref(pitch)), "abf_plan_query")
+    return dict(integrated_bytes=gb.value, workspace_bytes=wb.value, halo_lrbt=list(halo),
+                limbs=limbs.value, g_pitch=pitch.value)
+
+
+def abf_integrate(plan, f, f_pitch, g, ws, stream=None):
+    _check(lib().abf_integrate(plan, _ptr(f), f_pitch, _ptr(g), _ptr(ws), _stream(stream)), "abf_integrate")
+
+
+def abf_filter(plan, src, src_pitch, scales, scale_pitch, s, s_pitch, ws, stream=None):
+    _check(lib().abf_filter(plan, _ptr(src), src_pitch, _ptr(scales), scale_pitch, _ptr(s), s_pitch, _ptr(ws),
+                            _stream(stream)), "abf_filter")
+
+
+def abf_filter_numerator(plan, g, scales, scale_pitch, num, num_pitch, ws, stream=None):
+    _check(lib().abf_filter_numerator(plan, _ptr(g), _ptr(scales), scale_pitch, _ptr(num), num_pitch, _ptr(ws),
+                                      _stream(stream)), "abf_filter_numerator")
+
+
+def abf_prepare_scales(plan, scales, scale_pitch, C, C_pitch, stream=None):
+    _check(lib().abf_prepare_scales(plan, _ptr(scales), scale_pitch, _ptr(C), C_pitch, _stream(stream)),
+           "abf_prepare_scales")
+
+
+def abf_plan_denominator(plan):
+    w = (ctypes.c_uint32 * 4)()
+    _check(lib().abf_plan_denominator(plan, w), "abf_plan_denominator")
+    return sum(int(w[i]) << (32 * i) for i in range(4))
+
+
+def abf_last_device_status(plan):
+    c = ctypes.c_int32()
+    _check(lib().abf_last_device_status(plan, ctypes.byref(c)), "abf_last_device_status")
+    return c.value
+
+
+def abf_measure_scales(desc, scales, scale_pitch, stream=None):
+    """(max step, max product c1 c2 c3 c4) of a scale field (synchronises)."""
+    a, p = ctypes.c_double(), ctypes.c_double()
+    _check(lib().abf_measure_scales(ctypes.byref(desc), _ptr(scales), scale_pitch, ctypes.byref(a),
+                                    ctypes.byref(p), _stream(stream)), "abf_measure_scales")
+    return a.value, p.value
+
+
+def abf_weight_table_host(n, q_bits):
+    """(bytes, word_bytes, D) of the host-generated ZP^{*n} table."""
+    need, wb = ctypes.c_size_t(), ctypes.c_int32()
+    d = (ctypes.c_uint32 * 4)()
+    _check(lib().abf_weight_table_host(n, q_bits, None, 0, ctypes.byref(need), ctypes.byref(wb), d),
+           "abf_weight_table_host")
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().abf_weight_table_host(n, q_bits, buf, need.value, None, None, None), "abf_weight_table_host")
+    return buf.raw, wb.value, sum(int(d[i]) << (32 * i) for i in range(4))
+
+
+def abf_status_str(s):
+    return lib().abf_status_str(s).decode()
+
+
+def abf_version():
+    return lib().abf_version()

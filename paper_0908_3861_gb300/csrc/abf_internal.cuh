@@ -1,0 +1,216 @@
+// Internal definitions shared by the abf CUDA translation units.
+//
+// Exact arithmetic: integers modulo 2^(64 L) held as L little-endian uint64
+// limbs.  Running sums (Sec. 7 (1)) and the mesh numerator (Eq. (final_eqn))
+// are formed in this ring; only the final numerator, whose true size is bounded
+// (abf_plan_create checks the bound), is read back as a signed integer.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/abf.h"
+
+namespace abf {
+
+constexpr int kMaxLimbs = 4;
+
+// Lattice direction vectors of Sec. 7 (theta = 0, pi/4, pi/2, 3pi/4; b_k r_k = v_k).
+// v1 = (1,0), v2 = (1,1), v3 = (0,1), v4 = (-1,1).
+
+template <int L>
+struct Wide {
+  uint64_t w[L];
+};
+
+template <int L>
+__device__ __forceinline__ void wzero(Wide<L>& a) {
+#pragma unroll
+  for (int i = 0; i < L; ++i) a.w[i] = 0;
+}
+
+// a += b (mod 2^(64L))
+template <int L>
+__device__ __forceinline__ void wadd(Wide<L>& a, const Wide<L>& b) {
+  if constexpr (L == 1) {
+    a.w[0] += b.w[0];
+  } else {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      uint64_t s = a.w[i] + b.w[i];
+      uint64_t c1 = s < b.w[i];
+      uint64_t t = s + carry;
+      uint64_t c2 = t < carry;
+      a.w[i] = t;
+      carry = c1 | c2;
+    }
+  }
+}
+
+// a -= b (mod 2^(64L))
+template <int L>
+__device__ __forceinline__ void wsub(Wide<L>& a, const Wide<L>& b) {
+  if constexpr (L == 1) {
+    a.w[0] -= b.w[0];
+  } else {
+    uint64_t borrow = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      uint64_t d = a.w[i] - b.w[i];
+      uint64_t b1 = a.w[i] < b.w[i];
+      uint64_t t = d - borrow;
+      uint64_t b2 = d < borrow;
+      a.w[i] = t;
+      borrow = b1 | b2;
+    }
+  }
+}
+
+// acc += g * w (mod 2^(64L)), w an unsigned 64-bit factor.
+template <int L>
+__device__ __forceinline__ void wmac(Wide<L>& acc, const Wide<L>& g, uint64_t w) {
+  if constexpr (L == 1) {
+    acc.w[0] += g.w[0] * w;
+  } else {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      uint64_t lo = g.w[i] * w;
+      uint64_t s = acc.w[i] + lo;
+      uint64_t c1 = s < lo;
+      uint64_t t = s + carry;
+      uint64_t c2 = t < carry;
+      acc.w[i] = t;
+      if (i + 1 < L) carry = __umul64hi(g.w[i], w) + c1 + c2;
+    }
+  }
+}
+
+// acc += g * (wlo + 2^64 whi) (mod 2^(64L)): a 128-bit factor.
+template <int L>
+__device__ __forceinline__ void wmac128(Wide<L>& acc, const Wide<L>& g, uint64_t wlo, uint64_t whi) {
+  wmac<L>(acc, g, wlo);
+  if constexpr (L > 1) {
+    if (whi) {
+      Wide<L - 1> a1, g1;
+#pragma unroll
+      for (int i = 0; i < L - 1; ++i) {
+        a1.w[i] = acc.w[i + 1];
+        g1.w[i] = g.w[i];
+      }
+      wmac<L - 1>(a1, g1, whi);
+#pragma unroll
+      for (int i = 0; i < L - 1; ++i) acc.w[i + 1] = a1.w[i];
+    }
+  }
+}
+
+// acc += w * t for a small signed integer w.
+template <int L>
+__device__ __forceinline__ void wmac_signed(Wide<L>& acc, const Wide<L>& t, int w) {
+  if (w >= 0) {
+    wmac<L>(acc, t, (uint64_t)w);
+  } else {
+    Wide<L> p;
+    wzero<L>(p);
+    wmac<L>(p, t, (uint64_t)(-w));
+    wsub<L>(acc, p);
+  }
+}
+
+// Signed value of a two's complement L-limb integer, rounded to binary64
+// (a few roundings; the exact value is available from the numerator API).
+template <int L>
+__device__ __forceinline__ double wto_double(const Wide<L>& a) {
+  Wide<L> m = a;
+  const bool neg = (m.w[L - 1] >> 63) != 0;
+  if (neg) {
+    uint64_t carry = 1;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      uint64_t v = ~m.w[i] + carry;
+      carry = (carry && v == 0) ? 1 : 0;
+      m.w[i] = v;
+    }
+  }
+  double v = 0.0;
+#pragma unroll
+  for (int i = L - 1; i >= 0; --i) v = v * 18446744073709551616.0 + (double)m.w[i];
+  return neg ? -v : v;
+}
+
+template <int L>
+__device__ __forceinline__ Wide<L> wload(const uint64_t* p) {
+  Wide<L> r;
+  if constexpr (L == 2) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+    r.w[0] = v.x;
+    r.w[1] = v.y;
+  } else if constexpr (L == 4) {
+    const ulonglong2 v0 = reinterpret_cast<const ulonglong2*>(p)[0];
+    const ulonglong2 v1 = reinterpret_cast<const ulonglong2*>(p)[1];
+    r.w[0] = v0.x; r.w[1] = v0.y; r.w[2] = v1.x; r.w[3] = v1.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < L; ++i) r.w[i] = p[i];
+  }
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ void wstore(uint64_t* p, const Wide<L>& a) {
+  if constexpr (L == 2) {
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a.w[0], a.w[1]);
+  } else if constexpr (L == 4) {
+    reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(a.w[0], a.w[1]);
+    reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(a.w[2], a.w[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < L; ++i) p[i] = a.w[i];
+  }
+}
+
+// Sign-extend a signed 64-bit integer into L limbs.
+template <int L>
+__device__ __forceinline__ Wide<L> wfrom_i64(int64_t v) {
+  Wide<L> r;
+  r.w[0] = (uint64_t)v;
+  const uint64_t ext = v < 0 ? ~0ull : 0ull;
+#pragma unroll
+  for (int i = 1; i < L; ++i) r.w[i] = ext;
+  return r;
+}
+
+// Acquire / release accesses for the scan look-back flags.
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- host side
+
+// Everything a kernel needs to know about one plan (passed by value).
+struct PlanView {
+  int W, H, n, Q, P, F;
+  int left, right, above;         // lattice box margins (rows start at k2 = 0)
+  int Gw, Gh;                     // lattice box width / height
+  long long Gp;                   // row pitch of g, elements
+  int Cmax, Cmin;                 // integer step bounds (units 2^-Q)
+  int scale_kind, in_dtype, out_dtype;
+  int limbs;
+  double value_bound;             // bound on |f|
+  double log2D;                   // log2 of the weight denominator
+  double Dd;                      // D as binary64
+  int table_bytes_per_w;          // 4, 8 or 16
+  const void* table;              // (2^P)^2 rows of (3n)^2 weights
+};
+
+// Device status word bits are the ABF_DEV_* values of abf.h.
+__device__ __forceinline__ void raise_status(int32_t* st, int32_t bits) {
+  atomicOr(st, bits);
+}
+
+}  // namespace abf

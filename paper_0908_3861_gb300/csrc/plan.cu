@@ -1,0 +1,489 @@
+// Host side of libabf: plans, the exact ZP^{*n} weight tables, and the C ABI.
+//
+// Weight table.  The interpolation kernel of Eq. (final_eqn) is the ZP element
+// of Sec. 7 (the four-direction box spline with unit lattice directions
+// v1..v4), n-fold self-convolved at order n: a box spline M with N = 4n
+// directions.  Its values on the 2^-P grid are computed exactly, in integers, by
+// the refinement equation of box splines,
+//     M(y) = 2^(2-N) sum_k a_k M(2y - k),   sum_k a_k z^k = prod_xi (1 + z^xi),
+// starting from its values at the integer points (the eigenvector of the same
+// equation restricted to the integers, found in floating point, snapped to a
+// rational with a factorial denominator and then verified exactly).  Each
+// halving of the grid multiplies the common denominator by 2^(N-2), so
+// D = D0 2^((4n-2) P) makes every table entry an integer (D0: the least common
+// denominator of the integer-point values).  Every row (the 3n x 3n neighbours
+// of one fractional offset) sums to D exactly (partition of unity); the
+// generator checks that too.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "abf_internal.cuh"
+
+namespace abf {
+cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
+                          uint32_t* epoch, int32_t* status, cudaStream_t st);
+size_t line_ws_bytes(int Gw, int Gh, int L, int* nbands_out, int* nlines_out);
+cudaError_t run_mesh_exact(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
+                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st);
+cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t scale_pitch, void* C, size_t C_pitch,
+                               int32_t* status, cudaStream_t st);
+cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t scale_pitch,
+                               unsigned long long* out2, int32_t* status, cudaStream_t st);
+}  // namespace abf
+
+using u128 = unsigned __int128;
+
+namespace {
+
+// ------------------------------------------------------------- weight tables
+
+struct HostTable {
+  std::vector<uint8_t> bytes;  // (2^P)^2 rows x (3n)^2 weights, little-endian
+  u128 D = 0;
+  int wbytes = 0;
+  std::string err;
+};
+
+u128 gcd128(u128 a, u128 b) {
+  while (b) {
+    u128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool build_table(int n, int P, HostTable& out) {
+  const int N = 4 * n;
+  const int V[4][2] = {{1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+  // Mask prod_k (1 + z^{v_k})^n on x in [-n, 2n], y in [0, 3n].
+  const int mw = 3 * n + 1, mh = 3 * n + 1, mx0 = -n;
+  std::vector<int64_t> a(mw * mh, 0);
+  a[(0 - mx0) + 0 * mw] = 1;
+  for (int k = 0; k < 4; ++k)
+    for (int r = 0; r < n; ++r) {
+      std::vector<int64_t> b = a;
+      for (int y = 0; y < mh; ++y)
+        for (int xi = 0; xi < mw; ++xi) {
+          const int64_t v = a[xi + y * mw];
+          if (!v) continue;
+          const int nx = xi + V[k][0], ny = y + V[k][1];
+          if (nx < 0 || nx >= mw || ny < 0 || ny >= mh) { out.err = "mask out of range"; return false; }
+          b[nx + ny * mw] += v;
+        }
+      a.swap(b);
+    }
+  auto mask_at = [&](int kx, int ky) -> int64_t {
+    const int xi = kx - mx0;
+    if (xi < 0 || xi >= mw || ky < 0 || ky >= mh) return 0;
+    return a[xi + ky * mw];
+  };
+  // Integer-point values: v_p = 2^(2-N) sum_q a_{2p-q} v_q on the support points.
+  const int npts = mw * mh;
+  std::vector<long double> v(npts, 1.0L / npts), nv(npts);
+  for (int it = 0; it < 400; ++it) {
+    long double s = 0;
+    for (int p = 0; p < npts; ++p) {
+      const int px = p % mw + mx0, py = p / mw;
+      long double acc = 0;
+      for (int q = 0; q < npts; ++q) {
+        const int64_t c = mask_at(2 * px - (q % mw + mx0), 2 * py - q / mw);
+        if (c) acc += (long double)c * v[q];
+      }
+      nv[p] = acc;
+      s += acc;
+    }
+    for (int p = 0; p < npts; ++p) v[p] = nv[p] / s;
+  }
+  // Snap to the denominator 2 (N-2)! and verify exactly.
+  u128 Dc = 2;
+  for (int i = 2; i <= N - 2; ++i) Dc *= (u128)i;
+  std::vector<u128> Vq(npts);
+  bool ok = false;
+  for (int attempt = 0; attempt < 8 && !ok; ++attempt, Dc *= 2) {
+    ok = true;
+    u128 sum = 0;
+    for (int p = 0; p < npts; ++p) {
+      const long double x = v[p] * (long double)Dc;
+      const long double r = std::floor(x + 0.5L);
+      if (std::fabs((double)(x - r)) > 1e-3 || r < 0) { ok = false; break; }
+      Vq[p] = (u128)r;
+      sum += Vq[p];
+    }
+    if (!ok || sum != Dc) { ok = false; continue; }
+    const u128 scale = (u128)1 << (N - 2);
+    for (int p = 0; p < npts && ok; ++p) {
+      const int px = p % mw + mx0, py = p / mw;
+      u128 acc = 0;
+      for (int q = 0; q < npts; ++q) {
+        const int64_t c = mask_at(2 * px - (q % mw + mx0), 2 * py - q / mw);
+        if (c) acc += (u128)c * Vq[q];
+      }
+      if (acc != scale * Vq[p]) ok = false;
+    }
+    if (ok) break;
+  }
+  if (!ok) { out.err = "integer-point values of ZP^n failed the exact check"; return false; }
+  u128 g = Dc;
+  for (int p = 0; p < npts; ++p) g = gcd128(g, Vq[p]);
+  const u128 D0 = Dc / g;
+  for (int p = 0; p < npts; ++p) Vq[p] /= g;
+
+  // Refinement cascade to the 2^-P grid: level l has (3n 2^l + 1)^2 points,
+  // index (i, j) <-> (x, y) = (-n + i 2^-l, j 2^-l).
+  std::vector<u128> cur(Vq), nxt;
+  int side = 3 * n + 1;
+  std::vector<std::tuple<int, int, int64_t>> mk;
+  for (int ky = 0; ky < mh; ++ky)
+    for (int kx = mx0; kx < mx0 + mw; ++kx)
+      if (mask_at(kx, ky)) mk.emplace_back(kx, ky, mask_at(kx, ky));
+  for (int l = 1; l <= P; ++l) {
+    const int nside = 3 * n * (1 << l) + 1;
+    nxt.assign((size_t)nside * nside, 0);
+    const int h = 1 << (l - 1);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < nside; ++j) {
+      for (int i = 0; i < nside; ++i) {
+        u128 acc = 0;
+        for (const auto& t : mk) {
+          const int ip = i - (n + std::get<0>(t)) * h;
+          const int jp = j - std::get<1>(t) * h;
+          if (ip < 0 || ip >= side || jp < 0 || jp >= side) continue;
+          acc += (u128)std::get<2>(t) * cur[(size_t)jp * side + ip];
+        }
+        nxt[(size_t)j * nside + i] = acc;
+      }
+    }
+    cur.swap(nxt);
+    side = nside;
+  }
+  const u128 D = D0 << ((N - 2) * P);
+  // Centred table rows.
+  const int n3 = 3 * n;
+  const int dmin = (n % 2 == 0) ? (-(3 * n) / 2 + 1) : (-(3 * n - 1) / 2);
+  const int one = 1 << P;
+  const int half = (n % 2 == 0) ? 0 : one / 2;
+  const int wb = (n == 1) ? 4 : (n == 2 ? 8 : 16);
+  if (n == 1 && D >= ((u128)1 << 32)) { out.err = "D too large for 32-bit weights"; return false; }
+  if (n == 2 && D >= ((u128)1 << 64)) { out.err = "D too large for 64-bit weights"; return false; }
+  const size_t rows = (size_t)one * one;
+  out.bytes.assign(rows * n3 * n3 * wb, 0);
+  bool sums_ok = true;
+#pragma omp parallel for schedule(static) reduction(&& : sums_ok)
+  for (int ry = 0; ry < one; ++ry) {
+    for (int rx = 0; rx < one; ++rx) {
+      u128 rowsum = 0;
+      for (int iy = 0; iy < n3; ++iy)
+        for (int ix = 0; ix < n3; ++ix) {
+          // uncentred point (r - d) + n (1/2, 3/2), in units of 2^-P
+          const long X = (long)rx - half - (long)(dmin + ix) * one + (long)n * one / 2;
+          const long Y = (long)ry - half - (long)(dmin + iy) * one + (long)3 * n * one / 2;
+          const long i = X + (long)n * one, j = Y;
+          u128 w = 0;
+          if (i >= 0 && i < side && j >= 0 && j < side) w = cur[(size_t)j * side + i];
+          rowsum += w;
+          uint8_t* dst = &out.bytes[(((size_t)ry * one + rx) * n3 * n3 + (size_t)iy * n3 + ix) * wb];
+          for (int b = 0; b < wb; ++b) dst[b] = (uint8_t)(w >> (8 * b));
+        }
+      if (rowsum != D) sums_ok = false;
+    }
+  }
+  if (!sums_ok) { out.err = "ZP^n weight rows do not sum to D"; return false; }
+  out.D = D;
+  out.wbytes = wb;
+  return true;
+}
+
+struct DeviceTable {
+  void* ptr = nullptr;
+  u128 D = 0;
+  int wbytes = 0;
+};
+
+std::mutex g_table_mu;
+std::map<std::tuple<int, int, int>, DeviceTable> g_tables;  // (device, n, P); held until exit
+
+abf_status get_table(int device, int n, int P, DeviceTable* out) {
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  auto key = std::make_tuple(device, n, P);
+  auto it = g_tables.find(key);
+  if (it != g_tables.end()) {
+    *out = it->second;
+    return ABF_OK;
+  }
+  HostTable ht;
+  try {
+    if (!build_table(n, P, ht)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  DeviceTable dt;
+  if (cudaMalloc(&dt.ptr, ht.bytes.size()) != cudaSuccess) return ABF_ERR_OOM;
+  if (cudaMemcpy(dt.ptr, ht.bytes.data(), ht.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dt.ptr);
+    return ABF_ERR_CUDA;
+  }
+  dt.D = ht.D;
+  dt.wbytes = ht.wbytes;
+  g_tables[key] = dt;
+  *out = dt;
+  return ABF_OK;
+}
+
+double u128_to_double(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073709551616.0 + (double)(uint64_t)v; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ the plan
+
+struct abf_plan_s {
+  abf_desc desc;
+  abf::PlanView pv;
+  u128 D;
+  int device;
+  int32_t* d_status = nullptr;
+  size_t g_bytes = 0, ws_bytes = 0;
+  uint32_t epoch = 0;
+};
+
+extern "C" {
+
+int32_t abf_version(void) { return 1; }
+
+const char* abf_status_str(abf_status s) {
+  switch (s) {
+    case ABF_OK: return "ok";
+    case ABF_ERR_INVALID: return "invalid argument";
+    case ABF_ERR_OOM: return "out of memory";
+    case ABF_ERR_CUDA: return "CUDA error";
+    case ABF_ERR_UNSUPPORTED: return "unsupported";
+    case ABF_ERR_RANGE: return "numerator exceeds the limb budget";
+    case ABF_ERR_TIMEOUT: return "timeout";
+    case ABF_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
+  if (!d || !out) return ABF_ERR_INVALID;
+  *out = nullptr;
+  const int n = d->order_n;
+  if (d->width < 1 || d->height < 1 || n < 1 || n > 3) return ABF_ERR_INVALID;
+  if (d->in_dtype < ABF_U8 || d->in_dtype > ABF_F64) return ABF_ERR_INVALID;
+  if (d->out_dtype != ABF_F32 && d->out_dtype != ABF_F64) return ABF_ERR_INVALID;
+  if (d->scale_kind < ABF_SCALES_C4 || d->scale_kind > ABF_SCALES_ELLIPSE) return ABF_ERR_INVALID;
+  if (d->q_bits < 1 || d->q_bits > (n == 3 ? 8 : 9)) return ABF_ERR_INVALID;
+  if (d->in_frac_bits < 0 || d->in_frac_bits > 40) return ABF_ERR_INVALID;
+  if (d->in_dtype <= ABF_U16 && d->in_frac_bits != 0) return ABF_ERR_INVALID;
+  if (!(d->max_scale > 0) || !std::isfinite(d->max_scale) || d->max_scale > 4096) return ABF_ERR_INVALID;
+  if (d->form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  const int Q = d->q_bits;
+  const int P = (n % 2 == 0) ? Q : Q + 1;
+  const double qd = std::ldexp(1.0, Q);
+  const int Cmax = (int)std::lrint(d->max_scale * qd);
+  const double min_scale = d->min_scale > 0 ? d->min_scale : 1.0;
+  int Cmin = (int)std::ceil(min_scale * qd - 1e-9);
+  if (Cmin < 1) Cmin = 1;
+  if (Cmax < 1 || Cmin > Cmax) return ABF_ERR_INVALID;
+  double vb = d->value_bound;
+  if (!(vb > 0)) {
+    if (d->in_dtype == ABF_U8) vb = 255.0;
+    else if (d->in_dtype == ABF_U16) vb = 65535.0;
+    else return ABF_ERR_INVALID;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
+
+  abf_plan p = new (std::nothrow) abf_plan_s();
+  if (!p) return ABF_ERR_OOM;
+  p->desc = *d;
+  p->device = dev;
+  DeviceTable tab;
+  abf_status s = get_table(dev, n, P, &tab);
+  if (s != ABF_OK) { delete p; return s; }
+  p->D = tab.D;
+
+  // Numerator bound -> limbs.
+  const double cmax = (double)Cmax / qd;
+  const double prod = d->max_scale_product > 0 ? d->max_scale_product : std::pow(cmax, 4.0);
+  const double cmin = (double)Cmin / qd;
+  const double log2D = std::log2(u128_to_double(tab.D));
+  const double lb = log2D + n * std::log2(prod) + std::log2(vb) + d->in_frac_bits +
+                    2.0 * std::log2(1.0 + 1.0 / cmin) + 1e-6;
+  const int L = (int)std::floor((lb + 1.0) / 64.0) + 1;
+  if (L > abf::kMaxLimbs) { delete p; return ABF_ERR_RANGE; }
+
+  // Lattice box: reads of a pixel span [m1 - E - 2n, m1 + E + n] x [m2 - E - 3n, m2 + E],
+  // E = (n/2)(c_a + c_b + c_c) <= 1.5 n cmax.
+  const double E = 1.5 * n * cmax;
+  abf::PlanView& pv = p->pv;
+  pv.W = d->width; pv.H = d->height; pv.n = n; pv.Q = Q; pv.P = P; pv.F = d->in_frac_bits;
+  pv.left = (int)std::ceil(E + 2 * n);
+  pv.right = (int)std::ceil(E + n);
+  pv.above = (int)std::ceil(E);
+  pv.Gw = pv.W + pv.left + pv.right;
+  pv.Gh = pv.H + pv.above;
+  pv.Gp = ((long long)pv.Gw + 3) / 4 * 4;
+  pv.Cmax = Cmax; pv.Cmin = Cmin;
+  pv.scale_kind = d->scale_kind; pv.in_dtype = d->in_dtype; pv.out_dtype = d->out_dtype;
+  pv.limbs = L;
+  pv.value_bound = vb;
+  pv.log2D = log2D;
+  pv.Dd = u128_to_double(tab.D);
+  pv.table_bytes_per_w = tab.wbytes;
+  pv.table = tab.ptr;
+  p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
+  p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, nullptr, nullptr);
+  if (cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) { delete p; return ABF_ERR_OOM; }
+  if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+    cudaFree(p->d_status);
+    delete p;
+    return ABF_ERR_CUDA;
+  }
+  *out = p;
+  return ABF_OK;
+}
+
+abf_status abf_plan_destroy(abf_plan p) {
+  if (!p) return ABF_ERR_INVALID;
+  if (p->d_status) cudaFree(p->d_status);
+  delete p;
+  return ABF_OK;
+}
+
+abf_status abf_plan_query(abf_plan p, size_t* integrated_bytes, size_t* workspace_bytes, int32_t* halo_lrbt,
+                          int32_t* limbs, int64_t* g_pitch_elems) {
+  if (!p) return ABF_ERR_INVALID;
+  if (integrated_bytes) *integrated_bytes = p->g_bytes;
+  if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+  if (halo_lrbt) {
+    halo_lrbt[0] = p->pv.left;
+    halo_lrbt[1] = p->pv.right;
+    halo_lrbt[2] = 0;
+    halo_lrbt[3] = p->pv.above;
+  }
+  if (limbs) *limbs = p->pv.limbs;
+  if (g_pitch_elems) *g_pitch_elems = p->pv.Gp;
+  return ABF_OK;
+}
+
+abf_status abf_plan_denominator(abf_plan p, uint32_t* w4) {
+  if (!p || !w4) return ABF_ERR_INVALID;
+  for (int i = 0; i < 4; ++i) w4[i] = (uint32_t)(p->D >> (32 * i));
+  return ABF_OK;
+}
+
+static abf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ABF_OK : ABF_ERR_CUDA; }
+
+abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, void* d_ws, cudaStream_t st) {
+  if (!p || !d_f || !d_g || !d_ws) return ABF_ERR_INVALID;
+  const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
+  if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &p->epoch, p->d_status, st));
+}
+
+abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const void* d_scales, size_t scale_pitch,
+                      void* d_s, size_t s_pitch, void* d_ws, cudaStream_t st) {
+  (void)src_pitch;
+  (void)d_ws;
+  if (!p || !d_src || !d_scales || !d_s) return ABF_ERR_INVALID;
+  const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
+  if (scale_pitch < (size_t)p->pv.W * 16 || s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_src, d_scales, scale_pitch, d_s, s_pitch,
+                                         nullptr, 0, p->d_status, st));
+}
+
+abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_num,
+                                size_t num_pitch, void* d_ws, cudaStream_t st) {
+  (void)d_ws;
+  if (!p || !d_g || !d_scales || !d_num) return ABF_ERR_INVALID;
+  if (scale_pitch < (size_t)p->pv.W * 16 || num_pitch < (size_t)p->pv.W * 8 * p->pv.limbs) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, nullptr, 0,
+                                         (uint64_t*)d_num, num_pitch, p->d_status, st));
+}
+
+abf_status abf_prepare_scales(abf_plan p, const void* d_scales, size_t scale_pitch, void* d_C, size_t C_pitch,
+                              cudaStream_t st) {
+  if (!p || !d_scales || !d_C) return ABF_ERR_INVALID;
+  if (scale_pitch < (size_t)p->pv.W * 16 || C_pitch < (size_t)p->pv.W * 16) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_scales & 15) || (scale_pitch & 15) || ((uintptr_t)d_C & 15) || (C_pitch & 15))
+    return ABF_ERR_INVALID;
+  return cuda_status(abf::run_prepare_scales(p->pv, d_scales, scale_pitch, d_C, C_pitch, p->d_status, st));
+}
+
+abf_status abf_measure_scales(const abf_desc* d, const void* d_scales, size_t scale_pitch, double* max_step,
+                              double* max_product, cudaStream_t st) {
+  if (!d || !d_scales || !max_step || !max_product) return ABF_ERR_INVALID;
+  if (d->width < 1 || d->height < 1 || d->order_n < 1 || d->order_n > 3) return ABF_ERR_INVALID;
+  if (d->scale_kind < ABF_SCALES_C4 || d->scale_kind > ABF_SCALES_ELLIPSE) return ABF_ERR_INVALID;
+  if (d->q_bits < 1 || d->q_bits > 9 || !(d->max_scale > 0)) return ABF_ERR_INVALID;
+  if (scale_pitch < (size_t)d->width * 16 || (scale_pitch & 15) || ((uintptr_t)d_scales & 15)) return ABF_ERR_INVALID;
+  abf::PlanView pv{};
+  pv.W = d->width; pv.H = d->height; pv.n = d->order_n; pv.Q = d->q_bits;
+  pv.scale_kind = d->scale_kind;
+  pv.Cmax = (int)std::lrint(d->max_scale * std::ldexp(1.0, d->q_bits));
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * sizeof(unsigned long long) + sizeof(int32_t)) != cudaSuccess) return ABF_ERR_OOM;
+  int32_t* stw = (int32_t*)((char*)buf + 2 * sizeof(unsigned long long));
+  abf_status rs = ABF_OK;
+  unsigned long long h[2] = {0, 0};
+  int32_t hs = 0;
+  if (cudaMemsetAsync(stw, 0, sizeof(int32_t), st) != cudaSuccess ||
+      abf::run_measure_scales(pv, d_scales, scale_pitch, (unsigned long long*)buf, stw, st) != cudaSuccess ||
+      cudaMemcpyAsync(h, buf, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&hs, stw, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    rs = ABF_ERR_CUDA;
+  cudaFree(buf);
+  if (rs != ABF_OK) return rs;
+  double a, b;
+  std::memcpy(&a, &h[0], 8);
+  std::memcpy(&b, &h[1], 8);
+  *max_step = a;
+  *max_product = b;
+  return hs ? ABF_ERR_INVALID : ABF_OK;
+}
+
+abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t out_bytes, size_t* needed_bytes,
+                                 int32_t* wbytes, uint32_t* D_words4) {
+  if (n < 1 || n > 3 || q_bits < 1 || q_bits > (n == 3 ? 8 : 9)) return ABF_ERR_INVALID;
+  const int P = (n % 2 == 0) ? q_bits : q_bits + 1;
+  HostTable ht;
+  try {
+    if (!build_table(n, P, ht)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  if (needed_bytes) *needed_bytes = ht.bytes.size();
+  if (wbytes) *wbytes = ht.wbytes;
+  if (D_words4)
+    for (int i = 0; i < 4; ++i) D_words4[i] = (uint32_t)(ht.D >> (32 * i));
+  if (out) {
+    if (out_bytes < ht.bytes.size()) return ABF_ERR_INVALID;
+    std::memcpy(out, ht.bytes.data(), ht.bytes.size());
+  }
+  return ABF_OK;
+}
+
+abf_status abf_last_device_status(abf_plan p, int32_t* code) {
+  if (!p || !code) return ABF_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return ABF_ERR_CUDA;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, p->d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return ABF_ERR_CUDA;
+  if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) return ABF_ERR_CUDA;
+  *code = v;
+  return ABF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Non-adaptive step of Sec. 7 (1), Eq. (RS): the four running-sum recursions
+//   F0[k1,k2] = f[k1,k2]  + F0[k1-1,k2]        direction v1 = (1,0)
+//   Fq[k1,k2] = F0[k1,k2] + Fq[k1-1,k2-1]      direction v2 = (1,1)
+//   Fh[k1,k2] = Fq[k1,k2] + Fh[k1,k2-1]        direction v3 = (0,1)
+//   g [k1,k2] = Fh[k1,k2] + g [k1+1,k2-1]      direction v4 = (-1,1)
+// with unit weights (the paper's sqrt2 factors sit in the normaliser), each
+// applied n times, in wrap-around integers modulo 2^(64 L).
+//
+// Lattice box: columns [-left, W + right), rows [0, H + above).  Rows below the
+// image are identically zero and not stored.  v1, v2, v3 are exact on the box
+// (their backward rays leave it where the input is zero).  v4 runs last; a
+// backward 3pi/4 ray that leaves through the right edge misses values, and the
+// miss is a polynomial of degree < n along that 3pi/4 line (the exit point moves
+// linearly along the line), which the FD of the mesh along v4 annihilates.
+//
+// Kernels:
+//   row_scan   : one warp per row, input conversion (a0) fused, all n folds of
+//                v1 in one pass (lane-local scans + warp shuffles, a running
+//                carry per fold).
+//   line_scan  : v2 / v3 / v4, one thread per line (sheared so that a warp reads
+//                consecutive addresses), lines cut into bands of R rows; bands
+//                are chained by decoupled look-back on per-line flags, with a
+//                bounded wait that raises ABF_DEV_TIMEOUT instead of hanging.
+#include "abf_internal.cuh"
+
+namespace abf {
+
+// ------------------------------------------------------------------ rows (v1)
+
+template <typename T>
+__device__ __forceinline__ double as_double(T v) { return (double)v; }
+
+template <int L>
+__device__ __forceinline__ Wide<L> shfl_up_wide(const Wide<L>& v, int d) {
+  Wide<L> r;
+#pragma unroll
+  for (int i = 0; i < L; ++i) r.w[i] = __shfl_up_sync(0xffffffffu, v.w[i], d);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ Wide<L> shfl_wide(const Wide<L>& v, int src) {
+  Wide<L> r;
+#pragma unroll
+  for (int i = 0; i < L; ++i) r.w[i] = __shfl_sync(0xffffffffu, v.w[i], src);
+  return r;
+}
+
+// Inclusive scan of one value per lane across the warp.
+template <int L>
+__device__ __forceinline__ Wide<L> warp_inclusive(Wide<L> v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    Wide<L> o = shfl_up_wide<L>(v, d);
+    if (lane >= d) wadd<L>(v, o);
+  }
+  return v;
+}
+
+template <typename TIn>
+__device__ __forceinline__ int64_t load_f(const TIn* row, int x, double scale, double bound,
+                                          int32_t* status) {
+  const TIn raw = row[x];
+  if constexpr (sizeof(TIn) <= 2) {
+    return (int64_t)raw;
+  } else {
+    const double v = (double)raw * scale;  // exact: scale is a power of two
+    const double r = rint(v);
+    if (!(r == v) || !(fabs(r) <= bound)) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    return (int64_t)r;
+  }
+}
+
+constexpr int kRowVec = 4;  // elements per lane per chunk
+
+template <int L, typename TIn>
+__global__ void __launch_bounds__(256) row_scan_kernel(const PlanView pv, const TIn* __restrict__ f,
+                                                       size_t f_pitch, uint64_t* __restrict__ g,
+                                                       int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int y = warp;
+  if (y >= pv.Gh) return;
+  const double scale = ldexp(1.0, pv.F);
+  const double bound = pv.value_bound * scale;
+  const TIn* frow = (y < pv.H) ? reinterpret_cast<const TIn*>(reinterpret_cast<const char*>(f) + (size_t)y * f_pitch)
+                               : nullptr;
+  uint64_t* grow = g + (size_t)y * (size_t)pv.Gp * L;
+  Wide<L> carry[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) wzero<L>(carry[k]);
+  const int chunk = 32 * kRowVec;
+  for (int x0 = 0; x0 < pv.Gw; x0 += chunk) {
+    Wide<L> v[kRowVec];
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) {
+      const int xi = x0 + lane * kRowVec + e;   // box column
+      const int x = xi - pv.left;               // image column
+      int64_t val = 0;
+      if (frow && x >= 0 && x < pv.W && xi < pv.Gw) val = load_f<TIn>(frow, x, scale, bound, status);
+      v[e] = wfrom_i64<L>(val);
+    }
+    for (int k = 0; k < pv.n; ++k) {
+      // lane-local inclusive scan
+#pragma unroll
+      for (int e = 1; e < kRowVec; ++e) wadd<L>(v[e], v[e - 1]);
+      Wide<L> tot = v[kRowVec - 1];
+      Wide<L> incl = warp_inclusive<L>(tot, lane);
+      Wide<L> excl = shfl_up_wide<L>(incl, 1);
+      if (lane == 0) wzero<L>(excl);
+      wadd<L>(excl, carry[k]);
+#pragma unroll
+      for (int e = 0; e < kRowVec; ++e) wadd<L>(v[e], excl);
+      Wide<L> last = shfl_wide<L>(incl, 31);
+      wadd<L>(carry[k], last);
+    }
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) {
+      const int xi = x0 + lane * kRowVec + e;
+      if (xi < pv.Gw) wstore<L>(grow + (size_t)xi * L, v[e]);
+    }
+  }
+}
+
+// ---------------------------------------------------------- lines (v2, v3, v4)
+
+constexpr int kBand = 16;         // rows per band
+constexpr int kLinesPerCta = 128; // lines per CTA (one per thread)
+constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;
+constexpr long long kSpinLimit = 1ll << 22;
+
+struct LineWs {
+  uint32_t* flags;    // [nbands][nlines]
+  uint64_t* agg;      // [nbands][nlines][L]
+  uint64_t* pref;     // [nbands][nlines][L]
+  uint32_t* ticket;   // one counter, zeroed before each launch
+  int nbands, nlines, ngroups;
+};
+
+// DIR: 2 -> v2 = (1,1) (box column xi = l - (Gh-1) + y), 3 -> v3 (xi = l),
+//      4 -> v4 = (-1,1) (xi = l - y).
+template <int DIR>
+__device__ __forceinline__ int line_col(int l, int y, int Gh) {
+  if constexpr (DIR == 2) return l - (Gh - 1) + y;
+  else if constexpr (DIR == 3) return l;
+  else return l - y;
+}
+
+template <int L, int DIR>
+__global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
+                                                                 LineWs ws, uint32_t epoch,
+                                                                 int32_t* status) {
+  __shared__ uint32_t s_ticket;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(ws.ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_ticket;
+  const int band = (int)(t / (uint32_t)ws.ngroups);
+  const int grp = (int)(t % (uint32_t)ws.ngroups);
+  if (band >= ws.nbands) return;
+  const int l = grp * kLinesPerCta + threadIdx.x;
+  const bool line_ok = l < ws.nlines;
+  const int y0 = band * kBand;
+
+  Wide<L> v[kBand];
+  Wide<L> run;
+  wzero<L>(run);
+#pragma unroll
+  for (int i = 0; i < kBand; ++i) {
+    const int y = y0 + i;
+    const int xi = line_col<DIR>(l, y, pv.Gh);
+    Wide<L> val;
+    wzero<L>(val);
+    if (line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw)
+      val = wload<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L);
+    wadd<L>(run, val);
+    v[i] = run;
+  }
+
+  // Decoupled look-back over the bands below (same line).
+  Wide<L> carry;
+  wzero<L>(carry);
+  const size_t slot = (size_t)band * ws.nlines + (line_ok ? l : 0);
+  if (line_ok) {
+    if (band > 0) {
+      wstore<L>(ws.agg + slot * L, run);
+      __threadfence();
+      st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);
+      int bb = band - 1;
+      long long spins = 0;
+      while (bb >= 0) {
+        const size_t s2 = (size_t)bb * ws.nlines + l;
+        const uint32_t fl = ld_acquire(ws.flags + s2);
+        if ((fl >> 2) != epoch || (fl & 3u) == 0u) {
+          if (++spins > kSpinLimit) {
+            raise_status(status, ABF_DEV_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        if ((fl & 3u) == kFlagPrefix) {
+          Wide<L> p = wload<L>(ws.pref + s2 * L);
+          wadd<L>(carry, p);
+          break;
+        }
+        Wide<L> a = wload<L>(ws.agg + s2 * L);
+        wadd<L>(carry, a);
+        --bb;
+      }
+    }
+    Wide<L> incl = run;
+    wadd<L>(incl, carry);
+    wstore<L>(ws.pref + slot * L, incl);
+    __threadfence();
+    st_release(ws.flags + slot, (epoch << 2) | kFlagPrefix);
+  }
+
+#pragma unroll
+  for (int i = 0; i < kBand; ++i) {
+    const int y = y0 + i;
+    const int xi = line_col<DIR>(l, y, pv.Gh);
+    if (line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw) {
+      Wide<L> o = v[i];
+      wadd<L>(o, carry);
+      wstore<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L, o);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- launchers
+
+template <int L, typename TIn>
+static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g,
+                               int32_t* status, cudaStream_t st) {
+  const int warps_per_block = 8;
+  const int blocks = (pv.Gh + warps_per_block - 1) / warps_per_block;
+  row_scan_kernel<L, TIn><<<blocks, 32 * warps_per_block, 0, st>>>(pv, (const TIn*)f, f_pitch, g, status);
+  return cudaGetLastError();
+}
+
+template <int L, int DIR>
+static cudaError_t launch_lines(const PlanView& pv, uint64_t* g, const LineWs& ws, uint32_t epoch,
+                                int32_t* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const int ctas = ws.nbands * ws.ngroups;
+  line_scan_kernel<L, DIR><<<ctas, kLinesPerCta, 0, st>>>(pv, g, ws, epoch, status);
+  return cudaGetLastError();
+}
+
+// Workspace needed by the line scans for a plan (bytes) and its layout.
+size_t line_ws_bytes(int Gw, int Gh, int L, int* nbands_out, int* nlines_out) {
+  const int nbands = (Gh + kBand - 1) / kBand;
+  const int nlines = Gw + Gh;  // enough for every direction
+  if (nbands_out) *nbands_out = nbands;
+  if (nlines_out) *nlines_out = nlines;
+  const size_t cells = (size_t)nbands * (size_t)nlines;
+  size_t bytes = 256;                         // ticket
+  bytes += ((cells * 4 + 255) / 256) * 256;   // flags
+  bytes += cells * 8 * L * 2;                 // agg + pref
+  return bytes;
+}
+
+static LineWs carve(void* ws, int Gw, int Gh, int L, int DIR) {
+  LineWs w;
+  int nbands, nlines_all;
+  line_ws_bytes(Gw, Gh, L, &nbands, &nlines_all);
+  char* p = (char*)ws;
+  w.ticket = (uint32_t*)p;
+  p += 256;
+  const size_t cells = (size_t)nbands * (size_t)nlines_all;
+  w.flags = (uint32_t*)p;
+  p += ((cells * 4 + 255) / 256) * 256;
+  w.agg = (uint64_t*)p;
+  p += cells * 8 * L;
+  w.pref = (uint64_t*)p;
+  w.nbands = nbands;
+  w.nlines = (DIR == 3) ? Gw : (Gw + Gh - 1);
+  // keep the slot stride fixed across directions
+  w.nlines = nlines_all;
+  w.ngroups = ((DIR == 3 ? Gw : Gw + Gh - 1) + kLinesPerCta - 1) / kLinesPerCta;
+  return w;
+}
+
+template <int L>
+static cudaError_t integrate_L(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
+                               uint32_t* epoch, int32_t* status, cudaStream_t st) {
+  cudaError_t e;
+  switch (pv.in_dtype) {
+    case ABF_U8: e = launch_rows<L, uint8_t>(pv, f, f_pitch, g, status, st); break;
+    case ABF_U16: e = launch_rows<L, uint16_t>(pv, f, f_pitch, g, status, st); break;
+    case ABF_F32: e = launch_rows<L, float>(pv, f, f_pitch, g, status, st); break;
+    default: e = launch_rows<L, double>(pv, f, f_pitch, g, status, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  for (int dir = 2; dir <= 4; ++dir) {
+    for (int k = 0; k < pv.n; ++k) {
+      const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
+      if (dir == 2) e = launch_lines<L, 2>(pv, g, carve(ws, pv.Gw, pv.Gh, L, 2), ep, status, st);
+      else if (dir == 3) e = launch_lines<L, 3>(pv, g, carve(ws, pv.Gw, pv.Gh, L, 3), ep, status, st);
+      else e = launch_lines<L, 4>(pv, g, carve(ws, pv.Gw, pv.Gh, L, 4), ep, status, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
+                          uint32_t* epoch, int32_t* status, cudaStream_t st) {
+  switch (pv.limbs) {
+    case 1: return integrate_L<1>(pv, f, f_pitch, g, ws, epoch, status, st);
+    case 2: return integrate_L<2>(pv, f, f_pitch, g, ws, epoch, status, st);
+    case 3: return integrate_L<3>(pv, f, f_pitch, g, ws, epoch, status, st);
+    default: return integrate_L<4>(pv, f, f_pitch, g, ws, epoch, status, st);
+  }
+}
+
+}  // namespace abf

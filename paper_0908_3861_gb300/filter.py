@@ -1,0 +1,98 @@
+"""Convenience wrapper over the C ABI: one plan, its device buffers (allocated
+with PyTorch), and the two steps of Sec. 7.  Marshalling and allocation only;
+the computation is the library's."""
+import torch
+
+from . import _abf as C
+
+_DT = {torch.uint8: C.ABF_U8, torch.uint16: C.ABF_U16, torch.float32: C.ABF_F32, torch.float64: C.ABF_F64}
+_OUT = {"f32": (C.ABF_F32, torch.float32), "f64": (C.ABF_F64, torch.float64)}
+
+
+class AdaptiveFilter:
+    """s = adaptive box-spline filter of f (abf_integrate + abf_filter)."""
+
+    def __init__(self, width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0, max_scale=8.0,
+                 out="f64", form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0, device=None):
+        self.device = torch.device(device or "cuda")
+        self.W, self.H, self.n = int(width), int(height), int(n)
+        self.in_dtype = in_dtype
+        self.out_code, self.out_dtype = _OUT[out]
+        d = C.abf_desc()
+        d.width, d.height, d.order_n = self.W, self.H, self.n
+        d.in_dtype = _DT[in_dtype]
+        d.out_dtype = self.out_code
+        d.form = C.FORMS[form]
+        d.scale_kind = C.SCALE_KINDS[scale_kind]
+        d.q_bits = int(q_bits)
+        d.in_frac_bits = int(frac_bits)
+        d.flags = 0
+        d.max_scale = float(max_scale)
+        d.min_scale = float(min_scale)
+        d.value_bound = float(value_bound)
+        d.max_scale_product = float(max_scale_product)
+        self.desc = d
+        with torch.cuda.device(self.device):
+            self.plan = C.abf_plan_create(d)
+        q = C.abf_plan_query(self.plan)
+        self.info = q
+        self.limbs = q["limbs"]
+        self.g = torch.empty(max(q["integrated_bytes"], 16), dtype=torch.uint8, device=self.device)
+        self.ws = torch.empty(max(q["workspace_bytes"], 16), dtype=torch.uint8, device=self.device)
+
+    def close(self):
+        if self.plan is not None:
+            C.abf_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_f(self, f):
+        assert f.is_cuda and f.dtype == self.in_dtype and f.shape == (self.H, self.W) and f.is_contiguous()
+        return f.shape[1] * f.element_size()
+
+    def _check_scales(self, sc):
+        assert sc.is_cuda and sc.dtype == torch.float32 and sc.shape == (self.H, self.W, 4) and sc.is_contiguous()
+        return self.W * 16
+
+    def integrate(self, f, stream=None):
+        C.abf_integrate(self.plan, f, self._check_f(f), self.g, self.ws, stream)
+
+    def filter(self, scales, out=None, stream=None):
+        sp = self._check_scales(scales)
+        if out is None:
+            out = torch.empty((self.H, self.W), dtype=self.out_dtype, device=self.device)
+        C.abf_filter(self.plan, self.g, 0, scales, sp, out, self.W * out.element_size(), self.ws, stream)
+        return out
+
+    def __call__(self, f, scales, out=None, stream=None):
+        self.integrate(f, stream)
+        return self.filter(scales, out, stream)
+
+    def numerators(self, scales, stream=None):
+        sp = self._check_scales(scales)
+        num = torch.empty((self.H, self.W, self.limbs), dtype=torch.int64, device=self.device)
+        C.abf_filter_numerator(self.plan, self.g, scales, sp, num, self.W * 8 * self.limbs, self.ws, stream)
+        return num
+
+    def prepare_scales(self, scales, stream=None):
+        sp = self._check_scales(scales)
+        out = torch.empty((self.H, self.W, 4), dtype=torch.int32, device=self.device)
+        C.abf_prepare_scales(self.plan, scales, sp, out, self.W * 16, stream)
+        return out
+
+    def integrated(self):
+        """The integrated image as (rows, pitch, limbs) int64 (a view of the buffer)."""
+        rows = self.H + self.info["halo_lrbt"][3]
+        pitch = self.info["g_pitch"]
+        return self.g[: rows * pitch * self.limbs * 8].view(torch.int64).view(rows, pitch, self.limbs)
+
+    def denominator(self):
+        return C.abf_plan_denominator(self.plan)
+
+    def device_status(self):
+        return C.abf_last_device_status(self.plan)

@@ -1,0 +1,231 @@
+"""GPU parity of the exact form (wrap-around integer running sums, integer
+ZP^{*n} weights) against the exact CPU oracle, through the C ABI.
+
+Bit-exact: the per-pixel integer steps C_k, the numerators S (modulo
+2^(64 L)), and the integrated image wherever the 3pi/4 recursion's backward ray
+leaves the lattice box through its bottom row.  Floating point: the binary64
+output s = S / Den within 1e-13 relative (a handful of roundings in the final
+division; the oracle rounds the exact rational once).
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import paper
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _small_workload(n, shape, q, dtype, seed, lo=1.0, hi=6.0, neg=False):
+    rng = np.random.default_rng(seed)
+    if dtype == "u8":
+        img = rng.integers(0, 256, shape).astype(np.uint8)
+        fb, vb = 0, 255.0
+    elif dtype == "u16":
+        img = rng.integers(0, 65536, shape).astype(np.uint16)
+        fb, vb = 0, 65535.0
+    elif dtype == "f32":
+        img = synthetic.image_f32_grid(rng, shape, 6.0, 4, 16)
+        fb, vb = 16, 255.0
+    else:
+        img = rng.integers(-300 if neg else 0, 300, shape).astype(np.float64)
+        fb, vb = 0, 300.0
+    sc = synthetic.scales_a4(rng, shape, lo, hi, 8.0)
+    return dict(image=img, frac_bits=fb, scale_kind="a4", scales=sc, n=n, q_bits=q, cmax=hi, value_bound=vb)
+
+
+def _check_all_pixels(w, res):
+    C_ref = gu.oracle_C(w)
+    assert (res["C"] == C_ref).all(), "integer steps differ"
+    S_ref, s_ref = paper.filter_image(gu.f_int(w), C_ref, w["n"], w["q_bits"], w["frac_bits"])
+    L = res["limbs"]
+    got = gu.wide_to_int(res["num"], L)
+    mod = 1 << (64 * L)
+    ref = [int(v) % mod for v in S_ref.ravel()]
+    bad = [i for i, (a, b) in enumerate(zip(got, ref)) if a != b]
+    assert not bad, "numerators differ at %d pixels, first %s" % (len(bad), divmod(bad[0], w["image"].shape[1]))
+    gu.assert_close_f64(res["s"], s_ref, rel=1e-13, absol=1e-300)
+    return S_ref, s_ref
+
+
+def _check_g(w, res):
+    """Integrated image vs the oracle's recursions, where the GPU's is exact."""
+    H, W = w["image"].shape
+    left, right, _, above = res["halo"]
+    L = res["limbs"]
+    g_or = paper.integrate(gu.f_int(w), w["n"], -left, W + right, 0, H + above, exact=True)
+    g = res["g"]
+    mod = 1 << (64 * L)
+    for yi in range(H + above):
+        for xi in range(W + left + right):
+            x = xi - left
+            if x + yi < W + right:   # backward 3pi/4 ray reaches row 0 inside the box
+                v = sum(int(g[yi, xi, i]) << (64 * i) for i in range(L))
+                assert v == int(g_or[yi, xi]) % mod, (xi, yi)
+
+
+CASES = [
+    (1, (37, 70), 4, "u8", 1),
+    (1, (45, 33), 8, "f64", 2),
+    (2, (37, 70), 4, "f32", 3),
+    (2, (19, 129), 3, "u16", 4),
+    (3, (14, 23), 2, "u8", 5),
+]
+
+
+@pytest.mark.parametrize("n,shape,q,dtype,seed", CASES)
+def test_exact_small_images_all_pixels(n, shape, q, dtype, seed):
+    w = _small_workload(n, shape, q, dtype, seed, neg=(dtype == "f64"))
+    res = gu.run_exact(w, want=("s", "num", "C", "g"))
+    assert res["status"] == 0
+    _check_all_pixels(w, res)
+    _check_g(w, res)
+
+
+@pytest.mark.parametrize("n", [1, 2])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 17), (17, 1), (2, 3)])
+def test_degenerate_sizes(n, shape):
+    w = _small_workload(n, shape, 3, "u8", 10 + n)
+    res = gu.run_exact(w)
+    assert res["status"] == 0
+    _check_all_pixels(w, res)
+
+
+def test_zero_and_constant_images():
+    for val in (0, 200):
+        w = _small_workload(1, (20, 30), 3, "u8", 7)
+        w["image"] = np.full((20, 30), val, dtype=np.uint8)
+        w["scales"] = np.broadcast_to(np.array([2.0, 2.0 * np.sqrt(2), 3.0, np.sqrt(2)], np.float32),
+                                      (20, 30, 4)).copy()
+        res = gu.run_exact(w)
+        _check_all_pixels(w, res)
+        if val == 0:
+            assert (res["s"] == 0).all()
+        else:   # integer c1, c3: unit lattice sum in the interior
+            assert (res["s"][6:-6, 6:-6] == val).all()
+
+
+def test_repeatable_bitwise():
+    """Two runs give identical numerators (no order dependence in the scans)."""
+    w = _small_workload(2, (64, 150), 5, "f32", 21)
+    a = gu.run_exact(w, want=("num",))["num"]
+    b = gu.run_exact(w, want=("num",))["num"]
+    assert (a == b).all()
+
+
+def test_invalid_scales_are_flagged():
+    from paper_0908_3861_gb300 import _abf
+    w = _small_workload(1, (16, 40), 3, "u8", 8)
+    sc = w["scales"].copy()
+    sc[3, 5, 0] = np.nan
+    sc[7, 9, 2] = 0.0
+    sc[10, 30, 1] = 100.0      # above max_scale
+    w["scales"] = sc
+    res = gu.run_exact(w, want=("s",))
+    assert res["status"] & _abf.ABF_DEV_BAD_SCALE
+    s = res["s"]
+    assert np.isnan(s[3, 5]) and np.isnan(s[7, 9]) and np.isnan(s[10, 30])
+    ok = ~np.isnan(s)
+    assert ok.sum() == s.size - 3
+
+
+def test_bad_input_is_flagged():
+    from paper_0908_3861_gb300 import _abf
+    w = _small_workload(1, (16, 40), 3, "f32", 9)
+    img = w["image"].copy()
+    img[2, 3] = 1.0 + 2.0 ** -20        # not on the 2^-16 grid
+    w["image"] = img
+    res = gu.run_exact(w, want=("s",))
+    assert res["status"] & _abf.ABF_DEV_BAD_INPUT
+
+
+def test_plan_refuses_numerator_beyond_four_limbs():
+    import torch
+    from paper_0908_3861_gb300 import _abf, AdaptiveFilter
+    with pytest.raises(_abf.AbfError) as e:
+        AdaptiveFilter(64, 64, 3, torch.float64, scale_kind="a4", q_bits=8, frac_bits=40, max_scale=1000.0,
+                       value_bound=1e30)
+    assert e.value.status == 5   # ABF_ERR_RANGE
+
+
+def _sample_pixels(H, W, k, seed):
+    rng = np.random.default_rng(seed)
+    pts = {(0, 0), (W - 1, 0), (0, H - 1), (W - 1, H - 1), (W // 2, 0), (0, H // 2), (W - 1, H // 2),
+           (W // 2, H - 1)}
+    while len(pts) < k:
+        pts.add((int(rng.integers(0, W)), int(rng.integers(0, H))))
+    return sorted(pts)
+
+
+def _check_sampled(w, res, pix):
+    C_ref = gu.oracle_C(w)
+    assert (res["C"] == C_ref).all(), "integer steps differ"
+    S_ref, s_ref = paper.filter_pixels(gu.f_int(w), C_ref, w["n"], w["q_bits"], w["frac_bits"], pix)
+    L = res["limbs"]
+    mod = 1 << (64 * L)
+    for (x, y), S, sv in zip(pix, S_ref, s_ref):
+        got = sum(int(res["num"][y, x, i]) << (64 * i) for i in range(L))
+        assert got == S % mod, (x, y)
+        assert abs(res["s"][y, x] - sv) <= 1e-13 * abs(sv) + 1e-300, (x, y, res["s"][y, x], sv)
+
+
+def _measured_product(w):
+    import torch
+    from paper_0908_3861_gb300 import _abf
+    H, W = w["image"].shape
+    d = _abf.abf_desc()
+    d.width, d.height, d.order_n = W, H, w["n"]
+    d.scale_kind = _abf.SCALE_KINDS[w["scale_kind"]]
+    d.q_bits, d.max_scale = w["q_bits"], w["cmax"]
+    sc = gu.to_device(w["scales"].astype(np.float32), "cuda:0")
+    mx, prod = _abf.abf_measure_scales(d, sc, W * 16)
+    assert mx <= w["cmax"]
+    return prod
+
+
+def test_full_size_256_order1_all_pixels():
+    """256x256 integer image, n = 1, paper scales in [1, 8], Q = 8 (every pixel)."""
+    w = synthetic.workload("c1")
+    res = gu.run_exact(w)
+    assert res["status"] == 0 and res["limbs"] == 1
+    _check_all_pixels(w, res)
+
+
+@pytest.mark.slow
+def test_full_size_2048_order2_ellipse_sampled():
+    """2048x2048 float32 on the 2^-16 grid, n = 2, ellipse scales, Q = 8."""
+    w = synthetic.workload("c2")
+    prod = _measured_product(w)
+    res = gu.run_exact(w, max_scale_product=prod)
+    assert res["status"] == 0
+    assert np.isfinite(res["s"]).all()
+    H, W = w["image"].shape
+    _check_sampled(w, res, _sample_pixels(H, W, 24, 1))
+
+
+@pytest.mark.slow
+def test_full_size_8192_order3_sampled():
+    """8192x8192 uint16, n = 3, paper scales in [1, 48], Q = 8: sampled pixels,
+    and the first rows of the integrated image modulo 2^64."""
+    w = synthetic.workload("c3")
+    prod = _measured_product(w)
+    res = gu.run_exact(w, max_scale_product=prod, want=("s", "num", "C"))
+    assert res["status"] == 0
+    H, W = w["image"].shape
+    _check_sampled(w, res, _sample_pixels(H, W, 10, 2))
+    filt = res["filt"]
+    left, right, _, above = res["halo"]
+    rows = 48
+    g = filt.integrated()[:rows].cpu().numpy().astype(np.uint64)[..., 0]
+    g_or = paper.integrate(gu.f_int(w)[:rows], w["n"], -left, W + right, 0, rows, exact=False)
+    xs = np.arange(W + left + right)[None, :] - left
+    ys = np.arange(rows)[:, None]
+    region = xs + ys < W + right
+    assert (g[:, :W + left + right][region] == g_or[region]).all()
