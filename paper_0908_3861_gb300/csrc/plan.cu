@@ -15,6 +15,7 @@
 // of one fractional offset) sums to D exactly (partition of unity); the
 // generator checks that too.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -238,6 +239,20 @@ abf_status get_table(int device, int n, int P, DeviceTable* out) {
   return ABF_OK;
 }
 
+// Look-back flags carry an epoch so that a workspace needs no clearing between
+// scans.  Epochs come from one process-wide counter, so two plans (or two
+// threads) that use the same workspace one after the other never read each
+// other's flags as current.  Epoch 0 is never issued: it is the value of a
+// cleared flag.
+std::atomic<uint32_t> g_epoch{0};
+
+uint32_t reserve_epochs(uint32_t count) {
+  for (;;) {
+    uint32_t base = g_epoch.fetch_add(count) & 0x3fffffffu;
+    if (base + count <= 0x3fffffffu) return base;  // the scans use base+1 .. base+count
+  }
+}
+
 double u128_to_double(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073709551616.0 + (double)(uint64_t)v; }
 
 }  // namespace
@@ -251,7 +266,6 @@ struct abf_plan_s {
   int device;
   int32_t* d_status = nullptr;
   size_t g_bytes = 0, ws_bytes = 0;
-  uint32_t epoch = 0;
 };
 
 extern "C" {
@@ -388,7 +402,8 @@ abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g,
   const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
   if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
   if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
-  return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &p->epoch, p->d_status, st));
+  uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
+  return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, p->d_status, st));
 }
 
 abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const void* d_scales, size_t scale_pitch,

@@ -229,3 +229,22 @@ def test_full_size_8192_order3_sampled():
     ys = np.arange(rows)[:, None]
     region = xs + ys < W + right
     assert (g[:, :W + left + right][region] == g_or[region]).all()
+
+
+def test_two_plans_share_one_workspace():
+    """A workspace left behind by one plan's scans is safe for another plan."""
+    wa = _small_workload(2, (40, 90), 4, "u8", 31)
+    wb = _small_workload(2, (52, 70), 4, "u8", 32)
+    ra = gu.run_exact(wa, want=("num",))
+    rb = gu.run_exact(wb, want=("num",))
+    fa, fb = ra["filt"], rb["filt"]
+    big = fa.ws if fa.ws.numel() >= fb.ws.numel() else fb.ws
+    fa.ws = big
+    fb.ws = big
+    import torch
+    for _ in range(2):
+        for w, f, ref in ((wa, fa, ra["num"]), (wb, fb, rb["num"])):
+            f.integrate(gu.to_device(w["image"], "cuda:0"))
+            got = f.numerators(gu.to_device(w["scales"].astype(np.float32), "cuda:0"))
+            torch.cuda.synchronize()
+            assert (got.cpu().numpy().astype(np.uint64) == ref).all()
