@@ -123,9 +123,10 @@ abf_status abf_plan_query(abf_plan plan, size_t* integrated_bytes, size_t* works
  *           3pi/4 recursion's backward ray leaves the box through its bottom
  *           row; elsewhere it differs from them by a polynomial of degree < n
  *           along each 3pi/4 line, which the mesh annihilates.
- *   d_ws  : workspace of abf_plan_query() bytes (scan carries and flags).
- *           It needs no clearing and may be reused by any plan afterwards,
- *           but two calls that overlap on the GPU must not share it.         */
+ *   d_ws  : workspace of abf_plan_query() bytes (scan carries and flags),
+ *           any contents: the call clears what must start at zero.  It may be
+ *           reused by any plan afterwards, but two calls that overlap on the
+ *           GPU must not share it.                                           */
 abf_status abf_integrate(abf_plan plan, const void* d_f, size_t f_pitch, void* d_g,
                          void* d_ws, cudaStream_t stream);
 

@@ -239,11 +239,10 @@ abf_status get_table(int device, int n, int P, DeviceTable* out) {
   return ABF_OK;
 }
 
-// Look-back flags carry an epoch so that a workspace needs no clearing between
-// scans.  Epochs come from one process-wide counter, so two plans (or two
-// threads) that use the same workspace one after the other never read each
-// other's flags as current.  Epoch 0 is never issued: it is the value of a
-// cleared flag.
+// Look-back flags carry an epoch so that the passes of one call need no
+// clearing between them (the call clears the flags once, at its start).
+// Epochs come from one process-wide counter.  Epoch 0 is never issued: it is
+// the value of a cleared flag.
 std::atomic<uint32_t> g_epoch{0};
 
 uint32_t reserve_epochs(uint32_t count) {

@@ -263,6 +263,17 @@ size_t line_ws_bytes(int Gw, int Gh, int L, int* nbands_out, int* nlines_out) {
   return bytes;
 }
 
+// Bytes at the start of a line-scan workspace that must read as zero before
+// the first scan of a call: the ticket counter and the look-back flags.  A
+// workspace holds arbitrary bytes when it arrives (a fresh allocation may
+// reuse memory of any earlier buffer), and a stale word can look like a valid
+// flag, so every call clears them; later passes of the same call tell their
+// flags apart by epoch.
+size_t line_ws_zero_bytes(int Gw, int Gh) {
+  const size_t cells = (size_t)((Gh + kBand - 1) / kBand) * (size_t)(Gw + Gh);
+  return 256 + ((cells * 4 + 255) / 256) * 256;
+}
+
 static LineWs carve(void* ws, int Gw, int Gh, int L, int DIR) {
   LineWs w;
   int nbands, nlines_all;
@@ -309,6 +320,8 @@ static cudaError_t integrate_L(const PlanView& pv, const void* f, size_t f_pitch
 
 cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
                           uint32_t* epoch, int32_t* status, cudaStream_t st) {
+  const cudaError_t e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
+  if (e != cudaSuccess) return e;
   switch (pv.limbs) {
     case 1: return integrate_L<1>(pv, f, f_pitch, g, ws, epoch, status, st);
     case 2: return integrate_L<2>(pv, f, f_pitch, g, ws, epoch, status, st);
