@@ -130,6 +130,29 @@ abf_status abf_plan_query(abf_plan plan, size_t* integrated_bytes, size_t* works
 abf_status abf_integrate(abf_plan plan, const void* d_f, size_t f_pitch, void* d_g,
                          void* d_ws, cudaStream_t stream);
 
+/* abf_integrate without a caller workspace, for callers that cannot allocate
+ * device memory: for example a serving loop whose memory is reserved once, up
+ * front, by a caching allocator it may not step around, or code that must not
+ * risk the implicit device synchronisation of cudaMalloc / cudaFree.  The paper
+ * has no counterpart: this is an interface for such callers only.
+ *
+ * The scan carries and flags use a fixed scratch array inside the library
+ * (32 MiB, a static device array that every GPU loading the library holds until
+ * the process exits).  The call allocates nothing; the caller still supplies
+ * d_f and d_g exactly as for abf_integrate.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   - The current device must be the plan's device (else ABF_ERR_INVALID).
+ *   - Plans whose workspace (abf_plan_query) exceeds 32 MiB are rejected with
+ *     ABF_ERR_UNSUPPORTED (e.g. order 2, two limbs, steps up to 150: images up
+ *     to about 2048 x 2048).
+ *   - Every call shares the one array and clears the parts that must start at
+ *     zero; calls that overlap on the GPU (other streams, other threads) race
+ *     on it and give wrong results: serialise them.                          */
+abf_status abf_integrate_noalloc(abf_plan plan, const void* d_f, size_t f_pitch, void* d_g,
+                                 cudaStream_t stream);
+
 /* Adaptive step (Eq. (final_eqn)) for every pixel.
  *   exact form:      d_src = the integrated image from abf_integrate().
  *   PLAIN_F64 / TILE_F32: d_src = the image f itself (pitch f_pitch bytes);

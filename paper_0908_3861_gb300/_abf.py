@@ -56,6 +56,7 @@ def lib():
         "abf_plan_destroy": ([vp], st),
         "abf_plan_query": ([vp, P(sz), P(sz), P(i32), P(i32), P(ctypes.c_int64)], st),
         "abf_integrate": ([vp, vp, sz, vp, vp, vp], st),
+        "abf_integrate_noalloc": ([vp, vp, sz, vp, vp], st),
         "abf_filter": ([vp, vp, sz, vp, sz, vp, sz, vp, vp], st),
         "abf_filter_numerator": ([vp, vp, vp, sz, vp, sz, vp, vp], st),
         "abf_prepare_scales": ([vp, vp, sz, vp, sz, vp], st),
@@ -118,6 +119,11 @@ def abf_plan_query(plan):
 
 def abf_integrate(plan, f, f_pitch, g, ws, stream=None):
     _check(lib().abf_integrate(plan, _ptr(f), f_pitch, _ptr(g), _ptr(ws), _stream(stream)), "abf_integrate")
+
+
+def abf_integrate_noalloc(plan, f, f_pitch, g, stream=None):
+    """abf_integrate with the library's fixed scratch (no workspace argument)."""
+    _check(lib().abf_integrate_noalloc(plan, _ptr(f), f_pitch, _ptr(g), _stream(stream)), "abf_integrate_noalloc")
 
 
 def abf_filter(plan, src, src_pitch, scales, scale_pitch, s, s_pitch, ws, stream=None):

@@ -38,6 +38,9 @@ cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t sc
                                int32_t* status, cudaStream_t st);
 cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t scale_pitch,
                                unsigned long long* out2, int32_t* status, cudaStream_t st);
+size_t noalloc_scratch_bytes();
+cudaError_t run_integrate_noalloc(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, uint32_t* epoch,
+                                  int32_t* status, cudaStream_t st);
 }  // namespace abf
 
 using u128 = unsigned __int128;
@@ -403,6 +406,19 @@ abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g,
   if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
   uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
   return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, p->d_status, st));
+}
+
+abf_status abf_integrate_noalloc(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t st) {
+  if (!p || !d_f || !d_g) return ABF_ERR_INVALID;
+  const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
+  if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
+  if ((uintptr_t)d_g & 15) return ABF_ERR_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
+  if (dev != p->device) return ABF_ERR_INVALID;
+  if (p->ws_bytes > abf::noalloc_scratch_bytes()) return ABF_ERR_UNSUPPORTED;
+  uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
+  return cuda_status(abf::run_integrate_noalloc(p->pv, d_f, f_pitch, (uint64_t*)d_g, &ep, p->d_status, st));
 }
 
 abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const void* d_scales, size_t scale_pitch,

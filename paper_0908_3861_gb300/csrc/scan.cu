@@ -21,6 +21,8 @@
 //                consecutive addresses), lines cut into bands of R rows; bands
 //                are chained by decoupled look-back on per-line flags, with a
 //                bounded wait that raises ABF_DEV_TIMEOUT instead of hanging.
+#include <mutex>
+
 #include "abf_internal.cuh"
 
 namespace abf {
@@ -328,6 +330,51 @@ cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uin
     case 3: return integrate_L<3>(pv, f, f_pitch, g, ws, epoch, status, st);
     default: return integrate_L<4>(pv, f, f_pitch, g, ws, epoch, status, st);
   }
+}
+
+// ------------------------------------------------------ fixed-scratch variant
+// Scratch for abf_integrate_noalloc: callers that cannot allocate device
+// memory get the line scans' look-back workspace from this fixed array instead
+// of a buffer of their own.  It lives in the library's device image, so every
+// GPU that loads the library holds it until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+// Device address of the fixed scratch on the current device.  In host code the
+// array's name only stands for it, so the address is looked up once per device
+// (with that device current) and remembered.
+static cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+// The same scans as run_integrate, on the fixed scratch.  The ticket and the
+// flags are cleared first: the array keeps whatever the previous call left.
+cudaError_t run_integrate_noalloc(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, uint32_t* epoch,
+                                  int32_t* status, cudaStream_t st) {
+  void* ws = nullptr;
+  cudaError_t e = noalloc_scratch(&ws);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
+  if (e != cudaSuccess) return e;
+  return run_integrate(pv, f, f_pitch, g, ws, epoch, status, st);
 }
 
 }  // namespace abf
