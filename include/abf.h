@@ -84,7 +84,7 @@ typedef struct {
   int32_t out_dtype;          /* ABF_F32 or ABF_F64                                   */
   int32_t form;               /* abf_form                                             */
   int32_t scale_kind;         /* abf_scale_kind                                       */
-  int32_t q_bits;             /* Q: steps on the 2^-Q grid (1..9; 1..8 for n = 3)     */
+  int32_t q_bits;             /* Q: steps on the 2^-Q grid (1..9 for n = 1, else 1..8) */
   int32_t in_frac_bits;       /* F: f 2^F is an integer (exact form); 0 for u8/u16    */
   int32_t flags;              /* reserved, 0                                          */
   double max_scale;           /* upper bound on every step c_k (lattice units)        */
@@ -203,10 +203,14 @@ const char* abf_status_str(abf_status s);
 
 /* Host-only: generate the ZP^{*n} weight table for order n and grid 2^-Q (the
  * table abf_plan_create uploads) into a caller buffer, without touching a
- * device.  Layout: (2^P)^2 rows (row index ry 2^P + rx, P = Q for even n,
- * Q + 1 for odd n), each (3n)^2 weights D ZP^{*n}(r - d) ordered [dy][dx],
- * d from d_min = -3n/2 + 1 (n even) or -(3n - 1)/2 (n odd); r = rx 2^-P
- * (minus 1/2 for odd n).  Little-endian words of *wbytes bytes (4, 8 or 16).
+ * device.  Layout: (2^P)^2 rows, row index ry 2^P + rx (P = Q for even n,
+ * Q + 1 for odd n; fractional offset r = (rx, ry) 2^-P, minus 1/2 for odd n).
+ * Row entries: D ZP^{*n}(r - d) for the lattice neighbours d that can carry a
+ * non-zero weight (9, 32, 69 of the (3n)^2 candidates for n = 1, 2, 3), in
+ * [dy][dx] order, dx, dy from d_min = -3n/2 + 1 (n even) or -(3n - 1)/2
+ * (n odd); the dropped candidates are those whose box of r - d misses the
+ * open support |x|, |y| < 3n/2, |x +- y| < 2n.  Little-endian words of
+ * *wbytes bytes (4, 8 or 16).
  * With out = NULL only *needed_bytes, *wbytes and D are returned.            */
 abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t out_bytes,
                                  size_t* needed_bytes, int32_t* wbytes, uint32_t* D_words4);

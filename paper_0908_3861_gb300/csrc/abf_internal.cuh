@@ -104,6 +104,70 @@ __device__ __forceinline__ void wmac128(Wide<L>& acc, const Wide<L>& g, uint64_t
   }
 }
 
+// acc += g * w (mod 2^128) for a two-limb g and a 64-bit w, as one chain of
+// 32-bit multiply-adds with carry (the twelve partial products of a
+// 4 x 2 word product that land below bit 128).
+__device__ __forceinline__ void wmac2_u64(Wide<2>& acc, const Wide<2>& g, uint64_t w) {
+  uint32_t r0 = (uint32_t)acc.w[0], r1 = (uint32_t)(acc.w[0] >> 32);
+  uint32_t r2 = (uint32_t)acc.w[1], r3 = (uint32_t)(acc.w[1] >> 32);
+  const uint32_t a0 = (uint32_t)g.w[0], a1 = (uint32_t)(g.w[0] >> 32);
+  const uint32_t a2 = (uint32_t)g.w[1], a3 = (uint32_t)(g.w[1] >> 32);
+  const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32);
+  asm("{\n\t"
+      "mad.lo.cc.u32  %0, %4, %8, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %8, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
+      "madc.hi.u32    %3, %6, %8, %3;\n\t"
+      "mad.lo.cc.u32  %1, %5, %8, %1;\n\t"
+      "madc.lo.cc.u32 %2, %6, %8, %2;\n\t"
+      "madc.lo.u32    %3, %7, %8, %3;\n\t"
+      "mad.lo.cc.u32  %1, %4, %9, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %9, %2;\n\t"
+      "madc.hi.u32    %3, %5, %9, %3;\n\t"
+      "mad.lo.cc.u32  %2, %5, %9, %2;\n\t"
+      "madc.lo.u32    %3, %6, %9, %3;\n\t"
+      "}"
+      : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(w0), "r"(w1));
+  acc.w[0] = ((uint64_t)r1 << 32) | r0;
+  acc.w[1] = ((uint64_t)r3 << 32) | r2;
+}
+
+// acc += g * w (mod 2^128) for a two-limb g and a 32-bit w (seven partial products).
+__device__ __forceinline__ void wmac2_u32(Wide<2>& acc, const Wide<2>& g, uint32_t w0) {
+  uint32_t r0 = (uint32_t)acc.w[0], r1 = (uint32_t)(acc.w[0] >> 32);
+  uint32_t r2 = (uint32_t)acc.w[1], r3 = (uint32_t)(acc.w[1] >> 32);
+  const uint32_t a0 = (uint32_t)g.w[0], a1 = (uint32_t)(g.w[0] >> 32);
+  const uint32_t a2 = (uint32_t)g.w[1], a3 = (uint32_t)(g.w[1] >> 32);
+  asm("{\n\t"
+      "mad.lo.cc.u32  %0, %4, %8, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %8, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
+      "madc.hi.u32    %3, %6, %8, %3;\n\t"
+      "mad.lo.cc.u32  %1, %5, %8, %1;\n\t"
+      "madc.lo.cc.u32 %2, %6, %8, %2;\n\t"
+      "madc.lo.u32    %3, %7, %8, %3;\n\t"
+      "}"
+      : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(w0));
+  acc.w[0] = ((uint64_t)r1 << 32) | r0;
+  acc.w[1] = ((uint64_t)r3 << 32) | r2;
+}
+
+// -a (mod 2^(64L))
+template <int L>
+__device__ __forceinline__ Wide<L> wneg(const Wide<L>& a) {
+  Wide<L> r;
+  uint64_t carry = 1;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const uint64_t v = ~a.w[i] + carry;
+    carry = (carry && v == 0) ? 1 : 0;
+    r.w[i] = v;
+  }
+  return r;
+}
+
 // acc += w * t for a small signed integer w.
 template <int L>
 __device__ __forceinline__ void wmac_signed(Wide<L>& acc, const Wide<L>& t, int w) {
@@ -190,6 +254,50 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// ------------------------------------------------------- interpolation stencil
+// A tap y = p + r has r in [0,1)^2 (even n, p = floor y) or [-1/2,1/2)^2 (odd
+// n, p = nearest); its lattice neighbours are p + d, d in [dmin, dmin + 3n)^2.
+// The weight of neighbour d is ZP^{*n}(r - d), whose support is the open
+// octagon |x|, |y| < 3n/2, |x +- y| < 2n.  A neighbour whose weight is zero for
+// every r is dropped: the box of possible r - d and the octagon are convex, so
+// they meet iff their projections on x, y, x + y and x - y overlap (worked in
+// doubled coordinates).  9, 32 and 69 neighbours remain for n = 1, 2, 3.
+template <int N>
+__host__ __device__ constexpr bool stencil_keeps(int ix, int iy) {
+  const int dmin = (N % 2 == 0) ? (-(3 * N) / 2 + 1) : (-(3 * N - 1) / 2);
+  const int off = (N % 2 == 0) ? 0 : -1;  // 2 x (lower end of r)
+  const int lx = -2 * (dmin + ix) + off, hx = lx + 2;
+  const int ly = -2 * (dmin + iy) + off, hy = ly + 2;
+  return lx < 3 * N && -3 * N < hx && ly < 3 * N && -3 * N < hy && lx + ly < 4 * N && -4 * N < hx + hy &&
+         lx - hy < 4 * N && -4 * N < hx - ly;
+}
+
+template <int N>
+__host__ __device__ constexpr int stencil_count() {
+  int c = 0;
+  for (int iy = 0; iy < 3 * N; ++iy)
+    for (int ix = 0; ix < 3 * N; ++ix) c += stencil_keeps<N>(ix, iy) ? 1 : 0;
+  return c;
+}
+
+template <int N>
+struct Stencil {
+  static constexpr int kN3 = 3 * N;
+  static constexpr int kDmin = (N % 2 == 0) ? (-(3 * N) / 2 + 1) : (-(3 * N - 1) / 2);
+  int count;
+  int dx[9 * N * N];
+  int dy[9 * N * N];
+  constexpr Stencil() : count(0), dx(), dy() {
+    for (int iy = 0; iy < kN3; ++iy)
+      for (int ix = 0; ix < kN3; ++ix)
+        if (stencil_keeps<N>(ix, iy)) {
+          dx[count] = kDmin + ix;
+          dy[count] = kDmin + iy;
+          ++count;
+        }
+  }
+};
+
 // ---------------------------------------------------------------- host side
 
 // Everything a kernel needs to know about one plan (passed by value).
@@ -203,6 +311,7 @@ struct PlanView {
   int limbs;
   double value_bound;             // bound on |f|
   double log2D;                   // log2 of the weight denominator
+  float log2_base;                // log2(D |f|max 2^F): the pixel-independent part of the bound
   double Dd;                      // D as binary64
   int table_bytes_per_w;          // 4, 8 or 16
   const void* table;              // (2^P)^2 rows of (3n)^2 weights

@@ -96,14 +96,15 @@ __device__ __forceinline__ bool pixel_steps(const PlanView& pv, const float4* sc
   return true;
 }
 
-// log2 of the numerator bound for this pixel (see file header).
-__device__ __forceinline__ double numerator_log2_bound(const PlanView& pv, const int C[4]) {
-  double lp = 0.0;
+// log2 of the numerator bound for this pixel (see file header), in binary32
+// with a margin that covers its rounding (the check only has to be safe).
+__device__ __forceinline__ float numerator_log2_bound(const PlanView& pv, const int C[4]) {
+  float lp = 0.0f;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) lp += log2((double)C[k]);
-  const double q = ldexp(1.0, pv.Q);
-  const double kappa = (1.0 + q / C[0]) * (1.0 + q / C[2]);
-  return pv.log2D + pv.n * (lp - 4.0 * pv.Q) + log2(pv.value_bound) + pv.F + log2(kappa) + 1e-6;
+  for (int k = 0; k < 4; ++k) lp += __log2f((float)C[k]) - (float)pv.Q;
+  const float q = (float)(1 << pv.Q);
+  const float kappa = (1.0f + q / (float)C[0]) * (1.0f + q / (float)C[2]);
+  return pv.log2_base + (float)pv.n * lp + __log2f(kappa) + 0.05f;
 }
 
 // (-1)^j binom(N, j) for N <= 3: binom is 1 at the ends and N inside.
@@ -113,90 +114,40 @@ __device__ __forceinline__ int signed_binom(int j) {
   return (j & 1) ? -c : c;
 }
 
-// Weight table element types per order: D < 2^32 (n = 1), < 2^64 (n = 2), < 2^128 (n = 3).
+// Weight table element types per order: D < 2^32 (n = 1), < 2^60 (n = 2), < 2^121 (n = 3)
+// (room for the FD weight |w_j| <= 16, resp. 81, folded into the table weight).
 template <int N> struct WeightT;
 template <> struct WeightT<1> { using T = uint32_t; };
 template <> struct WeightT<2> { using T = uint64_t; };
 template <> struct WeightT<3> { using T = ulonglong2; };
 
+// acc += g * w for the table word types.
 template <int L, typename WT>
 __device__ __forceinline__ void mac_weight(Wide<L>& acc, const Wide<L>& gv, const WT w) {
   if constexpr (sizeof(WT) == 16) {
     wmac128<L>(acc, gv, w.x, w.y);
+  } else if constexpr (L == 2 && sizeof(WT) == 8) {
+    wmac2_u64(acc, gv, w);
+  } else if constexpr (L == 2 && sizeof(WT) == 4) {
+    wmac2_u32(acc, gv, w);
   } else {
     wmac<L>(acc, gv, (uint64_t)w);
   }
 }
 
-template <typename WT>
-__device__ __forceinline__ bool wnonzero(const WT w) {
-  if constexpr (sizeof(WT) == 16) return (w.x | w.y) != 0;
-  else return w != 0;
-}
-
-// The numerator S for pixel (x, y) with integer steps C.
-template <int N, int L>
-__device__ __forceinline__ Wide<L> mesh_numerator(const PlanView& pv, const uint64_t* __restrict__ g,
-                                                  int x, int y, const int C[4]) {
-  using WT = typename WeightT<N>::T;
-  constexpr int N3 = 3 * N;
-  constexpr int DMIN = (N % 2 == 0) ? (-(3 * N) / 2 + 1) : (-(3 * N - 1) / 2);
-  const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
-  const int P = pv.P;
-  const int sh = (N % 2 == 0) ? 0 : 1;        // 2^(P-Q)
-  const int one = 1 << pv.Q;
-  const int half = (N % 2 == 0) ? 0 : (1 << (P - 1));
-  const int mask = (1 << P) - 1;
-  // tau in units of 2^-P: (n/2) sum_k (C_k - 2^Q) v_k 2^(P-Q)
-  const int tx = (N * (C[0] + C[1] - C[3] - one)) << sh >> 1;
-  const int ty = (N * (C[1] + C[2] + C[3] - 3 * one)) << sh >> 1;
-  const int y0x = (x << P) + tx;
-  const int y0y = (y << P) + ty;
-  const int s1 = C[0] << sh, s2 = C[1] << sh, s3 = C[2] << sh, s4 = C[3] << sh;
-  const long long rowpitch = pv.Gp;
-  const int left = pv.left;
-
-  Wide<L> S;
-  wzero<L>(S);
-#pragma unroll 1
-  for (int j4 = 0; j4 <= N; ++j4) {
-#pragma unroll 1
-    for (int j2 = 0; j2 <= N; ++j2) {
-#pragma unroll 1
-      for (int j3 = 0; j3 <= N; ++j3) {
-#pragma unroll 1
-        for (int j1 = 0; j1 <= N; ++j1) {
-          const int w = signed_binom<N>(j1) * signed_binom<N>(j2) * signed_binom<N>(j3) * signed_binom<N>(j4);
-          // y_j = y0 - j1 c1 v1 - j2 c2 v2 - j3 c3 v3 - j4 c4 v4
-          const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4;
-          const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4;
-          const int px = (Yx + half) >> P;
-          const int py = (Yy + half) >> P;
-          const int rx = (Yx + half) & mask;
-          const int ry = (Yy + half) & mask;
-          const WT* __restrict__ wrow = table + (size_t)((ry << P) | rx) * (N3 * N3);
-          Wide<L> acc;
-          wzero<L>(acc);
-#pragma unroll
-          for (int iy = 0; iy < N3; ++iy) {
-            const int k2 = py + DMIN + iy;
-            if (k2 < 0) continue;  // rows below the image: g = 0
-            const uint64_t* __restrict__ grow = g + ((size_t)k2 * rowpitch + (size_t)(px + DMIN + left)) * L;
-#pragma unroll
-            for (int ix = 0; ix < N3; ++ix) {
-              const WT wt = wrow[iy * N3 + ix];
-              if (wnonzero(wt)) {
-                const Wide<L> gv = wload<L>(grow + (size_t)ix * L);
-                mac_weight<L, WT>(acc, gv, wt);
-              }
-            }
-          }
-          wmac_signed<L>(S, acc, w);
-        }
-      }
-    }
+// Table weight times the FD weight |w_j| (a power of two for n <= 2).
+template <int N, typename WT>
+__device__ __forceinline__ WT scale_weight(WT w, int aw) {
+  if constexpr (N == 1) {
+    return w;
+  } else if constexpr (N == 2) {
+    return w << (__ffs(aw) - 1);
+  } else {
+    // 128-bit times a small factor (|w_j| <= 81); fits: D 81 < 2^128.
+    const uint64_t lo = w.x * (uint64_t)aw;
+    const uint64_t hi = __umul64hi(w.x, (uint64_t)aw) + w.y * (uint64_t)aw;
+    return make_ulonglong2(lo, hi);
   }
-  return S;
 }
 
 template <typename TOut>
@@ -205,45 +156,172 @@ __device__ __forceinline__ void store_out(void* s, size_t s_pitch, int x, int y,
   row[x] = (TOut)v;
 }
 
+// One warp per run of 32 pixels of a row.  Lane i reads the scales of pixel
+// x0 + i and rounds them to integer steps; then the warp walks the 32 pixels
+// one at a time.  For a pixel, the lanes first tabulate its (n+1)^4 taps
+// (lattice point p_j, table row r_j, FD weight w_j) in shared memory; then the
+// (tap, neighbour) pairs -- (n+1)^4 taps times the stencil's neighbours -- are
+// dealt to the lanes in order, so the lanes of one tap read one contiguous
+// table row and one compact patch of g.  For n = 2 the 32 neighbours are
+// exactly the 32 lanes: every lane keeps its neighbour, the tap is the same
+// for the whole warp, and w_j = +-2^k folds into the table weight as a shift
+// with the sign choosing one of two accumulators.  Each lane accumulates
+// w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
+// numerator, which lane i keeps for its own pixel and stores at the end.
+constexpr int kMeshWarps = 8;
+
 template <int N, int L, typename TOut>
-__global__ void __launch_bounds__(128) mesh_exact_kernel(const PlanView pv, const uint64_t* __restrict__ g,
-                                                         const float4* __restrict__ scales, size_t scale_pitch,
-                                                         void* __restrict__ s, size_t s_pitch,
-                                                         uint64_t* __restrict__ num, size_t num_pitch,
-                                                         int32_t* status) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= pv.W || y >= pv.H) return;
-  int C[4];
-  if (!pixel_steps(pv, scales, scale_pitch, x, y, C)) {
-    raise_status(status, ABF_DEV_BAD_SCALE);
-    if (s) store_out<TOut>(s, s_pitch, x, y, __longlong_as_double(0x7ff8000000000000ll));
-    return;
+__global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  using WT = typename WeightT<N>::T;
+  constexpr int R = stencil_count<N>();
+  constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
+  constexpr int PAIRS = TAPS * R;
+  constexpr int ITERS = (PAIRS + 31) / 32;
+  __shared__ int s_dx[R], s_dy[R];
+  __shared__ int4 s_tap[kMeshWarps][TAPS];
+  if (threadIdx.x == 0) {
+    // the stencil's neighbours, in the same order as the table rows
+    int c = 0;
+    for (int iy = 0; iy < 3 * N; ++iy)
+      for (int ix = 0; ix < 3 * N; ++ix)
+        if (stencil_keeps<N>(ix, iy)) {
+          s_dx[c] = Stencil<N>::kDmin + ix;
+          s_dy[c] = Stencil<N>::kDmin + iy;
+          ++c;
+        }
   }
-  if (numerator_log2_bound(pv, C) >= 64.0 * L - 1.0) {
-    raise_status(status, ABF_DEV_RANGE);
-    if (s) store_out<TOut>(s, s_pitch, x, y, __longlong_as_double(0x7ff8000000000000ll));
-    return;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int wslot = threadIdx.x >> 5;
+  const int segs = (pv.W + 31) >> 5;
+  const int wid = blockIdx.x * kMeshWarps + wslot;
+  if (wid >= segs * pv.H) return;
+  const int y = wid / segs;
+  const int x0 = (wid - y * segs) * 32;
+  const int myx = x0 + lane;
+
+  // a5: this lane's pixel -> integer steps, validity, numerator bound
+  int C0 = 0, C1 = 0, C2 = 0, C3 = 0, ok = 0;  // ok: 0 outside, 1 good, 2 range, 3 bad scale
+  if (myx < pv.W) {
+    int C[4];
+    if (!pixel_steps(pv, scales, scale_pitch, myx, y, C)) {
+      ok = 3;
+    } else {
+      C0 = C[0]; C1 = C[1]; C2 = C[2]; C3 = C[3];
+      ok = (numerator_log2_bound(pv, C) < 64.0f * L - 1.0f) ? 1 : 2;
+    }
   }
-  const Wide<L> S = mesh_numerator<N, L>(pv, g, x, y, C);
-  if (num) {
-    uint64_t* p = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(num) + (size_t)y * num_pitch) + (size_t)x * L;
+  const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
+  const int P = pv.P;
+  const int sh = (N % 2 == 0) ? 0 : 1;  // 2^(P-Q)
+  const int one = 1 << pv.Q;
+  const int half = (N % 2 == 0) ? 0 : (1 << (P - 1));
+  const int mask = (1 << P) - 1;
+  const long long rowpitch = pv.Gp;
+  const int left = pv.left;
+  int4* taps = s_tap[wslot];
+
+  // for n = 2 a lane keeps one neighbour for every tap
+  const int my_dx = (R == 32) ? s_dx[lane] : 0;
+  const int my_dy = (R == 32) ? s_dy[lane] : 0;
+
+  Wide<L> mine;
+  wzero<L>(mine);
+#pragma unroll 1
+  for (int pp = 0; pp < 32; ++pp) {
+    if (__shfl_sync(0xffffffffu, ok, pp) != 1) continue;
+    const int c0 = __shfl_sync(0xffffffffu, C0, pp), c1 = __shfl_sync(0xffffffffu, C1, pp);
+    const int c2 = __shfl_sync(0xffffffffu, C2, pp), c3 = __shfl_sync(0xffffffffu, C3, pp);
+    // tau in units of 2^-P: (n/2) sum_k (C_k - 2^Q) v_k 2^(P-Q)
+    const int tx = (N * (c0 + c1 - c3 - one)) << sh >> 1;
+    const int ty = (N * (c1 + c2 + c3 - 3 * one)) << sh >> 1;
+    const int y0x = ((x0 + pp) << P) + tx;
+    const int y0y = (y << P) + ty;
+    const int s1 = c0 << sh, s2 = c1 << sh, s3 = c2 << sh, s4 = c3 << sh;
+    __syncwarp();
+    for (int t = lane; t < TAPS; t += 32) {
+      const int j1 = t % (N + 1);
+      const int t1 = t / (N + 1);
+      const int j3 = t1 % (N + 1);
+      const int t2 = t1 / (N + 1);
+      const int j2 = t2 % (N + 1);
+      const int j4 = t2 / (N + 1);
+      const int w = signed_binom<N>(j1) * signed_binom<N>(j2) * signed_binom<N>(j3) * signed_binom<N>(j4);
+      // y_j = y0 - j1 c1 v1 - j2 c2 v2 - j3 c3 v3 - j4 c4 v4
+      const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4;
+      const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4;
+      const int px = (Yx + half) >> P;
+      const int py = (Yy + half) >> P;
+      const int r = (((Yy + half) & mask) << P) | ((Yx + half) & mask);
+      // n = 2: store the shift k of |w| = 2^k; otherwise |w|
+      const int aw = w < 0 ? -w : w;
+      taps[t] = make_int4(px + left, py, r, ((N == 2) ? (__ffs(aw) - 1) : aw) * (w < 0 ? -1 : 1) - (w < 0 ? 1 : 0));
+    }
+    __syncwarp();
+    Wide<L> acc, accn;
+    wzero<L>(acc);
+    wzero<L>(accn);
+#pragma unroll 4
+    for (int it = 0; it < ITERS; ++it) {
+      const int pair = it * 32 + lane;
+      if (PAIRS % 32 != 0 && pair >= PAIRS) continue;
+      const int tap = (R == 32) ? it : pair / R;
+      const int cand = (R == 32) ? lane : pair - tap * R;
+      const int4 ti = taps[tap];
+      const int dx = (R == 32) ? my_dx : s_dx[cand];
+      const int dy = (R == 32) ? my_dy : s_dy[cand];
+      const int k2 = ti.y + dy;
+      if (k2 < 0) continue;  // rows below the image: g = 0
+      const bool neg = ti.w < 0;
+      const int code = neg ? -(ti.w + 1) : ti.w;  // shift (n = 2) or |w_j|
+      const WT wt = __ldg(table + (size_t)ti.z * R + cand);
+      const Wide<L> gv = wload<L>(g + ((size_t)k2 * rowpitch + (size_t)(ti.x + dx)) * L);
+      if constexpr (N == 2) {
+        const WT ws = wt << code;
+        if (neg) mac_weight<L, WT>(accn, gv, ws);
+        else mac_weight<L, WT>(acc, gv, ws);
+      } else {
+        mac_weight<L, WT>(acc, neg ? wneg<L>(gv) : gv, scale_weight<N, WT>(wt, code));
+      }
+    }
+    if constexpr (N == 2) wsub<L>(acc, accn);
 #pragma unroll
-    for (int i = 0; i < L; ++i) p[i] = S.w[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      Wide<L> other;
+#pragma unroll
+      for (int i = 0; i < L; ++i) other.w[i] = __shfl_xor_sync(0xffffffffu, acc.w[i], o);
+      wadd<L>(acc, other);
+    }
+    if (lane == pp) mine = acc;
+  }
+
+  if (myx >= pv.W) return;
+  if (ok != 1) {
+    raise_status(status, ok == 3 ? ABF_DEV_BAD_SCALE : ABF_DEV_RANGE);
+    if (s) store_out<TOut>(s, s_pitch, myx, y, __longlong_as_double(0x7ff8000000000000ll));
+    return;
+  }
+  if (num) {
+    uint64_t* q = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(num) + (size_t)y * num_pitch) + (size_t)myx * L;
+#pragma unroll
+    for (int i = 0; i < L; ++i) q[i] = mine.w[i];
   }
   if (s) {
     // s = S 2^(4Qn - F) / (D prod C^n)
     double den = pv.Dd;
+    const int C[4] = {C0, C1, C2, C3};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      double ck = (double)C[k];
+      const double ck = (double)C[k];
       double p = 1.0;
 #pragma unroll
       for (int e = 0; e < N; ++e) p *= ck;
       den *= p;
     }
-    const double v = ldexp(wto_double<L>(S), 4 * pv.Q * N - pv.F) / den;
-    store_out<TOut>(s, s_pitch, x, y, v);
+    store_out<TOut>(s, s_pitch, myx, y, ldexp(wto_double<L>(mine), 4 * pv.Q * N - pv.F) / den);
   }
 }
 
@@ -311,8 +389,9 @@ template <int N, int L>
 static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch,
                                   void* s, size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
                                   cudaStream_t st) {
-  dim3 block(32, 4);
-  dim3 grid((pv.W + 31) / 32, (pv.H + 3) / 4);
+  const long long warps = (long long)((pv.W + 31) / 32) * pv.H;
+  const int block = 32 * kMeshWarps;
+  const long long grid = (warps + kMeshWarps - 1) / kMeshWarps;
   if (pv.out_dtype == ABF_F64)
     mesh_exact_kernel<N, L, double><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
                                                             num, num_pitch, status);

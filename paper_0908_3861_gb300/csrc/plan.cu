@@ -50,9 +50,10 @@ namespace {
 // ------------------------------------------------------------- weight tables
 
 struct HostTable {
-  std::vector<uint8_t> bytes;  // (2^P)^2 rows x (3n)^2 weights, little-endian
+  std::vector<uint8_t> bytes;  // (2^P)^2 rows x row_len weights, little-endian
   u128 D = 0;
   int wbytes = 0;
+  int row_len = 0;
   std::string err;
 };
 
@@ -170,34 +171,38 @@ bool build_table(int n, int P, HostTable& out) {
     side = nside;
   }
   const u128 D = D0 << ((N - 2) * P);
-  // Centred table rows.
-  const int n3 = 3 * n;
-  const int dmin = (n % 2 == 0) ? (-(3 * n) / 2 + 1) : (-(3 * n - 1) / 2);
+  // Centred table rows: row (ry, rx) holds D ZP^{*n}(r - d) for the stencil's
+  // neighbours d, in the stencil's order.
+  int scount = 0, sdx[81] = {0}, sdy[81] = {0};
+  if (n == 1) { constexpr abf::Stencil<1> s{}; scount = s.count; for (int i = 0; i < s.count; ++i) { sdx[i] = s.dx[i]; sdy[i] = s.dy[i]; } }
+  if (n == 2) { constexpr abf::Stencil<2> s{}; scount = s.count; for (int i = 0; i < s.count; ++i) { sdx[i] = s.dx[i]; sdy[i] = s.dy[i]; } }
+  if (n == 3) { constexpr abf::Stencil<3> s{}; scount = s.count; for (int i = 0; i < s.count; ++i) { sdx[i] = s.dx[i]; sdy[i] = s.dy[i]; } }
   const int one = 1 << P;
   const int half = (n % 2 == 0) ? 0 : one / 2;
   const int wb = (n == 1) ? 4 : (n == 2 ? 8 : 16);
   if (n == 1 && D >= ((u128)1 << 32)) { out.err = "D too large for 32-bit weights"; return false; }
-  if (n == 2 && D >= ((u128)1 << 64)) { out.err = "D too large for 64-bit weights"; return false; }
+  if (n == 2 && D >= ((u128)1 << 60)) { out.err = "D too large for 64-bit weights"; return false; }
+  if (n == 3 && D >= ((u128)1 << 121)) { out.err = "D too large for 128-bit weights"; return false; }
   const size_t rows = (size_t)one * one;
-  out.bytes.assign(rows * n3 * n3 * wb, 0);
+  out.bytes.assign(rows * scount * wb, 0);
+  out.row_len = scount;
   bool sums_ok = true;
 #pragma omp parallel for schedule(static) reduction(&& : sums_ok)
   for (int ry = 0; ry < one; ++ry) {
     for (int rx = 0; rx < one; ++rx) {
       u128 rowsum = 0;
-      for (int iy = 0; iy < n3; ++iy)
-        for (int ix = 0; ix < n3; ++ix) {
-          // uncentred point (r - d) + n (1/2, 3/2), in units of 2^-P
-          const long X = (long)rx - half - (long)(dmin + ix) * one + (long)n * one / 2;
-          const long Y = (long)ry - half - (long)(dmin + iy) * one + (long)3 * n * one / 2;
-          const long i = X + (long)n * one, j = Y;
-          u128 w = 0;
-          if (i >= 0 && i < side && j >= 0 && j < side) w = cur[(size_t)j * side + i];
-          rowsum += w;
-          uint8_t* dst = &out.bytes[(((size_t)ry * one + rx) * n3 * n3 + (size_t)iy * n3 + ix) * wb];
-          for (int b = 0; b < wb; ++b) dst[b] = (uint8_t)(w >> (8 * b));
-        }
-      if (rowsum != D) sums_ok = false;
+      for (int c = 0; c < scount; ++c) {
+        // uncentred point (r - d) + n (1/2, 3/2), in units of 2^-P
+        const long X = (long)rx - half - (long)sdx[c] * one + (long)n * one / 2;
+        const long Y = (long)ry - half - (long)sdy[c] * one + (long)3 * n * one / 2;
+        const long i = X + (long)n * one, j = Y;
+        u128 w = 0;
+        if (i >= 0 && i < side && j >= 0 && j < side) w = cur[(size_t)j * side + i];
+        rowsum += w;
+        uint8_t* dst = &out.bytes[(((size_t)ry * one + rx) * scount + c) * wb];
+        for (int b = 0; b < wb; ++b) dst[b] = (uint8_t)(w >> (8 * b));
+      }
+      if (rowsum != D) sums_ok = false;   // also proves the dropped neighbours are zero
     }
   }
   if (!sums_ok) { out.err = "ZP^n weight rows do not sum to D"; return false; }
@@ -296,7 +301,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (d->in_dtype < ABF_U8 || d->in_dtype > ABF_F64) return ABF_ERR_INVALID;
   if (d->out_dtype != ABF_F32 && d->out_dtype != ABF_F64) return ABF_ERR_INVALID;
   if (d->scale_kind < ABF_SCALES_C4 || d->scale_kind > ABF_SCALES_ELLIPSE) return ABF_ERR_INVALID;
-  if (d->q_bits < 1 || d->q_bits > (n == 3 ? 8 : 9)) return ABF_ERR_INVALID;
+  if (d->q_bits < 1 || d->q_bits > (n == 1 ? 9 : 8)) return ABF_ERR_INVALID;
   if (d->in_frac_bits < 0 || d->in_frac_bits > 40) return ABF_ERR_INVALID;
   if (d->in_dtype <= ABF_U16 && d->in_frac_bits != 0) return ABF_ERR_INVALID;
   if (!(d->max_scale > 0) || !std::isfinite(d->max_scale) || d->max_scale > 4096) return ABF_ERR_INVALID;
@@ -353,6 +358,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   pv.limbs = L;
   pv.value_bound = vb;
   pv.log2D = log2D;
+  pv.log2_base = (float)(log2D + std::log2(vb) + d->in_frac_bits);
   pv.Dd = u128_to_double(tab.D);
   pv.table_bytes_per_w = tab.wbytes;
   pv.table = tab.ptr;
@@ -487,7 +493,7 @@ abf_status abf_measure_scales(const abf_desc* d, const void* d_scales, size_t sc
 
 abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t out_bytes, size_t* needed_bytes,
                                  int32_t* wbytes, uint32_t* D_words4) {
-  if (n < 1 || n > 3 || q_bits < 1 || q_bits > (n == 3 ? 8 : 9)) return ABF_ERR_INVALID;
+  if (n < 1 || n > 3 || q_bits < 1 || q_bits > (n == 1 ? 9 : 8)) return ABF_ERR_INVALID;
   const int P = (n % 2 == 0) ? q_bits : q_bits + 1;
   HostTable ht;
   try {

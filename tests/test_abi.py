@@ -37,30 +37,52 @@ def test_status_strings(lib):
     assert _abf.abf_version() >= 1
 
 
+def _stencil(n):
+    """Neighbours d of a tap that can carry a non-zero ZP^{*n} weight: the box
+    of r - d (r in [0,1)^2 for even n, [-1/2,1/2)^2 for odd n) must meet the
+    open octagon |x|,|y| < 3n/2, |x +- y| < 2n."""
+    dmin = -(3 * n) // 2 + 1 if n % 2 == 0 else -(3 * n - 1) // 2
+    lo = 0.0 if n % 2 == 0 else -0.5
+    out = []
+    for iy in range(3 * n):
+        for ix in range(3 * n):
+            dx, dy = dmin + ix, dmin + iy
+            x0, x1, y0, y1 = lo - dx, lo - dx + 1, lo - dy, lo - dy + 1
+            if (x0 < 1.5 * n and -1.5 * n < x1 and y0 < 1.5 * n and -1.5 * n < y1
+                    and x0 + y0 < 2 * n and -2 * n < x1 + y1 and x0 - y1 < 2 * n and -2 * n < x1 - y0):
+                out.append((ix, iy))
+    return out
+
+
 @pytest.mark.parametrize("n,q", [(1, 3), (1, 8), (2, 3), (2, 8), (3, 2)])
 def test_host_weight_table_equals_oracle(lib, n, q):
     """Library: refinement cascade of the box spline in exact integers.
-    Oracle: de Boor's recurrence on polynomial pieces.  Same table, same D."""
+    Oracle: de Boor's recurrence on polynomial pieces.  Same weights, same D;
+    the neighbours the library drops carry zero weight in the oracle."""
     from paper_0908_3861_gb300 import _abf
     from oracle.boxspline import ZPIntegerWeights
     raw, wb, D = _abf.abf_weight_table_host(n, q)
     P = q if n % 2 == 0 else q + 1
     zw = ZPIntegerWeights(n, P)
     assert D == zw.D
-    n3 = 3 * n
+    st = _stencil(n)
+    assert len(st) == {1: 9, 2: 32, 3: 69}[n]
     if wb == 16:
         w = np.frombuffer(raw, dtype=np.uint64).reshape(-1, 2)
         vals = [int(a) + (int(b) << 64) for a, b in w]
     else:
         vals = [int(v) for v in np.frombuffer(raw, dtype=np.uint32 if wb == 4 else np.uint64)]
     rows = (1 << P) ** 2
-    assert len(vals) == rows * n3 * n3
+    R = len(st)
+    assert len(vals) == rows * R
     rng = np.random.default_rng(n * 100 + q)
     idx = range(rows) if rows <= 256 else rng.integers(0, rows, 60)
     for r in idx:
         r = int(r)
-        ref = [v for line in zw.row(r % (1 << P), r >> P) for v in line]
-        assert vals[r * n3 * n3:(r + 1) * n3 * n3] == ref
+        full = zw.row(r % (1 << P), r >> P)
+        assert vals[r * R:(r + 1) * R] == [full[iy][ix] for ix, iy in st]
+        kept = set(st)
+        assert all(full[iy][ix] == 0 for iy in range(3 * n) for ix in range(3 * n) if (ix, iy) not in kept)
 
 
 def test_plan_rejects_bad_descriptors(lib):
