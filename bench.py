@@ -213,15 +213,42 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
+    out_exact = out.clone()
+    forms = {"exact": {"value": None, "ms_per_step": round(total_ms / K, 4), "numerator": "bit-exact vs the oracle"}}
+    for form in args.compare:
+        ff = AdaptiveFilter(W, H, n, tin, scale_kind=w["scale_kind"], q_bits=w["q_bits"], frac_bits=w["frac_bits"],
+                            max_scale=w["cmax"], out="f32", form=form, device=dev)
+        o2 = torch.empty_like(out)
+        for _ in range(args.warmup):
+            ff(f_t, s_t, o2)
+        torch.cuda.synchronize()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            ff(f_t, s_t, o2)
+        c.record(stream)
+        torch.cuda.synchronize()
+        st2 = ff.device_status()
+        ms2 = a.elapsed_time(c) / K
+        forms[form] = {"value": round(H * W / (ms2 * 1e-3) / 1e6, 3), "ms_per_step": round(ms2, 4),
+                       "device_status": st2, "out": o2.cpu().numpy()}
+        ff.close()
+
     pix = float(H * W)
     value = pix * K * world / (total_ms * 1e-3) / 1e6
+    forms["exact"]["value"] = round(value, 3)
+    forms["exact"]["out"] = out_exact.cpu().numpy()
     e2e_value = pix * K * world / (e2e_ms * 1e-3) / 1e6
     peaks = _peaks()
     L = filt.limbs
     macs = _algorithmic_macs(n) * pix
-    # peak: 152 SMs x 64 INT32 multiply lanes / clock x clock, divided by the
-    # 32-bit multiplies one L-limb x 64-bit MAC needs.
-    imad_per_mac = {1: 3, 2: 7, 3: 11, 4: 15}[L] * (2 if n == 3 else 1)
+    # peak (derived): 152 SMs x 64 INT32 multiply-add lanes / clock x SM clock,
+    # divided by the 32-bit multiply-adds one MAC needs (the partial products of
+    # a 2L-word g and a k-word weight that land below bit 64 L, low and high
+    # halves counted separately).
+    wwords = {1: 1, 2: 2, 3: 4}[n]
+    imad_per_mac = (sum(1 for i in range(2 * L) for j in range(wwords) if i + j <= 2 * L - 1)
+                    + sum(1 for i in range(2 * L) for j in range(wwords) if i + j <= 2 * L - 2))
     clk = clk.summary()
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     peak_macs = 152 * 64 * sm_mhz * 1e6 / imad_per_mac
@@ -241,15 +268,23 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(o_h.numel() * 4)},
         "gpu_launches": int(K * (1 + 3 * n + 1)),
         "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_macs / 1e12,
-                     "unit": "T MAC/s (%d-limb integer)" % L, "frac": achieved / peak_macs,
-                     "traffic": None, "kernel": "mesh_exact_kernel",
-                     "peak_note": "derived: 152 SM x 64 INT32 mul lanes x median SM clock / %d 32-bit "
-                                  "multiplies per MAC" % imad_per_mac},
+        "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak_macs / 1e9, 2),
+                     "unit": "G MAC/s (%d-limb integer x %d-bit weight)" % (L, 32 * wwords),
+                     "frac": round(achieved / peak_macs, 4), "traffic": None, "kernel": "mesh_exact_kernel",
+                     "peak_note": "derived: 152 SM x 64 INT32 multiply-add lanes x median SM clock / %d "
+                                  "32-bit multiply-adds per MAC; achieved = (n+1)^4 x 7n^2 stencil MACs per pixel"
+                                  % imad_per_mac},
         "clocks": clk,
     }
     if rank == 0 and args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, seconds=args.cpu_seconds)
+        cb, pts, vals = cpu_baseline(w, seconds=args.cpu_seconds, keep=True)
+        line["cpu_baseline"] = cb
+        for k, v in forms.items():
+            v["err_range_vs_oracle"] = err_range(v["out"], pts, vals, img)
+            v["err_sample"] = "%d sampled pixels" % len(pts)
+    for v in forms.values():
+        v.pop("out", None)
+    line["forms"] = forms
     if rank == 0:
         print(json.dumps(line), flush=True)
     filt.close()
@@ -257,7 +292,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(w, seconds=15.0, sample=None):
+def cpu_baseline(w, seconds=15.0, sample=None, keep=False):
     """The oracle (exact, per-pixel windows) on a bounded sample of the workload."""
     from oracle import paper, scales as osc
     img, sc = w["image"], w["scales"]
@@ -266,15 +301,27 @@ def cpu_baseline(w, seconds=15.0, sample=None):
     rng = np.random.default_rng(7)
     C = osc.scales_to_C(w["scale_kind"], sc, w["n"], w["q_bits"], w["cmax"])
     done, t0 = 0, time.perf_counter()
-    pts = []
+    pts, vals = [], []
     while time.perf_counter() - t0 < seconds and (sample is None or done < sample):
         p = (int(rng.integers(0, W)), int(rng.integers(0, H)))
-        paper.filter_pixels(fi, C, w["n"], w["q_bits"], w["frac_bits"], [p])
+        _, sv = paper.filter_pixels(fi, C, w["n"], w["q_bits"], w["frac_bits"], [p])
         pts.append(p)
+        vals.append(float(sv[0]))
         done += 1
     el = time.perf_counter() - t0
-    return {"value": done / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d random pixels of the same workload, exact per-pixel evaluation, %.1f s" % (done, el)}
+    out = {"value": done / el / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d random pixels of the same workload, exact per-pixel evaluation, %.1f s" % (done, el)}
+    if keep:
+        return out, pts, vals
+    return out
+
+
+def err_range(out, pts, vals, img):
+    """max |s - s_oracle| / (max f - min f) over the sampled pixels."""
+    if not pts:
+        return None
+    rng = float(img.max()) - float(img.min())
+    return max(abs(float(out[y, x]) - v) for (x, y), v in zip(pts, vals)) / rng
 
 
 def run_reference(args):
@@ -314,7 +361,10 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--compare", default="plain_f64",
+                    help="comma-separated forms timed beside the exact form ('' for none)")
     args = ap.parse_args()
+    args.compare = [c for c in args.compare.split(",") if c]
     if args.impl == "reference":
         run_reference(args)
     else:

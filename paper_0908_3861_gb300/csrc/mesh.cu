@@ -24,78 +24,6 @@
 
 namespace abf {
 
-constexpr double kInvSqrt2 = 0.7071067811865476;
-
-// Lattice steps from one pixel's scale record; returns false on invalid input.
-__device__ __forceinline__ bool read_steps(int kind, float4 sc, int n, double cmax, double c[4]) {
-  const double a0 = sc.x, a1 = sc.y, a2 = sc.z, a3 = sc.w;
-  if (kind == ABF_SCALES_C4) {
-    c[0] = a0; c[1] = a1; c[2] = a2; c[3] = a3;
-  } else if (kind == ABF_SCALES_A4) {
-    c[0] = a0;
-    c[1] = __dmul_rn(a1, kInvSqrt2);
-    c[2] = a2;
-    c[3] = __dmul_rn(a3, kInvSqrt2);
-  } else {
-    // Ellipse (sigma, elongation, cos t, sin t) -> covariance -> moment rule.
-    const double sigma = a0, elong = a1, ct = a2, st = a3;
-    if (!(sigma > 0.0) || !(elong > 0.0) || !isfinite(sigma) || !isfinite(elong) || !isfinite(ct) ||
-        !isfinite(st))
-      return false;
-    const double s2 = __dmul_rn(sigma, sigma);
-    const double ev1 = __dmul_rn(s2, elong);
-    const double ev2 = __ddiv_rn(s2, elong);
-    const double cc = __dmul_rn(ct, ct);
-    const double ss = __dmul_rn(st, st);
-    const double cs = __dmul_rn(ct, st);
-    const double c11 = __dadd_rn(__dmul_rn(ev1, cc), __dmul_rn(ev2, ss));
-    const double c22 = __dadd_rn(__dmul_rn(ev1, ss), __dmul_rn(ev2, cc));
-    const double c12 = __dmul_rn(__dsub_rn(ev1, ev2), cs);
-    const double a12 = fabs(c12);
-    const double mn = c11 < c22 ? c11 : c22;
-    const double t = (a12 <= mn) ? __dmul_rn(0.25, __dadd_rn(a12, mn)) : __dmul_rn(0.5, mn);
-    const double h = __dmul_rn(0.5, c12);
-    double u[4];
-    u[0] = __dsub_rn(c11, __dmul_rn(2.0, t));
-    u[1] = __dadd_rn(t, h);
-    u[2] = __dsub_rn(c22, __dmul_rn(2.0, t));
-    u[3] = __dsub_rn(t, h);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double uk = u[k] < 0.0 ? 0.0 : u[k];
-      double ck = __dsqrt_rn(__ddiv_rn(__dmul_rn(12.0, uk), (double)n));
-      if (ck < 1.0) ck = 1.0;
-      if (ck > cmax) ck = cmax;
-      c[k] = ck;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (!isfinite(c[k]) || !(c[k] > 0.0)) return false;
-  return true;
-}
-
-// C_k = rint(c_k 2^Q), validated against the plan's bounds.
-__device__ __forceinline__ bool pixel_steps(const PlanView& pv, const float4* scales, size_t scale_pitch,
-                                            int x, int y, int C[4]) {
-  const float4 sc = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(scales) +
-                                                     (size_t)y * scale_pitch + (size_t)x * sizeof(float4));
-  double c[4];
-  const double cmax = ldexp((double)pv.Cmax, -pv.Q);
-  if (!read_steps(pv.scale_kind, sc, pv.n, cmax, c)) return false;
-  const double q = ldexp(1.0, pv.Q);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double v = c[k] * q;  // exact (power of two)
-    if (!(v <= (double)pv.Cmax)) return false;
-    const long long r = __double2ll_rn(v);
-    if (r < 1) return false;
-    C[k] = (int)r;
-  }
-  if (C[0] < pv.Cmin || C[2] < pv.Cmin) return false;
-  return true;
-}
-
 // log2 of the numerator bound for this pixel (see file header), in binary32
 // with a margin that covers its rounding (the check only has to be safe).
 __device__ __forceinline__ float numerator_log2_bound(const PlanView& pv, const int C[4]) {

@@ -39,6 +39,11 @@ cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t sc
 cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t scale_pitch,
                                unsigned long long* out2, int32_t* status, cudaStream_t st);
 size_t noalloc_scratch_bytes();
+size_t tile_ws_bytes(const PlanView& pv, int real_bytes, int* slots_out, size_t* slot_elems_out, size_t* off_bmax,
+                     size_t* off_tiles, size_t* off_cnt, size_t* off_scratch);
+cudaError_t run_tiles(const PlanView& pv, bool f64, const void* f, size_t f_pitch, const void* scales,
+                      size_t scale_pitch, void* s, size_t s_pitch, void* ws, const void* wtab, int32_t* status,
+                      cudaStream_t st);
 cudaError_t run_integrate_noalloc(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, uint32_t* epoch,
                                   int32_t* status, cudaStream_t st);
 }  // namespace abf
@@ -260,6 +265,47 @@ uint32_t reserve_epochs(uint32_t count) {
   }
 }
 
+// Floating-point copies of a weight table (D ZP^{*n} / D, rounded once), for
+// the tile forms; same row layout as the integer table.
+std::map<std::tuple<int, int, int, int>, void*> g_real_tables;  // (device, n, P, bytes); held until exit
+
+double u128_to_double(u128 v);
+
+abf_status get_real_table(int device, int n, int P, int real_bytes, void** out) {
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  auto key = std::make_tuple(device, n, P, real_bytes);
+  auto it = g_real_tables.find(key);
+  if (it != g_real_tables.end()) {
+    *out = it->second;
+    return ABF_OK;
+  }
+  HostTable ht;
+  try {
+    if (!build_table(n, P, ht)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  const size_t count = ht.bytes.size() / ht.wbytes;
+  std::vector<uint8_t> buf(count * real_bytes);
+  const double D = u128_to_double(ht.D);
+  for (size_t i = 0; i < count; ++i) {
+    u128 w = 0;
+    for (int b = 0; b < ht.wbytes; ++b) w |= (u128)ht.bytes[i * ht.wbytes + b] << (8 * b);
+    const double v = u128_to_double(w) / D;
+    if (real_bytes == 8) std::memcpy(&buf[i * 8], &v, 8);
+    else { const float fv = (float)v; std::memcpy(&buf[i * 4], &fv, 4); }
+  }
+  void* d = nullptr;
+  if (cudaMalloc(&d, buf.size()) != cudaSuccess) return ABF_ERR_OOM;
+  if (cudaMemcpy(d, buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return ABF_ERR_CUDA;
+  }
+  g_real_tables[key] = d;
+  *out = d;
+  return ABF_OK;
+}
+
 double u128_to_double(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073709551616.0 + (double)(uint64_t)v; }
 
 }  // namespace
@@ -269,6 +315,7 @@ double u128_to_double(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073
 struct abf_plan_s {
   abf_desc desc;
   abf::PlanView pv;
+  void* real_table = nullptr;  // tile forms
   u128 D;
   int device;
   int32_t* d_status = nullptr;
@@ -305,7 +352,8 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (d->in_frac_bits < 0 || d->in_frac_bits > 40) return ABF_ERR_INVALID;
   if (d->in_dtype <= ABF_U16 && d->in_frac_bits != 0) return ABF_ERR_INVALID;
   if (!(d->max_scale > 0) || !std::isfinite(d->max_scale) || d->max_scale > 4096) return ABF_ERR_INVALID;
-  if (d->form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  if (d->form < ABF_FORM_EXACT || d->form > ABF_FORM_TILE_F32) return ABF_ERR_INVALID;
+  const bool exact = d->form == ABF_FORM_EXACT;
   const int Q = d->q_bits;
   const int P = (n % 2 == 0) ? Q : Q + 1;
   const double qd = std::ldexp(1.0, Q);
@@ -318,7 +366,8 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (!(vb > 0)) {
     if (d->in_dtype == ABF_U8) vb = 255.0;
     else if (d->in_dtype == ABF_U16) vb = 65535.0;
-    else return ABF_ERR_INVALID;
+    else if (exact) return ABF_ERR_INVALID;
+    else vb = 1.0;
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
@@ -339,7 +388,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   const double log2D = std::log2(u128_to_double(tab.D));
   const double lb = log2D + n * std::log2(prod) + std::log2(vb) + d->in_frac_bits +
                     2.0 * std::log2(1.0 + 1.0 / cmin) + 1e-6;
-  const int L = (int)std::floor((lb + 1.0) / 64.0) + 1;
+  const int L = exact ? (int)std::floor((lb + 1.0) / 64.0) + 1 : 1;
   if (L > abf::kMaxLimbs) { delete p; return ABF_ERR_RANGE; }
 
   // Lattice box: reads of a pixel span [m1 - E - 2n, m1 + E + n] x [m2 - E - 3n, m2 + E],
@@ -362,8 +411,18 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   pv.Dd = u128_to_double(tab.D);
   pv.table_bytes_per_w = tab.wbytes;
   pv.table = tab.ptr;
-  p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
-  p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, nullptr, nullptr);
+  if (exact) {
+    p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
+    p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, nullptr, nullptr);
+  } else {
+    const int rb = d->form == ABF_FORM_PLAIN_F64 ? 8 : 4;
+    abf_status rs = get_real_table(dev, n, P, rb, &p->real_table);
+    if (rs != ABF_OK) { delete p; return rs; }
+    int slots;
+    size_t se, o1, o2, o3, o4;
+    p->g_bytes = 0;
+    p->ws_bytes = abf::tile_ws_bytes(pv, rb, &slots, &se, &o1, &o2, &o3, &o4);
+  }
   if (cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) { delete p; return ABF_ERR_OOM; }
   if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
     cudaFree(p->d_status);
@@ -407,6 +466,7 @@ static abf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ABF_OK 
 
 abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, void* d_ws, cudaStream_t st) {
   if (!p || !d_f || !d_g || !d_ws) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
   const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
   if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
   if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
@@ -416,6 +476,7 @@ abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g,
 
 abf_status abf_integrate_noalloc(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t st) {
   if (!p || !d_f || !d_g) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
   const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
   if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
   if ((uintptr_t)d_g & 15) return ABF_ERR_INVALID;
@@ -429,12 +490,16 @@ abf_status abf_integrate_noalloc(abf_plan p, const void* d_f, size_t f_pitch, vo
 
 abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const void* d_scales, size_t scale_pitch,
                       void* d_s, size_t s_pitch, void* d_ws, cudaStream_t st) {
-  (void)src_pitch;
-  (void)d_ws;
   if (!p || !d_src || !d_scales || !d_s) return ABF_ERR_INVALID;
   const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
   if (scale_pitch < (size_t)p->pv.W * 16 || s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) {
+    const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
+    if (!d_ws || src_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
+    return cuda_status(abf::run_tiles(p->pv, p->desc.form == ABF_FORM_PLAIN_F64, d_src, src_pitch, d_scales,
+                                      scale_pitch, d_s, s_pitch, d_ws, p->real_table, p->d_status, st));
+  }
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_src, d_scales, scale_pitch, d_s, s_pitch,
                                          nullptr, 0, p->d_status, st));
 }
@@ -443,6 +508,7 @@ abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scale
                                 size_t num_pitch, void* d_ws, cudaStream_t st) {
   (void)d_ws;
   if (!p || !d_g || !d_scales || !d_num) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
   if (scale_pitch < (size_t)p->pv.W * 16 || num_pitch < (size_t)p->pv.W * 8 * p->pv.limbs) return ABF_ERR_INVALID;
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, nullptr, 0,

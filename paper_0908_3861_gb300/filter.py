@@ -59,19 +59,32 @@ class AdaptiveFilter:
         assert sc.is_cuda and sc.dtype == torch.float32 and sc.shape == (self.H, self.W, 4) and sc.is_contiguous()
         return self.W * 16
 
+    @property
+    def exact(self):
+        return self.desc.form == C.ABF_FORM_EXACT
+
     def integrate(self, f, stream=None):
+        """Exact form: the non-adaptive step into the plan's integrated image."""
         C.abf_integrate(self.plan, f, self._check_f(f), self.g, self.ws, stream)
 
-    def filter(self, scales, out=None, stream=None):
+    def filter(self, scales, out=None, stream=None, f=None):
+        """Adaptive step.  Exact form: from the integrated image; tile forms:
+        from the image f (the running sums are restarted per tile)."""
         sp = self._check_scales(scales)
         if out is None:
             out = torch.empty((self.H, self.W), dtype=self.out_dtype, device=self.device)
-        C.abf_filter(self.plan, self.g, 0, scales, sp, out, self.W * out.element_size(), self.ws, stream)
+        if self.exact:
+            C.abf_filter(self.plan, self.g, 0, scales, sp, out, self.W * out.element_size(), self.ws, stream)
+        else:
+            C.abf_filter(self.plan, f, self._check_f(f), scales, sp, out, self.W * out.element_size(), self.ws,
+                         stream)
         return out
 
     def __call__(self, f, scales, out=None, stream=None):
-        self.integrate(f, stream)
-        return self.filter(scales, out, stream)
+        if self.exact:
+            self.integrate(f, stream)
+            return self.filter(scales, out, stream)
+        return self.filter(scales, out, stream, f=f)
 
     def numerators(self, scales, stream=None):
         sp = self._check_scales(scales)
