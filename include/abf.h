@@ -173,6 +173,32 @@ abf_status abf_filter_numerator(abf_plan plan, const void* d_g, const void* d_sc
                                 size_t scale_pitch, void* d_num, size_t num_pitch, void* d_ws,
                                 cudaStream_t stream);
 
+/* One image of a batch: its (exact-form) plan, its integrated image from
+ * abf_integrate, its scale field and its output (as for abf_filter).        */
+typedef struct {
+  abf_plan plan;
+  const void* d_g;
+  const void* d_scales;
+  size_t scale_pitch;
+  void* d_s;
+  size_t s_pitch;
+} abf_job;
+
+/* Adaptive step (Eq. (final_eqn)) for many images of uneven size, order and
+ * limb count in ONE persistent launch: the images' 32-pixel runs are numbered
+ * (most expensive images first) and every warp takes the next run from a
+ * device counter, so the work stays balanced across SMs.  Each image's
+ * result is bit-identical to abf_filter on that image alone.
+ *   jobs  : njobs entries (host memory, read during the call), every plan of
+ *           the exact form; up to abf_batch_max_jobs() per call (larger
+ *           batches are split into several launches).
+ *   d_ws  : device workspace of at least 256 bytes (the work counter); two
+ *           calls that overlap on the GPU must not share it.
+ * Device errors go to each job's plan status word.                           */
+abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes,
+                            cudaStream_t stream);
+int32_t abf_batch_max_jobs(void);
+
 /* The per-pixel integer steps C_k = rint(c_k 2^Q) (int32 x4 per pixel) that
  * abf_filter uses, for inspection and reuse.                                 */
 abf_status abf_prepare_scales(abf_plan plan, const void* d_scales, size_t scale_pitch,

@@ -9,11 +9,11 @@ ABI of include/abf.h (libabf.so).  ``_abf`` binds that ABI one to one;
 from . import _abf
 from ._abf import AbfError
 
-__all__ = ["_abf", "AbfError", "AdaptiveFilter"]
+__all__ = ["_abf", "AbfError", "AdaptiveFilter", "Batch"]
 
 
 def __getattr__(name):
-    if name == "AdaptiveFilter":
-        from .filter import AdaptiveFilter
-        return AdaptiveFilter
+    if name in ("AdaptiveFilter", "Batch"):
+        from . import filter as _f
+        return getattr(_f, name)
     raise AttributeError(name)

@@ -29,6 +29,11 @@ class AbfError(RuntimeError):
         super().__init__("%s: %s" % (where, STATUS_NAMES.get(status, status)))
 
 
+class abf_job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_g", ctypes.c_void_p), ("d_scales", ctypes.c_void_p),
+                ("scale_pitch", ctypes.c_size_t), ("d_s", ctypes.c_void_p), ("s_pitch", ctypes.c_size_t)]
+
+
 class abf_desc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("order_n", ctypes.c_int32),
                 ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32), ("form", ctypes.c_int32),
@@ -64,6 +69,8 @@ def lib():
         "abf_last_device_status": ([vp, P(i32)], st),
         "abf_measure_scales": ([P(abf_desc), vp, sz, P(ctypes.c_double), P(ctypes.c_double), vp], st),
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
+        "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
+        "abf_batch_max_jobs": ([], i32),
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
@@ -170,6 +177,17 @@ def abf_weight_table_host(n, q_bits):
     buf = ctypes.create_string_buffer(need.value)
     _check(lib().abf_weight_table_host(n, q_bits, buf, need.value, None, None, None), "abf_weight_table_host")
     return buf.raw, wb.value, sum(int(d[i]) << (32 * i) for i in range(4))
+
+
+def abf_filter_batch(jobs, ws, stream=None):
+    """jobs: list of abf_job structures."""
+    arr = (abf_job * len(jobs))(*jobs)
+    _check(lib().abf_filter_batch(arr, len(jobs), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "abf_filter_batch")
+
+
+def abf_batch_max_jobs():
+    return lib().abf_batch_max_jobs()
 
 
 def abf_status_str(s):

@@ -97,38 +97,36 @@ __device__ __forceinline__ void store_out(void* s, size_t s_pitch, int x, int y,
 // w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
 // numerator, which lane i keeps for its own pixel and stores at the end.
 constexpr int kMeshWarps = 8;
+constexpr int kMaxTaps = 256;  // (n+1)^4 for n = 3
 
-template <int N, int L, typename TOut>
-__global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
-    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
-    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+// The stencil's neighbours, in the same order as the table rows (one thread).
+template <int N>
+__device__ __forceinline__ void fill_stencil(int* s_dx, int* s_dy) {
+  int c = 0;
+  for (int iy = 0; iy < 3 * N; ++iy)
+    for (int ix = 0; ix < 3 * N; ++ix)
+      if (stencil_keeps<N>(ix, iy)) {
+        s_dx[c] = Stencil<N>::kDmin + ix;
+        s_dy[c] = Stencil<N>::kDmin + iy;
+        ++c;
+      }
+}
+
+// Mesh for the run of 32 pixels (x0 .. x0+31, y) of one image; the whole warp
+// calls it.  taps: this warp's (n+1)^4-entry shared tap table; s_dx/s_dy: the
+// order-n stencil in shared memory.
+template <int N, int L>
+__device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __restrict__ g,
+                                         const float4* __restrict__ scales, size_t scale_pitch, void* __restrict__ s,
+                                         size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch,
+                                         int32_t* status, int y, int x0, int4* taps, const int* s_dx,
+                                         const int* s_dy) {
   using WT = typename WeightT<N>::T;
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   constexpr int PAIRS = TAPS * R;
   constexpr int ITERS = (PAIRS + 31) / 32;
-  __shared__ int s_dx[R], s_dy[R];
-  __shared__ int4 s_tap[kMeshWarps][TAPS];
-  if (threadIdx.x == 0) {
-    // the stencil's neighbours, in the same order as the table rows
-    int c = 0;
-    for (int iy = 0; iy < 3 * N; ++iy)
-      for (int ix = 0; ix < 3 * N; ++ix)
-        if (stencil_keeps<N>(ix, iy)) {
-          s_dx[c] = Stencil<N>::kDmin + ix;
-          s_dy[c] = Stencil<N>::kDmin + iy;
-          ++c;
-        }
-  }
-  __syncthreads();
-
   const int lane = threadIdx.x & 31;
-  const int wslot = threadIdx.x >> 5;
-  const int segs = (pv.W + 31) >> 5;
-  const int wid = blockIdx.x * kMeshWarps + wslot;
-  if (wid >= segs * pv.H) return;
-  const int y = wid / segs;
-  const int x0 = (wid - y * segs) * 32;
   const int myx = x0 + lane;
 
   // a5: this lane's pixel -> integer steps, validity, numerator bound
@@ -150,7 +148,6 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   const int mask = (1 << P) - 1;
   const long long rowpitch = pv.Gp;
   const int left = pv.left;
-  int4* taps = s_tap[wslot];
 
   // for n = 2 a lane keeps one neighbour for every tap
   const int my_dx = (R == 32) ? s_dx[lane] : 0;
@@ -227,9 +224,14 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   }
 
   if (myx >= pv.W) return;
+  const bool f64 = pv.out_dtype == ABF_F64;
   if (ok != 1) {
     raise_status(status, ok == 3 ? ABF_DEV_BAD_SCALE : ABF_DEV_RANGE);
-    if (s) store_out<TOut>(s, s_pitch, myx, y, __longlong_as_double(0x7ff8000000000000ll));
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (s) {
+      if (f64) store_out<double>(s, s_pitch, myx, y, nan);
+      else store_out<float>(s, s_pitch, myx, y, nan);
+    }
     return;
   }
   if (num) {
@@ -249,7 +251,117 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
       for (int e = 0; e < N; ++e) p *= ck;
       den *= p;
     }
-    store_out<TOut>(s, s_pitch, myx, y, ldexp(wto_double<L>(mine), 4 * pv.Q * N - pv.F) / den);
+    const double v = ldexp(wto_double<L>(mine), 4 * pv.Q * N - pv.F) / den;
+    if (f64) store_out<double>(s, s_pitch, myx, y, v);
+    else store_out<float>(s, s_pitch, myx, y, v);
+  }
+}
+
+// One warp per run of 32 pixels of a row.  Lane i reads the scales of pixel
+// x0 + i and rounds them to integer steps; then the warp walks the 32 pixels
+// one at a time.  For a pixel, the lanes first tabulate its (n+1)^4 taps
+// (lattice point p_j, table row r_j, FD weight w_j) in shared memory; then the
+// (tap, neighbour) pairs -- (n+1)^4 taps times the stencil's neighbours -- are
+// dealt to the lanes in order, so the lanes of one tap read one contiguous
+// table row and one compact patch of g.  For n = 2 the 32 neighbours are
+// exactly the 32 lanes: every lane keeps its neighbour, the tap is the same
+// for the whole warp, and w_j = +-2^k folds into the table weight as a shift
+// with the sign choosing one of two accumulators.  Each lane accumulates
+// w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
+// numerator, which lane i keeps for its own pixel and stores at the end.
+template <int N, int L>
+__global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  constexpr int R = stencil_count<N>();
+  constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
+  __shared__ int s_dx[R], s_dy[R];
+  __shared__ int4 s_tap[kMeshWarps][TAPS];
+  if (threadIdx.x == 0) fill_stencil<N>(s_dx, s_dy);
+  __syncthreads();
+  const int segs = (pv.W + 31) >> 5;
+  const int wid = blockIdx.x * kMeshWarps + (threadIdx.x >> 5);
+  if (wid >= segs * pv.H) return;
+  const int y = wid / segs;
+  const int x0 = (wid - y * segs) * 32;
+  mesh_run<N, L>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0, s_tap[threadIdx.x >> 5],
+                 s_dx, s_dy);
+}
+
+// ------------------------------------------------------------------- batches
+// Many images (each its own plan: size, order n, limbs) in one persistent
+// launch.  The images' 32-pixel runs are numbered consecutively, the most
+// expensive images first; every warp repeatedly takes the next run from a
+// global counter and filters it with its image's plan, so images of uneven
+// size and order share the GPU without a tail of idle SMs.
+constexpr int kMaxBatch = 96;
+
+struct BatchJob {
+  PlanView pv;
+  const uint64_t* g;
+  const float4* scales;
+  size_t scale_pitch;
+  void* s;
+  size_t s_pitch;
+  int32_t* status;
+  long long runs_begin;  // first global run index of this image
+  int segs;              // runs per row
+};
+
+struct BatchJobs {
+  int njobs;
+  long long total_runs;
+  BatchJob job[kMaxBatch];
+};
+
+template <int N, int L>
+__device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int x0, int4* taps, const int* sdx,
+                                                 const int* sdy) {
+  mesh_run<N, L>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0, taps, sdx,
+                 sdy);
+}
+
+__global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
+                                                                     unsigned long long* counter) {
+  __shared__ int s_dx1[9], s_dy1[9], s_dx2[32], s_dy2[32], s_dx3[69], s_dy3[69];
+  __shared__ int4 s_tap[kMeshWarps][kMaxTaps];
+  if (threadIdx.x == 0) {
+    fill_stencil<1>(s_dx1, s_dy1);
+    fill_stencil<2>(s_dx2, s_dy2);
+    fill_stencil<3>(s_dx3, s_dy3);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  int4* taps = s_tap[threadIdx.x >> 5];
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if ((long long)item >= jobs.total_runs) break;
+    int lo = 0, hi = jobs.njobs - 1;  // last job with runs_begin <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs.job[mid].runs_begin <= (long long)item) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchJob& jb = jobs.job[lo];
+    const long long r = (long long)item - jb.runs_begin;
+    const int y = (int)(r / jb.segs);
+    const int x0 = (int)(r - (long long)y * jb.segs) * 32;
+    switch (jb.pv.n * 8 + jb.pv.limbs) {
+      case 9: batch_dispatch_L<1, 1>(jb, y, x0, taps, s_dx1, s_dy1); break;
+      case 10: batch_dispatch_L<1, 2>(jb, y, x0, taps, s_dx1, s_dy1); break;
+      case 11: batch_dispatch_L<1, 3>(jb, y, x0, taps, s_dx1, s_dy1); break;
+      case 12: batch_dispatch_L<1, 4>(jb, y, x0, taps, s_dx1, s_dy1); break;
+      case 17: batch_dispatch_L<2, 1>(jb, y, x0, taps, s_dx2, s_dy2); break;
+      case 18: batch_dispatch_L<2, 2>(jb, y, x0, taps, s_dx2, s_dy2); break;
+      case 19: batch_dispatch_L<2, 3>(jb, y, x0, taps, s_dx2, s_dy2); break;
+      case 20: batch_dispatch_L<2, 4>(jb, y, x0, taps, s_dx2, s_dy2); break;
+      case 25: batch_dispatch_L<3, 1>(jb, y, x0, taps, s_dx3, s_dy3); break;
+      case 26: batch_dispatch_L<3, 2>(jb, y, x0, taps, s_dx3, s_dy3); break;
+      case 27: batch_dispatch_L<3, 3>(jb, y, x0, taps, s_dx3, s_dy3); break;
+      default: batch_dispatch_L<3, 4>(jb, y, x0, taps, s_dx3, s_dy3); break;
+    }
   }
 }
 
@@ -320,12 +432,8 @@ static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const v
   const long long warps = (long long)((pv.W + 31) / 32) * pv.H;
   const int block = 32 * kMeshWarps;
   const long long grid = (warps + kMeshWarps - 1) / kMeshWarps;
-  if (pv.out_dtype == ABF_F64)
-    mesh_exact_kernel<N, L, double><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
-                                                            num, num_pitch, status);
-  else
-    mesh_exact_kernel<N, L, float><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
-                                                           num, num_pitch, status);
+  mesh_exact_kernel<N, L><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch, num,
+                                                  num_pitch, status);
   return cudaGetLastError();
 }
 
@@ -348,6 +456,62 @@ cudaError_t run_mesh_exact(const PlanView& pv, const uint64_t* g, const void* sc
     case 2: return launch_mesh_N<2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
     default: return launch_mesh_N<3>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
   }
+}
+
+// Host side of the batched launch: order the images by cost (order n, then
+// pixels), number their runs, and launch persistent CTAs over them.
+struct BatchIn {
+  PlanView pv;
+  const uint64_t* g;
+  const void* scales;
+  size_t scale_pitch;
+  void* s;
+  size_t s_pitch;
+  int32_t* status;
+};
+
+int batch_max_jobs() { return kMaxBatch; }
+
+cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st) {
+  BatchJobs jobs;
+  jobs.njobs = njobs;
+  int order[kMaxBatch];
+  for (int i = 0; i < njobs; ++i) order[i] = i;
+  auto cost = [&](int i) {
+    const double macs = (double)((in[i].pv.n + 1) * (in[i].pv.n + 1)) * (in[i].pv.n + 1) * (in[i].pv.n + 1);
+    return macs * in[i].pv.limbs * (double)in[i].pv.W * in[i].pv.H;
+  };
+  for (int i = 1; i < njobs; ++i)
+    for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) {
+      const int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  long long runs = 0;
+  for (int k = 0; k < njobs; ++k) {
+    const BatchIn& b = in[order[k]];
+    BatchJob& jb = jobs.job[k];
+    jb.pv = b.pv;
+    jb.g = b.g;
+    jb.scales = (const float4*)b.scales;
+    jb.scale_pitch = b.scale_pitch;
+    jb.s = b.s;
+    jb.s_pitch = b.s_pitch;
+    jb.status = b.status;
+    jb.segs = (b.pv.W + 31) / 32;
+    jb.runs_begin = runs;
+    runs += (long long)jb.segs * b.pv.H;
+  }
+  jobs.total_runs = runs;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel, 32 * kMeshWarps, 0);
+  if (per_sm < 1) per_sm = 1;
+  mesh_batch_kernel<<<sms * per_sm, 32 * kMeshWarps, 0, st>>>(jobs, counter);
+  return cudaGetLastError();
 }
 
 cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t scale_pitch, void* C, size_t C_pitch,

@@ -39,6 +39,17 @@ cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t sc
 cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t scale_pitch,
                                unsigned long long* out2, int32_t* status, cudaStream_t st);
 size_t noalloc_scratch_bytes();
+struct BatchIn {
+  PlanView pv;
+  const uint64_t* g;
+  const void* scales;
+  size_t scale_pitch;
+  void* s;
+  size_t s_pitch;
+  int32_t* status;
+};
+int batch_max_jobs();
+cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st);
 size_t tile_ws_bytes(const PlanView& pv, int real_bytes, int* slots_out, size_t* slot_elems_out, size_t* off_bmax,
                      size_t* off_tiles, size_t* off_cnt, size_t* off_scratch);
 cudaError_t run_tiles(const PlanView& pv, bool f64, const void* f, size_t f_pitch, const void* scales,
@@ -513,6 +524,31 @@ abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scale
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, nullptr, 0,
                                          (uint64_t*)d_num, num_pitch, p->d_status, st));
+}
+
+int32_t abf_batch_max_jobs(void) { return abf::batch_max_jobs(); }
+
+abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t st) {
+  if (!jobs || njobs < 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  if (njobs == 0) return ABF_OK;
+  std::vector<abf::BatchIn> in((size_t)njobs);
+  for (int i = 0; i < njobs; ++i) {
+    const abf_job& j = jobs[i];
+    abf_plan p = j.plan;
+    if (!p || !j.d_g || !j.d_scales || !j.d_s) return ABF_ERR_INVALID;
+    if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+    const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
+    if (j.scale_pitch < (size_t)p->pv.W * 16 || j.s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
+    if (((uintptr_t)j.d_scales & 15) || (j.scale_pitch & 15)) return ABF_ERR_INVALID;
+    in[i] = abf::BatchIn{p->pv, (const uint64_t*)j.d_g, j.d_scales, j.scale_pitch, j.d_s, j.s_pitch, p->d_status};
+  }
+  const int chunk = abf::batch_max_jobs();
+  for (int b = 0; b < njobs; b += chunk) {
+    const int k = std::min(chunk, njobs - b);
+    cudaError_t e = abf::run_mesh_batch(in.data() + b, k, (unsigned long long*)d_ws, st);
+    if (e != cudaSuccess) return ABF_ERR_CUDA;
+  }
+  return ABF_OK;
 }
 
 abf_status abf_prepare_scales(abf_plan p, const void* d_scales, size_t scale_pitch, void* d_C, size_t C_pitch,

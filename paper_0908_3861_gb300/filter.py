@@ -109,3 +109,24 @@ class AdaptiveFilter:
 
     def device_status(self):
         return C.abf_last_device_status(self.plan)
+
+
+class Batch:
+    """Many exact-form filters run as one batch: each image's non-adaptive
+    step (abf_integrate), then one persistent launch of the adaptive step
+    over all images (abf_filter_batch)."""
+
+    def __init__(self, filters, device=None):
+        self.filters = list(filters)
+        self.device = torch.device(device or "cuda")
+        self.ws = torch.zeros(256, dtype=torch.uint8, device=self.device)
+
+    def __call__(self, images, scales, outs, stream=None):
+        jobs = []
+        for flt, f, sc, o in zip(self.filters, images, scales, outs):
+            flt.integrate(f, stream)
+            flt._check_scales(sc)
+            jobs.append(C.abf_job(flt.plan.value, flt.g.data_ptr(), sc.data_ptr(), flt.W * 16, o.data_ptr(),
+                                  flt.W * o.element_size()))
+        C.abf_filter_batch(jobs, self.ws, stream)
+        return outs
