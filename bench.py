@@ -365,6 +365,96 @@ def run_batch(args):
         f.close()
 
 
+def run_serve(args):
+    """Poisson-arrival stream of filter jobs (sides U{256..4096}, n U{1,2},
+    float32 images on the 2^-16 grid with ellipse fields as the 2048^2 case)
+    through the library's request loop, admitted by device-memory footprint
+    (budget: half the free HBM).  Measures the saturation rate, then p50/p99
+    latency (done - arrival) at 0.5, 0.8 and 0.95 of it; and the same stream
+    at 0.8 of it through a one-job-at-a-time server."""
+    import torch
+    import synthetic
+    from paper_0908_3861_gb300 import _abf, Server, make_desc
+    import __graft_entry__
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    rng = np.random.default_rng(synthetic.SEED_BASE + 4 + 97 * rank)
+    pool = []
+    for i in range(args.pool):
+        h, w = int(rng.integers(256, 4097)), int(rng.integers(256, 4097))
+        r = np.random.default_rng(synthetic.SEED_BASE + 4 + 1000 * (i + 1))
+        img = synthetic.image_f32_grid(r, (h, w), 24.0, 12, 16)
+        sc = synthetic.ellipse_field(r, (h, w))
+        d = _abf.abf_desc()
+        d.width, d.height, d.scale_kind, d.q_bits, d.max_scale = w, h, _abf.ABF_SCALES_ELLIPSE, 8, 150.0
+        prods = {}
+        for n in (1, 2):
+            d.order_n = n
+            prods[n] = _abf.abf_measure_scales(d, torch.from_numpy(sc).to(dev), w * 16)[1]
+        pool.append(dict(img=torch.from_numpy(img).pin_memory(), sc=torch.from_numpy(sc).pin_memory(),
+                         outs=[torch.empty((h, w), dtype=torch.float32).pin_memory() for _ in range(args.inflight + 2)],
+                         desc={n: make_desc(w, h, n, torch.float32, scale_kind="ellipse", q_bits=8, frac_bits=16,
+                                            max_scale=150.0, out="f32", value_bound=255.0,
+                                            max_scale_product=prods[n]) for n in (1, 2)},
+                         px=h * w, next=0))
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.5)
+
+    def draw(rg):
+        e = pool[int(rg.integers(0, len(pool)))]
+        return e, int(rg.integers(1, 3))
+
+    def submit(srv, e, n):
+        o = e["outs"][e["next"] % len(e["outs"])]
+        e["next"] += 1
+        return srv.submit(e["desc"][n], e["img"], e["sc"], o), e["px"]
+
+    def run_stream(inflight, lam, njobs, warm, seed):
+        srv = Server(budget, max_inflight=inflight, device=dev)
+        rg = np.random.default_rng(seed)
+        for e in pool:                       # plans and tables, outside the measurement
+            for n in (1, 2):
+                srv.wait(submit(srv, e, n)[0])
+        gaps = rg.exponential(1.0 / lam, njobs) if lam else np.zeros(njobs)
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for k in range(njobs):
+            due += gaps[k]
+            dt = due - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            e, n = draw(rg)
+            tickets.append(submit(srv, e, n))
+        stats = [(srv.wait(t), px) for t, px in tickets]
+        srv.close()
+        meas = stats[warm:]
+        lat = np.array([(s["t_done_us"] - s["t_submit_us"]) * 1e-3 for s, _ in meas])
+        span = (max(s["t_done_us"] for s, _ in meas) - min(s["t_submit_us"] for s, _ in meas)) * 1e-6
+        return dict(p50_ms=round(float(np.percentile(lat, 50)), 2), p99_ms=round(float(np.percentile(lat, 99)), 2),
+                    mpix_s=round(sum(px for _, px in meas) / span / 1e6, 2), jobs=len(meas),
+                    jobs_per_s=round(len(meas) / span, 2))
+
+    with ClockSampler(local) as clk:
+        sat = run_stream(args.inflight, 0.0, args.sat_jobs, 0, 11)
+        mu = sat["jobs_per_s"]
+        loads = {}
+        for frac in (0.5, 0.8, 0.95):
+            loads[str(frac)] = run_stream(args.inflight, frac * mu, args.jobs + args.jobs // 10, args.jobs // 10,
+                                          int(frac * 100))
+        fifo = run_stream(1, 0.8 * mu, args.jobs + args.jobs // 10, args.jobs // 10, 80)
+    line = {"metric": METRIC, "value": sat["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": args.sat_jobs,
+            "warmup": 2 * len(pool), "ms_per_step": round(1e3 / mu, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64 limbs", "data": "synthetic",
+            "config": {"workload": "Poisson stream of filter jobs, sides U{256..4096}, n U{1,2}, f32 2^-16 grid, "
+                                   "ellipse fields; exact form; HBM budget = half the free memory",
+                       "pool_images": len(pool), "slots": args.inflight, "budget_bytes": budget},
+            "saturation": sat, "latency": loads, "fifo_at_0.8": fifo, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(w, seconds=15.0, sample=None, keep=False):
     """The oracle (exact, per-pixel windows) on a bounded sample of the workload."""
     from oracle import paper, scales as osc
@@ -434,6 +524,10 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--pool", type=int, default=8, help="c5: distinct images in the request pool")
+    ap.add_argument("--inflight", type=int, default=4, help="c5: concurrent jobs (slots)")
+    ap.add_argument("--jobs", type=int, default=200, help="c5: measured jobs per load")
+    ap.add_argument("--sat-jobs", dest="sat_jobs", type=int, default=48, help="c5: jobs of the saturation burst")
     ap.add_argument("--compare", default="plain_f64",
                     help="comma-separated forms timed beside the exact form ('' for none)")
     args = ap.parse_args()
@@ -442,6 +536,8 @@ def main():
         run_reference(args)
     elif args.workload == "c4":
         run_batch(args)
+    elif args.workload == "c5":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -199,6 +199,64 @@ abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size
                             cudaStream_t stream);
 int32_t abf_batch_max_jobs(void);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop for filter jobs (image + per-pixel scale field, host memory)
+ * on one GPU.  A worker thread admits queued jobs in arrival order as long as
+ * a slot (a CUDA stream) is free and the job's device footprint (image,
+ * scales, output, integrated image, workspace) fits the HBM budget; later
+ * jobs that fit may pass a head job that does not.  Admitted jobs run
+ * concurrently on their streams (copy in, abf_integrate, abf_filter, copy out),
+ * so jobs that arrive while others run overlap with them on the device.
+ * Integrated images can stay resident under an image id: a later job with the
+ * same id and the same descriptor skips the copy of the image and the
+ * non-adaptive step (filtering the same image with a new scale field).
+ * Resident images are evicted least-recently-used when memory is needed.
+ * Results are the same as abf_integrate + abf_filter on the job alone.      */
+typedef struct abf_server_s* abf_server;
+
+typedef struct {
+  size_t hbm_budget;        /* bytes of device memory the server may hold (> 0)    */
+  int32_t max_inflight;     /* jobs running at once (slots, 1..64)                  */
+  int32_t flags;            /* reserved, 0                                          */
+} abf_server_cfg;
+
+typedef struct {
+  abf_desc desc;            /* exact form                                           */
+  const void* h_f;          /* host image (pinned memory lets copies overlap)       */
+  size_t f_pitch;
+  const void* h_scales;     /* host scale field, H x W float4                       */
+  size_t scale_pitch;
+  void* h_s;                /* host output, H x W desc.out_dtype                    */
+  size_t s_pitch;
+  uint64_t image_id;        /* 0: do not keep; else keep the integrated image       */
+} abf_request;
+
+typedef struct {
+  double t_submit_us, t_admit_us, t_done_us;  /* host steady clock, microseconds  */
+  int32_t resident_hit;     /* 1 if the integrated image was reused                 */
+  int32_t status;           /* abf_status of the job (valid once done)              */
+  int32_t device_status;    /* OR of ABF_DEV_* bits seen by this job's plan          */
+  int32_t reserved;
+} abf_job_stats;
+
+/* Start a server on the current device.  Errors: ABF_ERR_INVALID, ABF_ERR_CUDA. */
+abf_status abf_server_create(const abf_server_cfg* cfg, abf_server* out);
+/* Queue a job; the host buffers must stay valid until the job is done.
+ * ABF_ERR_BUSY if the job alone exceeds the budget.                         */
+abf_status abf_submit(abf_server srv, const abf_request* req, uint64_t* ticket);
+/* done = 1 once the job finished (stats filled); the record is kept until waited. */
+abf_status abf_poll(abf_server srv, uint64_t ticket, int32_t* done, abf_job_stats* stats);
+/* Wait up to timeout_us (< 0: no limit) for a job; ABF_ERR_TIMEOUT if it is not
+ * done by then (the job stays queued or running).  Releases the record when done. */
+abf_status abf_wait(abf_server srv, uint64_t ticket, int64_t timeout_us, abf_job_stats* stats);
+/* Stop (1) or resume (0) admitting queued jobs; running jobs continue.     */
+abf_status abf_server_pause(abf_server srv, int32_t paused);
+/* Bytes held now / at most so far, jobs running, jobs queued, resident images. */
+abf_status abf_server_stats(abf_server srv, size_t* used, size_t* peak, int32_t* inflight,
+                            int32_t* queued, int32_t* resident);
+/* Finish every queued and running job, then free everything.               */
+abf_status abf_server_destroy(abf_server srv);
+
 /* The per-pixel integer steps C_k = rint(c_k 2^Q) (int32 x4 per pixel) that
  * abf_filter uses, for inspection and reuse.                                 */
 abf_status abf_prepare_scales(abf_plan plan, const void* d_scales, size_t scale_pitch,

@@ -9,11 +9,11 @@ ABI of include/abf.h (libabf.so).  ``_abf`` binds that ABI one to one;
 from . import _abf
 from ._abf import AbfError
 
-__all__ = ["_abf", "AbfError", "AdaptiveFilter", "Batch"]
+__all__ = ["_abf", "AbfError", "AdaptiveFilter", "Batch", "Server", "make_desc"]
 
 
 def __getattr__(name):
-    if name in ("AdaptiveFilter", "Batch"):
+    if name in ("AdaptiveFilter", "Batch", "Server", "make_desc"):
         from . import filter as _f
         return getattr(_f, name)
     raise AttributeError(name)

@@ -43,6 +43,22 @@ class abf_desc(ctypes.Structure):
                 ("value_bound", ctypes.c_double), ("max_scale_product", ctypes.c_double)]
 
 
+class abf_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class abf_request(ctypes.Structure):
+    _fields_ = [("desc", abf_desc), ("h_f", ctypes.c_void_p), ("f_pitch", ctypes.c_size_t),
+                ("h_scales", ctypes.c_void_p), ("scale_pitch", ctypes.c_size_t), ("h_s", ctypes.c_void_p),
+                ("s_pitch", ctypes.c_size_t), ("image_id", ctypes.c_uint64)]
+
+
+class abf_job_stats(ctypes.Structure):
+    _fields_ = [("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
+                ("resident_hit", ctypes.c_int32), ("status", ctypes.c_int32), ("device_status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -71,6 +87,13 @@ def lib():
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
         "abf_batch_max_jobs": ([], i32),
+        "abf_server_create": ([P(abf_server_cfg), P(vp)], st),
+        "abf_submit": ([vp, P(abf_request), P(ctypes.c_uint64)], st),
+        "abf_poll": ([vp, ctypes.c_uint64, P(i32), P(abf_job_stats)], st),
+        "abf_wait": ([vp, ctypes.c_uint64, ctypes.c_int64, P(abf_job_stats)], st),
+        "abf_server_pause": ([vp, i32], st),
+        "abf_server_stats": ([vp, P(sz), P(sz), P(i32), P(i32), P(i32)], st),
+        "abf_server_destroy": ([vp], st),
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
@@ -188,6 +211,48 @@ def abf_filter_batch(jobs, ws, stream=None):
 
 def abf_batch_max_jobs():
     return lib().abf_batch_max_jobs()
+
+
+def abf_server_create(hbm_budget, max_inflight):
+    cfg = abf_server_cfg(int(hbm_budget), int(max_inflight), 0)
+    h = ctypes.c_void_p()
+    _check(lib().abf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "abf_server_create")
+    return h
+
+
+def abf_submit(server, req):
+    t = ctypes.c_uint64()
+    _check(lib().abf_submit(server, ctypes.byref(req), ctypes.byref(t)), "abf_submit")
+    return t.value
+
+
+def abf_poll(server, ticket):
+    done = ctypes.c_int32()
+    st = abf_job_stats()
+    _check(lib().abf_poll(server, ticket, ctypes.byref(done), ctypes.byref(st)), "abf_poll")
+    return bool(done.value), st
+
+
+def abf_wait(server, ticket, timeout_us=-1):
+    st = abf_job_stats()
+    _check(lib().abf_wait(server, ticket, int(timeout_us), ctypes.byref(st)), "abf_wait")
+    return st
+
+
+def abf_server_pause(server, paused):
+    _check(lib().abf_server_pause(server, 1 if paused else 0), "abf_server_pause")
+
+
+def abf_server_stats(server):
+    u, p = ctypes.c_size_t(), ctypes.c_size_t()
+    i, q, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().abf_server_stats(server, ctypes.byref(u), ctypes.byref(p), ctypes.byref(i), ctypes.byref(q),
+                                  ctypes.byref(r)), "abf_server_stats")
+    return dict(used=u.value, peak=p.value, inflight=i.value, queued=q.value, resident=r.value)
+
+
+def abf_server_destroy(server):
+    _check(lib().abf_server_destroy(server), "abf_server_destroy")
 
 
 def abf_status_str(s):

@@ -401,3 +401,14 @@ __device__ __forceinline__ void raise_status(int32_t* st, int32_t bits) {
 }
 
 }  // namespace abf
+
+// A plan (opaque in the C ABI).
+struct abf_plan_s {
+  abf_desc desc;
+  abf::PlanView pv;
+  void* real_table = nullptr;  // tile forms
+  unsigned __int128 D;
+  int device;
+  int32_t* d_status = nullptr;
+  size_t g_bytes = 0, ws_bytes = 0;
+};

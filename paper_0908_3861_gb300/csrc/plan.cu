@@ -323,15 +323,7 @@ double u128_to_double(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073
 
 // ------------------------------------------------------------------ the plan
 
-struct abf_plan_s {
-  abf_desc desc;
-  abf::PlanView pv;
-  void* real_table = nullptr;  // tile forms
-  u128 D;
-  int device;
-  int32_t* d_status = nullptr;
-  size_t g_bytes = 0, ws_bytes = 0;
-};
+
 
 extern "C" {
 

@@ -130,3 +130,70 @@ class Batch:
                                   flt.W * o.element_size()))
         C.abf_filter_batch(jobs, self.ws, stream)
         return outs
+
+
+def make_desc(width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0, max_scale=8.0, out="f64",
+              form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0):
+    d = C.abf_desc()
+    d.width, d.height, d.order_n = int(width), int(height), int(n)
+    d.in_dtype = _DT[in_dtype]
+    d.out_dtype = _OUT[out][0]
+    d.form = C.FORMS[form]
+    d.scale_kind = C.SCALE_KINDS[scale_kind]
+    d.q_bits = int(q_bits)
+    d.in_frac_bits = int(frac_bits)
+    d.flags = 0
+    d.max_scale = float(max_scale)
+    d.min_scale = float(min_scale)
+    d.value_bound = float(value_bound)
+    d.max_scale_product = float(max_scale_product)
+    return d
+
+
+class Server:
+    """The library's request loop (abf_server_*): jobs from host memory,
+    admitted by device-memory footprint, run concurrently on their own streams,
+    integrated images optionally kept resident by image id."""
+
+    def __init__(self, hbm_budget, max_inflight=4, device=None):
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.h = C.abf_server_create(hbm_budget, max_inflight)
+        self.keep = {}
+
+    def submit(self, desc, f, scales, out, image_id=0):
+        """f, scales, out: CPU tensors (pinned for overlapping copies); f may be
+        None when the image is resident under image_id."""
+        req = C.abf_request()
+        req.desc = desc
+        req.h_f = f.data_ptr() if f is not None else None
+        req.f_pitch = desc.width * (f.element_size() if f is not None else 0)
+        req.h_scales = scales.data_ptr()
+        req.scale_pitch = desc.width * 16
+        req.h_s = out.data_ptr()
+        req.s_pitch = desc.width * out.element_size()
+        req.image_id = int(image_id)
+        t = C.abf_submit(self.h, req)
+        self.keep[t] = (f, scales, out)
+        return t
+
+    def wait(self, ticket, timeout_s=None):
+        st = C.abf_wait(self.h, ticket, -1 if timeout_s is None else int(timeout_s * 1e6))
+        self.keep.pop(ticket, None)
+        return dict(t_submit_us=st.t_submit_us, t_admit_us=st.t_admit_us, t_done_us=st.t_done_us,
+                    resident_hit=st.resident_hit, status=st.status, device_status=st.device_status)
+
+    def poll(self, ticket):
+        done, st = C.abf_poll(self.h, ticket)
+        return done
+
+    def pause(self, paused=True):
+        C.abf_server_pause(self.h, paused)
+
+    def stats(self):
+        return C.abf_server_stats(self.h)
+
+    def close(self):
+        if self.h is not None:
+            C.abf_server_destroy(self.h)
+            self.h = None
