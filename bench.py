@@ -253,6 +253,9 @@ def run_ours(args):
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     peak_macs = 152 * 64 * sm_mhz * 1e6 / imad_per_mac
     achieved = macs / (mesh_ms * 1e-3)
+    hl = filt.info["halo_lrbt"]
+    gw, gh = W + hl[0] + hl[1], H + hl[3]
+    integ_bytes = float(img.nbytes) + 7.0 * gw * gh * 8 * L
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
@@ -266,7 +269,9 @@ def run_ours(args):
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(f_h.numel() * f_h.element_size() + s_h.numel() * 4),
                 "d2h_bytes_per_step": int(o_h.numel() * 4)},
-        "gpu_launches": int(K * (1 + 3 * n + 1)),
+        # per step: one row scan, one fused n-fold line scan per direction
+        # (v2, v3, v4), one mesh launch
+        "gpu_launches": int(K * (1 + 3 + 1)),
         "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak_macs / 1e9, 2),
                      "unit": "G MAC/s (%d-limb integer x %d-bit weight)" % (L, 32 * wwords),
@@ -274,6 +279,13 @@ def run_ours(args):
                      "peak_note": "derived: 152 SM x 64 INT32 multiply-add lanes x median SM clock / %d "
                                   "32-bit multiply-adds per MAC; achieved = (n+1)^4 x 7n^2 stencil MACs per pixel"
                                   % imad_per_mac},
+        "roofline_integrate": {"bound": "hbm", "achieved": round(integ_bytes / (integ_ms * 1e-3) / 1e9, 1),
+                               "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                               "frac": (round(integ_bytes / (integ_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
+                                        if peaks.get("hbm_gbs") else None),
+                               "traffic": None, "kernel": "row_scan_kernel + 3 x line_scan_kernel",
+                               "bytes_note": "f read once, g written by the row scan, then read and written "
+                                             "once per line direction: |f| + 7 |g| per integrate"},
         "clocks": clk,
     }
     if rank == 0 and args.cpu_baseline:

@@ -31,7 +31,7 @@
 namespace abf {
 cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
                           uint32_t* epoch, int32_t* status, cudaStream_t st);
-size_t line_ws_bytes(int Gw, int Gh, int L, int* nbands_out, int* nlines_out);
+size_t line_ws_bytes(int Gw, int Gh, int L, int n, int* nbands_out, int* nlines_out);
 cudaError_t run_mesh_exact(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
                            size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st);
 cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t scale_pitch, void* C, size_t C_pitch,
@@ -416,7 +416,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   pv.table = tab.ptr;
   if (exact) {
     p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
-    p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, nullptr, nullptr);
+    p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, n, nullptr, nullptr);
   } else {
     const int rb = d->form == ABF_FORM_PLAIN_F64 ? 8 : 4;
     abf_status rs = get_real_table(dev, n, P, rb, &p->real_table);

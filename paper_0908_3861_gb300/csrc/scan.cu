@@ -128,16 +128,23 @@ __global__ void __launch_bounds__(256) row_scan_kernel(const PlanView pv, const 
 }
 
 // ---------------------------------------------------------- lines (v2, v3, v4)
+// One pass per direction carries all n cascaded running sums: per line a state
+// (s_1..s_n), updated per element x as s_1 += x, s_2 += s_1, ..., out = s_n.
+// A band of R rows maps an incoming state c to T_R(c) + A, where A is the
+// band's own result from a zero state and T_t is the zero-input evolution over
+// t steps, T_t(c)_k = sum_{j<=k} c_j binom(t + k - j - 1, k - j).  Look-back
+// therefore sums T_{dR}(A) over the d-th band below until a band that has
+// published its inclusive state P, which enters as T_{dR}(P).
 
-constexpr int kBand = 16;         // rows per band
+constexpr int kBand = 32;         // rows per band
 constexpr int kLinesPerCta = 128; // lines per CTA (one per thread)
 constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;
 constexpr long long kSpinLimit = 1ll << 22;
 
 struct LineWs {
   uint32_t* flags;    // [nbands][nlines]
-  uint64_t* agg;      // [nbands][nlines][L]
-  uint64_t* pref;     // [nbands][nlines][L]
+  uint64_t* agg;      // [nbands][nlines][NF][L]
+  uint64_t* pref;     // [nbands][nlines][NF][L]
   uint32_t* ticket;   // one counter, zeroed before each launch
   int nbands, nlines, ngroups;
 };
@@ -151,7 +158,54 @@ __device__ __forceinline__ int line_col(int l, int y, int Gh) {
   else return l - y;
 }
 
-template <int L, int DIR>
+template <int L, int NF>
+struct LineState {
+  Wide<L> s[NF];
+};
+
+template <int L, int NF>
+__device__ __forceinline__ void st_zero(LineState<L, NF>& a) {
+#pragma unroll
+  for (int k = 0; k < NF; ++k) wzero<L>(a.s[k]);
+}
+
+template <int L, int NF>
+__device__ __forceinline__ void st_step(LineState<L, NF>& a, const Wide<L>& x) {
+  wadd<L>(a.s[0], x);
+#pragma unroll
+  for (int k = 1; k < NF; ++k) wadd<L>(a.s[k], a.s[k - 1]);
+}
+
+// acc += T_t(c): the zero-input evolution of state c over t steps.
+template <int L, int NF>
+__device__ __forceinline__ void st_add_transported(LineState<L, NF>& acc, const LineState<L, NF>& c, long long t) {
+  wadd<L>(acc.s[0], c.s[0]);
+  if constexpr (NF >= 2) {
+    wadd<L>(acc.s[1], c.s[1]);
+    wmac<L>(acc.s[1], c.s[0], (uint64_t)t);
+  }
+  if constexpr (NF >= 3) {
+    wadd<L>(acc.s[2], c.s[2]);
+    wmac<L>(acc.s[2], c.s[1], (uint64_t)t);
+    wmac<L>(acc.s[2], c.s[0], (uint64_t)(t * (t + 1) / 2));
+  }
+}
+
+template <int L, int NF>
+__device__ __forceinline__ LineState<L, NF> st_load(const uint64_t* p) {
+  LineState<L, NF> r;
+#pragma unroll
+  for (int k = 0; k < NF; ++k) r.s[k] = wload<L>(p + k * L);
+  return r;
+}
+
+template <int L, int NF>
+__device__ __forceinline__ void st_store(uint64_t* p, const LineState<L, NF>& a) {
+#pragma unroll
+  for (int k = 0; k < NF; ++k) wstore<L>(p + k * L, a.s[k]);
+}
+
+template <int L, int DIR, int NF>
 __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
                                                                  LineWs ws, uint32_t epoch,
                                                                  int32_t* status) {
@@ -166,10 +220,10 @@ __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView 
   const bool line_ok = l < ws.nlines;
   const int y0 = band * kBand;
 
-  Wide<L> v[kBand];
-  Wide<L> run;
-  wzero<L>(run);
-#pragma unroll
+  // band aggregate from a zero state
+  LineState<L, NF> agg;
+  st_zero<L, NF>(agg);
+#pragma unroll 8
   for (int i = 0; i < kBand; ++i) {
     const int y = y0 + i;
     const int xi = line_col<DIR>(l, y, pv.Gh);
@@ -177,20 +231,20 @@ __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView 
     wzero<L>(val);
     if (line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw)
       val = wload<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L);
-    wadd<L>(run, val);
-    v[i] = run;
+    st_step<L, NF>(agg, val);
   }
 
-  // Decoupled look-back over the bands below (same line).
-  Wide<L> carry;
-  wzero<L>(carry);
+  // decoupled look-back over the bands below (same line)
+  LineState<L, NF> carry;
+  st_zero<L, NF>(carry);
   const size_t slot = (size_t)band * ws.nlines + (line_ok ? l : 0);
   if (line_ok) {
     if (band > 0) {
-      wstore<L>(ws.agg + slot * L, run);
+      st_store<L, NF>(ws.agg + slot * NF * L, agg);
       __threadfence();
       st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);
       int bb = band - 1;
+      long long dist = 0;  // rows between the end of band bb and the start of this band
       long long spins = 0;
       while (bb >= 0) {
         const size_t s2 = (size_t)bb * ws.nlines + l;
@@ -203,31 +257,34 @@ __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView 
           continue;
         }
         if ((fl & 3u) == kFlagPrefix) {
-          Wide<L> p = wload<L>(ws.pref + s2 * L);
-          wadd<L>(carry, p);
+          st_add_transported<L, NF>(carry, st_load<L, NF>(ws.pref + s2 * NF * L), dist);
           break;
         }
-        Wide<L> a = wload<L>(ws.agg + s2 * L);
-        wadd<L>(carry, a);
+        st_add_transported<L, NF>(carry, st_load<L, NF>(ws.agg + s2 * NF * L), dist);
+        dist += kBand;
         --bb;
       }
     }
-    Wide<L> incl = run;
-    wadd<L>(incl, carry);
-    wstore<L>(ws.pref + slot * L, incl);
+    LineState<L, NF> incl = agg;
+    st_add_transported<L, NF>(incl, carry, kBand);
+    st_store<L, NF>(ws.pref + slot * NF * L, incl);
     __threadfence();
     st_release(ws.flags + slot, (epoch << 2) | kFlagPrefix);
   }
 
-#pragma unroll
+  // rescan the band from the carried state (the band's data is hot in cache)
+  LineState<L, NF> st = carry;
+#pragma unroll 8
   for (int i = 0; i < kBand; ++i) {
     const int y = y0 + i;
     const int xi = line_col<DIR>(l, y, pv.Gh);
-    if (line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw) {
-      Wide<L> o = v[i];
-      wadd<L>(o, carry);
-      wstore<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L, o);
-    }
+    const bool ok = line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw;
+    Wide<L> val;
+    wzero<L>(val);
+    uint64_t* p = g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L;
+    if (ok) val = wload<L>(p);
+    st_step<L, NF>(st, val);
+    if (ok) wstore<L>(p, st.s[NF - 1]);
   }
 }
 
@@ -242,18 +299,19 @@ static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch
   return cudaGetLastError();
 }
 
-template <int L, int DIR>
+template <int L, int DIR, int NF>
 static cudaError_t launch_lines(const PlanView& pv, uint64_t* g, const LineWs& ws, uint32_t epoch,
                                 int32_t* status, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const int ctas = ws.nbands * ws.ngroups;
-  line_scan_kernel<L, DIR><<<ctas, kLinesPerCta, 0, st>>>(pv, g, ws, epoch, status);
+  line_scan_kernel<L, DIR, NF><<<ctas, kLinesPerCta, 0, st>>>(pv, g, ws, epoch, status);
   return cudaGetLastError();
 }
 
-// Workspace needed by the line scans for a plan (bytes) and its layout.
-size_t line_ws_bytes(int Gw, int Gh, int L, int* nbands_out, int* nlines_out) {
+// Workspace needed by the line scans for a plan (bytes): flags plus an
+// n-component aggregate and prefix of L limbs per (band, line).
+size_t line_ws_bytes(int Gw, int Gh, int L, int n, int* nbands_out, int* nlines_out) {
   const int nbands = (Gh + kBand - 1) / kBand;
   const int nlines = Gw + Gh;  // enough for every direction
   if (nbands_out) *nbands_out = nbands;
@@ -261,7 +319,7 @@ size_t line_ws_bytes(int Gw, int Gh, int L, int* nbands_out, int* nlines_out) {
   const size_t cells = (size_t)nbands * (size_t)nlines;
   size_t bytes = 256;                         // ticket
   bytes += ((cells * 4 + 255) / 256) * 256;   // flags
-  bytes += cells * 8 * L * 2;                 // agg + pref
+  bytes += cells * 8 * L * n * 2;             // agg + pref
   return bytes;
 }
 
@@ -276,10 +334,10 @@ size_t line_ws_zero_bytes(int Gw, int Gh) {
   return 256 + ((cells * 4 + 255) / 256) * 256;
 }
 
-static LineWs carve(void* ws, int Gw, int Gh, int L, int DIR) {
+static LineWs carve(void* ws, int Gw, int Gh, int L, int n, int DIR) {
   LineWs w;
   int nbands, nlines_all;
-  line_ws_bytes(Gw, Gh, L, &nbands, &nlines_all);
+  line_ws_bytes(Gw, Gh, L, n, &nbands, &nlines_all);
   char* p = (char*)ws;
   w.ticket = (uint32_t*)p;
   p += 256;
@@ -287,14 +345,26 @@ static LineWs carve(void* ws, int Gw, int Gh, int L, int DIR) {
   w.flags = (uint32_t*)p;
   p += ((cells * 4 + 255) / 256) * 256;
   w.agg = (uint64_t*)p;
-  p += cells * 8 * L;
+  p += cells * 8 * L * n;
   w.pref = (uint64_t*)p;
   w.nbands = nbands;
-  w.nlines = (DIR == 3) ? Gw : (Gw + Gh - 1);
-  // keep the slot stride fixed across directions
-  w.nlines = nlines_all;
+  w.nlines = nlines_all;  // slot stride, the same for every direction
   w.ngroups = ((DIR == 3 ? Gw : Gw + Gh - 1) + kLinesPerCta - 1) / kLinesPerCta;
   return w;
+}
+
+template <int L, int NF>
+static cudaError_t lines_NF(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
+                            cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int dir = 2; dir <= 4 && e == cudaSuccess; ++dir) {
+    const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
+    const LineWs w = carve(ws, pv.Gw, pv.Gh, L, NF, dir);
+    if (dir == 2) e = launch_lines<L, 2, NF>(pv, g, w, ep, status, st);
+    else if (dir == 3) e = launch_lines<L, 3, NF>(pv, g, w, ep, status, st);
+    else e = launch_lines<L, 4, NF>(pv, g, w, ep, status, st);
+  }
+  return e;
 }
 
 template <int L>
@@ -308,16 +378,11 @@ static cudaError_t integrate_L(const PlanView& pv, const void* f, size_t f_pitch
     default: e = launch_rows<L, double>(pv, f, f_pitch, g, status, st); break;
   }
   if (e != cudaSuccess) return e;
-  for (int dir = 2; dir <= 4; ++dir) {
-    for (int k = 0; k < pv.n; ++k) {
-      const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
-      if (dir == 2) e = launch_lines<L, 2>(pv, g, carve(ws, pv.Gw, pv.Gh, L, 2), ep, status, st);
-      else if (dir == 3) e = launch_lines<L, 3>(pv, g, carve(ws, pv.Gw, pv.Gh, L, 3), ep, status, st);
-      else e = launch_lines<L, 4>(pv, g, carve(ws, pv.Gw, pv.Gh, L, 4), ep, status, st);
-      if (e != cudaSuccess) return e;
-    }
+  switch (pv.n) {
+    case 1: return lines_NF<L, 1>(pv, g, ws, epoch, status, st);
+    case 2: return lines_NF<L, 2>(pv, g, ws, epoch, status, st);
+    default: return lines_NF<L, 3>(pv, g, ws, epoch, status, st);
   }
-  return cudaSuccess;
 }
 
 cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
