@@ -159,9 +159,9 @@ abf_status abf_integrate_noalloc(abf_plan plan, const void* d_f, size_t f_pitch,
  *                    the running sums are restarted per output tile.
  *   d_scales : H rows of W float4 (desc.scale_kind), row pitch in bytes.
  *   d_s      : H rows of W desc.out_dtype, row pitch in bytes.
- * Pixels whose scales are invalid (non-finite, c_k <= 0, c_k > max_scale,
- * c1 or c3 < min_scale) or whose numerator bound exceeds the limbs get NaN and
- * set the device status.                                                     */
+ * Pixels whose scales are invalid (non-finite, C_k = rint(c_k 2^Q) < 1 or
+ * > rint(max_scale 2^Q), c1 or c3 < min_scale) or whose numerator bound
+ * exceeds the limbs get NaN and set the device status.                       */
 abf_status abf_filter(abf_plan plan, const void* d_src, size_t src_pitch, const void* d_scales,
                       size_t scale_pitch, void* d_s, size_t s_pitch, void* d_ws,
                       cudaStream_t stream);
@@ -185,14 +185,15 @@ typedef struct {
 } abf_job;
 
 /* Adaptive step (Eq. (final_eqn)) for many images of uneven size, order and
- * limb count in ONE persistent launch: the images' 32-pixel runs are numbered
- * (most expensive images first) and every warp takes the next run from a
- * device counter, so the work stays balanced across SMs.  Each image's
- * result is bit-identical to abf_filter on that image alone.
+ * limb count in one persistent launch per order n present: the images' units
+ * (8 rows x 32 columns) are numbered (largest images first) and every CTA
+ * takes the next unit from a device counter, so the work stays balanced
+ * across SMs.  Each image's result is bit-identical to abf_filter on that
+ * image alone.
  *   jobs  : njobs entries (host memory, read during the call), every plan of
  *           the exact form; up to abf_batch_max_jobs() per call (larger
  *           batches are split into several launches).
- *   d_ws  : device workspace of at least 256 bytes (the work counter); two
+ *   d_ws  : device workspace of at least 256 bytes (the work counters); two
  *           calls that overlap on the GPU must not share it.
  * Device errors go to each job's plan status word.                           */
 abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes,

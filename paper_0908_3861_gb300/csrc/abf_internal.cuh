@@ -385,9 +385,9 @@ __device__ __forceinline__ bool pixel_steps(const PlanView& pv, const float4* sc
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const double v = c[k] * q;  // exact (power of two)
-    if (!(v <= (double)pv.Cmax)) return false;
+    if (!(v < 2147483648.0)) return false;
     const long long r = __double2ll_rn(v);
-    if (r < 1) return false;
+    if (r < 1 || r > pv.Cmax) return false;  // Cmax = rint(max_scale 2^Q): rint is monotone
     C[k] = (int)r;
   }
   if (C[0] < pv.Cmin || C[2] < pv.Cmin) return false;

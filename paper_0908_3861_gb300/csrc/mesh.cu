@@ -22,6 +22,7 @@
 // with any other IEEE implementation of the same operation sequence.
 #include "abf_internal.cuh"
 
+
 namespace abf {
 
 // log2 of the numerator bound for this pixel (see file header), in binary32
@@ -97,7 +98,6 @@ __device__ __forceinline__ void store_out(void* s, size_t s_pitch, int x, int y,
 // w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
 // numerator, which lane i keeps for its own pixel and stores at the end.
 constexpr int kMeshWarps = 8;
-constexpr int kMaxTaps = 256;  // (n+1)^4 for n = 3
 
 // The stencil's neighbours, in the same order as the table rows (one thread).
 template <int N>
@@ -112,15 +112,72 @@ __device__ __forceinline__ void fill_stencil(int* s_dx, int* s_dy) {
       }
 }
 
+// a <<= k (mod 2^(64 L)), 0 <= k < 64.
+template <int L>
+__device__ __forceinline__ void wshl(Wide<L>& a, int k) {
+  if (k == 0) return;
+#pragma unroll
+  for (int i = L - 1; i > 0; --i) a.w[i] = (a.w[i] << k) | (a.w[i - 1] >> (64 - k));
+  a.w[0] <<= k;
+}
+
+// n = 2: the FD weight of vertex j is w_j = (-2)^k, k = #{i : j_i = 1}.  The
+// taps are visited grouped by k (group sizes binom(4,k) 2^(4-k) = 16, 32, 24,
+// 8, 1), each group summed without its weight and then added with it.
+__host__ __device__ constexpr int n2_group_begin(int k) {
+  return k <= 0 ? 0 : k == 1 ? 16 : k == 2 ? 48 : k == 3 ? 72 : k == 4 ? 80 : 81;
+}
+
+// Tap order for n = 2 (one thread): slot -> natural tap index t = j1 + 3 j3 + 9 j2 + 27 j4.
+__device__ __forceinline__ void fill_n2_order(unsigned char* order) {
+  int c = 0;
+  for (int k = 0; k <= 4; ++k)
+    for (int t = 0; t < 81; ++t) {
+      int ones = 0;
+      for (int u = t, i = 0; i < 4; ++i, u /= 3) ones += (u % 3) == 1;
+      if (ones == k) order[c++] = (unsigned char)t;
+    }
+}
+
+// One pixel's numerator share for n = 2 (lane = neighbour): taps[s] holds
+// (x: g offset of the tap's lattice point from this lane's base gl, y: table
+// offset from this lane's base tl, z: the tap's lattice row).  A tap whose
+// whole stencil lies below row 0 points at the table's zero row and at a
+// readable patch; CHECK also drops this lane's read where its own row is below 0
+// (taps that straddle row 0).
+template <int L, bool CHECK>
+__device__ __forceinline__ void n2_pixel(Wide<L>& acc, const int4* taps, const uint64_t* gl,
+                                         const uint64_t* __restrict__ tl, int dy) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    Wide<L> part;
+    wzero<L>(part);
+#pragma unroll
+    for (int s = n2_group_begin(k); s < n2_group_begin(k + 1); ++s) {
+      const int2 ti = *reinterpret_cast<const int2*>(&taps[s]);
+      if (CHECK && taps[s].z + dy < 0) continue;
+      const Wide<L> gv = wload<L>(gl + (ptrdiff_t)ti.x * L);
+      const uint64_t wt = __ldg(tl + ti.y);
+      mac_weight<L, uint64_t>(part, gv, wt);
+    }
+    wshl<L>(part, k);
+    if (k & 1) wsub<L>(acc, part);
+    else wadd<L>(acc, part);
+  }
+}
+
 // Mesh for the run of 32 pixels (x0 .. x0+31, y) of one image; the whole warp
 // calls it.  taps: this warp's (n+1)^4-entry shared tap table; s_dx/s_dy: the
-// order-n stencil in shared memory.
-template <int N, int L>
+// order-n stencil in shared memory.  FAST (n = 2 only): lanes keep their
+// neighbour's g and table bases, taps carry plain offsets, and the FD weights
+// are applied per group (n2_pixel); s_order is then the group-sorted tap order,
+// and g offsets must fit 32 bits and the box have at least 3n rows.
+template <int N, int L, bool FAST = false>
 __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __restrict__ g,
                                          const float4* __restrict__ scales, size_t scale_pitch, void* __restrict__ s,
                                          size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch,
                                          int32_t* status, int y, int x0, int4* taps, const int* s_dx,
-                                         const int* s_dy) {
+                                         const int* s_dy, const unsigned char* s_order = nullptr) {
   using WT = typename WeightT<N>::T;
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
@@ -167,52 +224,79 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
     const int y0y = (y << P) + ty;
     const int s1 = c0 << sh, s2 = c1 << sh, s3 = c2 << sh, s4 = c3 << sh;
     __syncwarp();
-    for (int t = lane; t < TAPS; t += 32) {
-      const int j1 = t % (N + 1);
-      const int t1 = t / (N + 1);
-      const int j3 = t1 % (N + 1);
-      const int t2 = t1 / (N + 1);
-      const int j2 = t2 % (N + 1);
-      const int j4 = t2 / (N + 1);
-      const int w = signed_binom<N>(j1) * signed_binom<N>(j2) * signed_binom<N>(j3) * signed_binom<N>(j4);
-      // y_j = y0 - j1 c1 v1 - j2 c2 v2 - j3 c3 v3 - j4 c4 v4
-      const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4;
-      const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4;
-      const int px = (Yx + half) >> P;
-      const int py = (Yy + half) >> P;
-      const int r = (((Yy + half) & mask) << P) | ((Yx + half) & mask);
-      // n = 2: store the shift k of |w| = 2^k; otherwise |w|
-      const int aw = w < 0 ? -w : w;
-      taps[t] = make_int4(px + left, py, r, ((N == 2) ? (__ffs(aw) - 1) : aw) * (w < 0 ? -1 : 1) - (w < 0 ? 1 : 0));
-    }
-    __syncwarp();
-    Wide<L> acc, accn;
+    Wide<L> acc;
     wzero<L>(acc);
-    wzero<L>(accn);
-#pragma unroll 4
-    for (int it = 0; it < ITERS; ++it) {
-      const int pair = it * 32 + lane;
-      if (PAIRS % 32 != 0 && pair >= PAIRS) continue;
-      const int tap = (R == 32) ? it : pair / R;
-      const int cand = (R == 32) ? lane : pair - tap * R;
-      const int4 ti = taps[tap];
-      const int dx = (R == 32) ? my_dx : s_dx[cand];
-      const int dy = (R == 32) ? my_dy : s_dy[cand];
-      const int k2 = ti.y + dy;
-      if (k2 < 0) continue;  // rows below the image: g = 0
-      const bool neg = ti.w < 0;
-      const int code = neg ? -(ti.w + 1) : ti.w;  // shift (n = 2) or |w_j|
-      const WT wt = __ldg(table + (size_t)ti.z * R + cand);
-      const Wide<L> gv = wload<L>(g + ((size_t)k2 * rowpitch + (size_t)(ti.x + dx)) * L);
-      if constexpr (N == 2) {
-        const WT ws = wt << code;
-        if (neg) mac_weight<L, WT>(accn, gv, ws);
-        else mac_weight<L, WT>(acc, gv, ws);
-      } else {
-        mac_weight<L, WT>(acc, neg ? wneg<L>(gv) : gv, scale_weight<N, WT>(wt, code));
+    if constexpr (FAST) {
+      static_assert(N == 2 && R == 32, "fast path is for n = 2");
+      constexpr int kDyMin = Stencil<N>::kDmin, kDyMax = Stencil<N>::kDmin + 3 * N - 1;
+      const int gp = (int)rowpitch;
+      int strad = 0;
+      for (int slot = lane; slot < TAPS; slot += 32) {
+        const int t = s_order[slot];
+        const int j1 = t % 3, j3 = (t / 3) % 3, j2 = (t / 9) % 3, j4 = t / 27;
+        const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4;
+        const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4;
+        const int px = Yx >> P, py = Yy >> P;
+        const int r = ((Yy & mask) << P) | (Yx & mask);
+        const bool below = py + kDyMax < 0;
+        strad |= (py + kDyMin < 0) && !below;
+        const int xf = (below ? -kDyMin : py) * gp + px + left;
+        const int tf = (below ? (1 << (2 * P)) : r) * R;
+        taps[slot] = make_int4(xf, tf, py, 0);
       }
+      const bool check = __any_sync(0xffffffffu, strad) != 0;
+      __syncwarp();
+      const uint64_t* gl = g + ((ptrdiff_t)my_dy * rowpitch + my_dx) * L;
+      const uint64_t* tl = reinterpret_cast<const uint64_t*>(pv.table) + lane;
+      if (check) n2_pixel<L, true>(acc, taps, gl, tl, my_dy);
+      else n2_pixel<L, false>(acc, taps, gl, tl, my_dy);
+    } else {
+      for (int t = lane; t < TAPS; t += 32) {
+        const int j1 = t % (N + 1);
+        const int t1 = t / (N + 1);
+        const int j3 = t1 % (N + 1);
+        const int t2 = t1 / (N + 1);
+        const int j2 = t2 % (N + 1);
+        const int j4 = t2 / (N + 1);
+        const int w = signed_binom<N>(j1) * signed_binom<N>(j2) * signed_binom<N>(j3) * signed_binom<N>(j4);
+        // y_j = y0 - j1 c1 v1 - j2 c2 v2 - j3 c3 v3 - j4 c4 v4
+        const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4;
+        const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4;
+        const int px = (Yx + half) >> P;
+        const int py = (Yy + half) >> P;
+        const int r = (((Yy + half) & mask) << P) | ((Yx + half) & mask);
+        // n = 2: store the shift k of |w| = 2^k; otherwise |w|
+        const int aw = w < 0 ? -w : w;
+        taps[t] = make_int4(px + left, py, r, ((N == 2) ? (__ffs(aw) - 1) : aw) * (w < 0 ? -1 : 1) - (w < 0 ? 1 : 0));
+      }
+      __syncwarp();
+      Wide<L> accn;
+      wzero<L>(accn);
+#pragma unroll 4
+      for (int it = 0; it < ITERS; ++it) {
+        const int pair = it * 32 + lane;
+        if (PAIRS % 32 != 0 && pair >= PAIRS) continue;
+        const int tap = (R == 32) ? it : pair / R;
+        const int cand = (R == 32) ? lane : pair - tap * R;
+        const int4 ti = taps[tap];
+        const int dx = (R == 32) ? my_dx : s_dx[cand];
+        const int dy = (R == 32) ? my_dy : s_dy[cand];
+        const int k2 = ti.y + dy;
+        if (k2 < 0) continue;  // rows below the image: g = 0
+        const bool neg = ti.w < 0;
+        const int code = neg ? -(ti.w + 1) : ti.w;  // shift (n = 2) or |w_j|
+        const WT wt = __ldg(table + (size_t)ti.z * R + cand);
+        const Wide<L> gv = wload<L>(g + ((size_t)k2 * rowpitch + (size_t)(ti.x + dx)) * L);
+        if constexpr (N == 2) {
+          const WT ws = wt << code;
+          if (neg) mac_weight<L, WT>(accn, gv, ws);
+          else mac_weight<L, WT>(acc, gv, ws);
+        } else {
+          mac_weight<L, WT>(acc, neg ? wneg<L>(gv) : gv, scale_weight<N, WT>(wt, code));
+        }
+      }
+      if constexpr (N == 2) wsub<L>(acc, accn);
     }
-    if constexpr (N == 2) wsub<L>(acc, accn);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       Wide<L> other;
@@ -269,31 +353,38 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
 // with the sign choosing one of two accumulators.  Each lane accumulates
 // w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
 // numerator, which lane i keeps for its own pixel and stores at the end.
-template <int N, int L>
+// A CTA takes the 32-column runs of kMeshWarps consecutive rows: neighbouring
+// rows have nearby taps, so their g patches are shared in L1.
+template <int N, int L, bool FAST>
 __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R];
+  __shared__ unsigned char s_order[TAPS];
   __shared__ int4 s_tap[kMeshWarps][TAPS];
-  if (threadIdx.x == 0) fill_stencil<N>(s_dx, s_dy);
+  if (threadIdx.x == 0) {
+    fill_stencil<N>(s_dx, s_dy);
+    if constexpr (FAST) fill_n2_order(s_order);
+  }
   __syncthreads();
   const int segs = (pv.W + 31) >> 5;
-  const int wid = blockIdx.x * kMeshWarps + (threadIdx.x >> 5);
-  if (wid >= segs * pv.H) return;
-  const int y = wid / segs;
-  const int x0 = (wid - y * segs) * 32;
-  mesh_run<N, L>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0, s_tap[threadIdx.x >> 5],
-                 s_dx, s_dy);
+  const int band = blockIdx.x / segs;
+  const int y = band * kMeshWarps + (threadIdx.x >> 5);
+  if (y >= pv.H) return;
+  const int x0 = (blockIdx.x - band * segs) * 32;
+  mesh_run<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
+                       s_tap[threadIdx.x >> 5], s_dx, s_dy, s_order);
 }
 
 // ------------------------------------------------------------------- batches
 // Many images (each its own plan: size, order n, limbs) in one persistent
-// launch.  The images' 32-pixel runs are numbered consecutively, the most
-// expensive images first; every warp repeatedly takes the next run from a
-// global counter and filters it with its image's plan, so images of uneven
-// size and order share the GPU without a tail of idle SMs.
+// launch per order n.  The images' units (kMeshWarps rows x 32 columns) are
+// numbered consecutively, the most expensive images first; every CTA
+// repeatedly takes the next unit from a global counter and filters it with its
+// image's plan, so images of uneven size share the GPU without a tail of idle
+// SMs.
 constexpr int kMaxBatch = 96;
 
 struct BatchJob {
@@ -304,63 +395,73 @@ struct BatchJob {
   void* s;
   size_t s_pitch;
   int32_t* status;
-  long long runs_begin;  // first global run index of this image
-  int segs;              // runs per row
+  long long units_begin;  // first global unit index of this image
+  int segs;               // 32-column runs per row
+  int fast;               // n = 2 fast path usable (mesh_fast_ok)
 };
 
 struct BatchJobs {
   int njobs;
-  long long total_runs;
+  long long total_units;
   BatchJob job[kMaxBatch];
 };
 
 template <int N, int L>
 __device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int x0, int4* taps, const int* sdx,
-                                                 const int* sdy) {
+                                                 const int* sdy, const unsigned char* order) {
+  if constexpr (N == 2) {
+    if (jb.fast) {
+      mesh_run<N, L, true>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0,
+                           taps, sdx, sdy, order);
+      return;
+    }
+  }
   mesh_run<N, L>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0, taps, sdx,
                  sdy);
 }
 
+// A unit is the 32-column runs of kMeshWarps consecutive rows of one image (one
+// per warp of the CTA, as in the single-image launch); CTAs take units from a
+// global counter.  One kernel per order n, so that each gets its own register
+// budget; the images of one launch share n and differ in size and limbs.
+template <int N>
 __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
                                                                      unsigned long long* counter) {
-  __shared__ int s_dx1[9], s_dy1[9], s_dx2[32], s_dy2[32], s_dx3[69], s_dy3[69];
-  __shared__ int4 s_tap[kMeshWarps][kMaxTaps];
+  constexpr int R = stencil_count<N>();
+  constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
+  __shared__ int s_dx[R], s_dy[R];
+  __shared__ unsigned char s_order[TAPS];
+  __shared__ int4 s_tap[kMeshWarps][TAPS];
+  __shared__ unsigned long long s_item;
   if (threadIdx.x == 0) {
-    fill_stencil<1>(s_dx1, s_dy1);
-    fill_stencil<2>(s_dx2, s_dy2);
-    fill_stencil<3>(s_dx3, s_dy3);
+    fill_stencil<N>(s_dx, s_dy);
+    if constexpr (N == 2) fill_n2_order(s_order);
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  int4* taps = s_tap[threadIdx.x >> 5];
+  const int warp = threadIdx.x >> 5;
+  int4* taps = s_tap[warp];
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(counter, 1ull);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if ((long long)item >= jobs.total_runs) break;
-    int lo = 0, hi = jobs.njobs - 1;  // last job with runs_begin <= item
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+    __syncthreads();
+    const unsigned long long item = s_item;
+    __syncthreads();
+    if ((long long)item >= jobs.total_units) break;
+    int lo = 0, hi = jobs.njobs - 1;  // last job with units_begin <= item
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (jobs.job[mid].runs_begin <= (long long)item) lo = mid;
+      if (jobs.job[mid].units_begin <= (long long)item) lo = mid;
       else hi = mid - 1;
     }
     const BatchJob& jb = jobs.job[lo];
-    const long long r = (long long)item - jb.runs_begin;
-    const int y = (int)(r / jb.segs);
-    const int x0 = (int)(r - (long long)y * jb.segs) * 32;
-    switch (jb.pv.n * 8 + jb.pv.limbs) {
-      case 9: batch_dispatch_L<1, 1>(jb, y, x0, taps, s_dx1, s_dy1); break;
-      case 10: batch_dispatch_L<1, 2>(jb, y, x0, taps, s_dx1, s_dy1); break;
-      case 11: batch_dispatch_L<1, 3>(jb, y, x0, taps, s_dx1, s_dy1); break;
-      case 12: batch_dispatch_L<1, 4>(jb, y, x0, taps, s_dx1, s_dy1); break;
-      case 17: batch_dispatch_L<2, 1>(jb, y, x0, taps, s_dx2, s_dy2); break;
-      case 18: batch_dispatch_L<2, 2>(jb, y, x0, taps, s_dx2, s_dy2); break;
-      case 19: batch_dispatch_L<2, 3>(jb, y, x0, taps, s_dx2, s_dy2); break;
-      case 20: batch_dispatch_L<2, 4>(jb, y, x0, taps, s_dx2, s_dy2); break;
-      case 25: batch_dispatch_L<3, 1>(jb, y, x0, taps, s_dx3, s_dy3); break;
-      case 26: batch_dispatch_L<3, 2>(jb, y, x0, taps, s_dx3, s_dy3); break;
-      case 27: batch_dispatch_L<3, 3>(jb, y, x0, taps, s_dx3, s_dy3); break;
-      default: batch_dispatch_L<3, 4>(jb, y, x0, taps, s_dx3, s_dy3); break;
+    const long long u = (long long)item - jb.units_begin;
+    const int band = (int)(u / jb.segs);
+    const int y = band * kMeshWarps + warp;
+    const int x0 = (int)(u - (long long)band * jb.segs) * 32;
+    if (y >= jb.pv.H) continue;
+    switch (jb.pv.limbs) {
+      case 1: batch_dispatch_L<N, 1>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
+      case 2: batch_dispatch_L<N, 2>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
+      case 3: batch_dispatch_L<N, 3>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
+      default: batch_dispatch_L<N, 4>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
     }
   }
 }
@@ -425,15 +526,27 @@ cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t sc
   return cudaGetLastError();
 }
 
+// The n = 2 fast path addresses g with 32-bit element offsets (rows -2 .. Gh
+// of pitch Gp) and parks taps below the image on rows 0 .. 5 of the box.
+static bool mesh_fast_ok(const PlanView& pv) {
+  return pv.n == 2 && pv.Gh >= 6 && ((long long)pv.Gh + 8) * pv.Gp < (1ll << 31);
+}
+
 template <int N, int L>
 static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch,
                                   void* s, size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
                                   cudaStream_t st) {
-  const long long warps = (long long)((pv.W + 31) / 32) * pv.H;
+  const long long grid = (long long)((pv.W + 31) / 32) * ((pv.H + kMeshWarps - 1) / kMeshWarps);
   const int block = 32 * kMeshWarps;
-  const long long grid = (warps + kMeshWarps - 1) / kMeshWarps;
-  mesh_exact_kernel<N, L><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch, num,
-                                                  num_pitch, status);
+  if constexpr (N == 2) {
+    if (mesh_fast_ok(pv)) {
+      mesh_exact_kernel<N, L, true><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
+                                                            num, num_pitch, status);
+      return cudaGetLastError();
+    }
+  }
+  mesh_exact_kernel<N, L, false><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch, num,
+                                                         num_pitch, status);
   return cudaGetLastError();
 }
 
@@ -472,46 +585,59 @@ struct BatchIn {
 
 int batch_max_jobs() { return kMaxBatch; }
 
-cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st) {
-  BatchJobs jobs;
-  jobs.njobs = njobs;
-  int order[kMaxBatch];
-  for (int i = 0; i < njobs; ++i) order[i] = i;
-  auto cost = [&](int i) {
-    const double macs = (double)((in[i].pv.n + 1) * (in[i].pv.n + 1)) * (in[i].pv.n + 1) * (in[i].pv.n + 1);
-    return macs * in[i].pv.limbs * (double)in[i].pv.W * in[i].pv.H;
-  };
-  for (int i = 1; i < njobs; ++i)
-    for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) {
-      const int t = order[j];
-      order[j] = order[j - 1];
-      order[j - 1] = t;
-    }
-  long long runs = 0;
-  for (int k = 0; k < njobs; ++k) {
-    const BatchIn& b = in[order[k]];
-    BatchJob& jb = jobs.job[k];
-    jb.pv = b.pv;
-    jb.g = b.g;
-    jb.scales = (const float4*)b.scales;
-    jb.scale_pitch = b.scale_pitch;
-    jb.s = b.s;
-    jb.s_pitch = b.s_pitch;
-    jb.status = b.status;
-    jb.segs = (b.pv.W + 31) / 32;
-    jb.runs_begin = runs;
-    runs += (long long)jb.segs * b.pv.H;
-  }
-  jobs.total_runs = runs;
+template <int N>
+static cudaError_t launch_batch_N(const BatchJobs& jobs, unsigned long long* counter, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel, 32 * kMeshWarps, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel<N>, 32 * kMeshWarps, 0);
   if (per_sm < 1) per_sm = 1;
-  mesh_batch_kernel<<<sms * per_sm, 32 * kMeshWarps, 0, st>>>(jobs, counter);
+  mesh_batch_kernel<N><<<sms * per_sm, 32 * kMeshWarps, 0, st>>>(jobs, counter);
   return cudaGetLastError();
+}
+
+// counter: three 64-bit counters (one per order n), device memory.
+cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st) {
+  auto cost = [&](int i) { return (double)in[i].pv.limbs * (double)in[i].pv.W * in[i].pv.H; };
+  for (int n = 3; n >= 1; --n) {
+    int order[kMaxBatch];
+    int m = 0;
+    for (int i = 0; i < njobs; ++i)
+      if (in[i].pv.n == n) order[m++] = i;
+    if (m == 0) continue;
+    for (int i = 1; i < m; ++i)
+      for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) {
+        const int t = order[j];
+        order[j] = order[j - 1];
+        order[j - 1] = t;
+      }
+    BatchJobs jobs;
+    jobs.njobs = m;
+    long long units = 0;
+    for (int k = 0; k < m; ++k) {
+      const BatchIn& b = in[order[k]];
+      BatchJob& jb = jobs.job[k];
+      jb.pv = b.pv;
+      jb.g = b.g;
+      jb.scales = (const float4*)b.scales;
+      jb.scale_pitch = b.scale_pitch;
+      jb.s = b.s;
+      jb.s_pitch = b.s_pitch;
+      jb.status = b.status;
+      jb.segs = (b.pv.W + 31) / 32;
+      jb.fast = mesh_fast_ok(b.pv) ? 1 : 0;
+      jb.units_begin = units;
+      units += (long long)jb.segs * ((b.pv.H + kMeshWarps - 1) / kMeshWarps);
+    }
+    jobs.total_units = units;
+    cudaError_t e = n == 1 ? launch_batch_N<1>(jobs, counter + n - 1, st)
+                   : n == 2 ? launch_batch_N<2>(jobs, counter + n - 1, st)
+                            : launch_batch_N<3>(jobs, counter + n - 1, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t scale_pitch, void* C, size_t C_pitch,

@@ -250,9 +250,13 @@ abf_status get_table(int device, int n, int P, DeviceTable* out) {
   } catch (const std::bad_alloc&) {
     return ABF_ERR_OOM;
   }
+  // One all-zero row follows the 2^(2P) table rows: a tap known to read only
+  // zeros of g may point there instead of being tested per lane.
   DeviceTable dt;
-  if (cudaMalloc(&dt.ptr, ht.bytes.size()) != cudaSuccess) return ABF_ERR_OOM;
-  if (cudaMemcpy(dt.ptr, ht.bytes.data(), ht.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+  const size_t row_bytes = (size_t)ht.row_len * ht.wbytes;
+  if (cudaMalloc(&dt.ptr, ht.bytes.size() + row_bytes) != cudaSuccess) return ABF_ERR_OOM;
+  if (cudaMemcpy(dt.ptr, ht.bytes.data(), ht.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset((char*)dt.ptr + ht.bytes.size(), 0, row_bytes) != cudaSuccess) {
     cudaFree(dt.ptr);
     return ABF_ERR_CUDA;
   }

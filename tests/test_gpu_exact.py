@@ -98,6 +98,18 @@ def test_degenerate_sizes(n, shape):
     _check_all_pixels(w, res)
 
 
+@pytest.mark.parametrize("shape", [(1, 40), (3, 40), (2, 70)])
+def test_order2_shallow_box(shape):
+    """Scales below one leave a lattice box of fewer than 3n rows (H + above
+    < 6 for shape (1, 40)): the n = 2 mesh then runs its general path; (3, 40)
+    sits exactly at the fast path's limit of six rows."""
+    w = _small_workload(2, shape, 4, "u8", 30 + shape[0], lo=0.3, hi=0.9)
+    w["min_scale"] = 0.1
+    res = gu.run_exact(w)
+    assert res["status"] == 0
+    _check_all_pixels(w, res)
+
+
 def test_zero_and_constant_images():
     for val in (0, 200):
         w = _small_workload(1, (20, 30), 3, "u8", 7)
