@@ -104,9 +104,23 @@ def _dist():
     return world, rank, local
 
 
-def _workload(name, rank):
+def _workload(name, rank, shape=None):
     import synthetic
-    return synthetic.workload(name, seed_offset=rank)
+    return synthetic.workload(name, shape=shape, seed_offset=rank)
+
+
+WORKLOAD_TEXT = {
+    "c1": "f64 integers 0..255, order n=1, paper scales a_k in [1,8], Q=8",
+    "c2": "f32 (2^-16 grid), order n=2, per-pixel ellipse (sigma 1-24, elongation 1-6), Q=8",
+    "c3": "u16, order n=3, paper scales a_k in [1,48], Q=8",
+}
+
+
+def _shape(args):
+    if not args.shape:
+        return None
+    h, w = args.shape.lower().split("x")
+    return int(h), int(w)
 
 
 MESH_DRAM_BYTES = 158916096 + 15363072
@@ -117,6 +131,14 @@ def _algorithmic_macs(n):
     of the support octagon of ZP^{*n}, i.e. its average count of non-zero
     lattice weights)."""
     return (n + 1) ** 4 * 7 * n * n
+
+
+def _host_tensor(img):
+    """numpy image -> CPU tensor (uint16 through an int16 view: numpy has no torch bridge for it)."""
+    import torch
+    if img.dtype == np.uint16:
+        return torch.from_numpy(img.view(np.int16).copy()).view(torch.uint16)
+    return torch.from_numpy(np.ascontiguousarray(img))
 
 
 def max_over_ranks(ms, world, device):
@@ -150,11 +172,11 @@ def run_ours(args):
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
-    w = _workload(args.workload, rank)
+    w = _workload(args.workload, rank, _shape(args))
     img, sc = w["image"], w["scales"]
     H, W = img.shape
     n = w["n"]
-    f_t = torch.from_numpy(img).to(dev)
+    f_t = _host_tensor(img).to(dev)
     s_t = torch.from_numpy(sc.astype(np.float32)).to(dev)
     d = _abf.abf_desc()
     d.width, d.height, d.order_n = W, H, n
@@ -162,7 +184,7 @@ def run_ours(args):
     d.q_bits, d.max_scale = w["q_bits"], w["cmax"]
     _, max_prod = _abf.abf_measure_scales(d, s_t, W * 16)
     tin = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64,
-           np.dtype(np.uint8): torch.uint8}[img.dtype]
+           np.dtype(np.uint8): torch.uint8, np.dtype(np.uint16): torch.uint16}[img.dtype]
     filt = AdaptiveFilter(W, H, n, tin, scale_kind=w["scale_kind"], q_bits=w["q_bits"], frac_bits=w["frac_bits"],
                           max_scale=w["cmax"], out="f32", value_bound=w["value_bound"],
                           max_scale_product=max_prod, device=dev)
@@ -204,7 +226,7 @@ def run_ours(args):
     assert filt.device_status() == 0
 
     # End to end through the public API with host buffers (pinned), H2D + D2H inside.
-    f_h = torch.from_numpy(img).pin_memory()
+    f_h = _host_tensor(img).pin_memory()
     s_h = torch.from_numpy(sc.astype(np.float32)).pin_memory()
     o_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
     f_d = torch.empty_like(f_t)
@@ -275,8 +297,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64x%d" % L, "data": "synthetic",
-        "config": {"workload": "2048x2048 f32 (2^-16 grid), order n=2, per-pixel ellipse (sigma 1-24, "
-                               "elongation 1-6), Q=8, exact form (%d-limb wrap-around integers)" % L,
+        "config": {"workload": "%dx%d %s, exact form (%d-limb wrap-around integers)" % (
+                       H, W, WORKLOAD_TEXT[args.workload], L),
                    "image": [H, W], "order_n": n, "form": "exact", "limbs": L,
                    "l2": "inputs larger than L2 (integrated image %.0f MB + scales %.0f MB)" % (
                        filt.info["integrated_bytes"] / 1e6, H * W * 16 / 1e6),
@@ -522,7 +544,7 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    w = _workload(args.workload, 0)
+    w = _workload(args.workload, 0, _shape(args))
     K = args.steps
     for _ in range(args.warmup):
         cpu_baseline(w, seconds=0.0, sample=1)
@@ -539,7 +561,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": el * 1e3 / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "exact (python int)", "data": "synthetic",
-            "config": {"workload": "2048x2048 f32 (2^-16 grid), order n=2, per-pixel ellipse, Q=8"},
+            "config": {"workload": "%dx%d %s" % (w["image"].shape[0], w["image"].shape[1],
+                                                   WORKLOAD_TEXT[args.workload])},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d random pixels per step, exact per-pixel evaluation" % (tot_pix // K)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -553,6 +576,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
+    ap.add_argument("--shape", default="", help="HxW: the same recipe at another size (profiling, sweeps)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--pool", type=int, default=8, help="c5: distinct images in the request pool")

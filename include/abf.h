@@ -185,7 +185,7 @@ typedef struct {
 } abf_job;
 
 /* Adaptive step (Eq. (final_eqn)) for many images of uneven size, order and
- * limb count in one persistent launch per order n present: the images' units
+ * limb count in one persistent launch per (order n, limbs) present: the images' units
  * (8 rows x 32 columns) are numbered (largest images first) and every CTA
  * takes the next unit from a device counter, so the work stays balanced
  * across SMs.  Each image's result is bit-identical to abf_filter on that

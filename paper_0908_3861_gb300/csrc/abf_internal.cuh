@@ -133,6 +133,232 @@ __device__ __forceinline__ void wmac2_u64(Wide<2>& acc, const Wide<2>& g, uint64
   acc.w[1] = ((uint64_t)r3 << 32) | r2;
 }
 
+// Carry-chained multiply-accumulates for wider limbs and weights (written by
+// gen_mac_chains.py beside this file, which also checks the schedule).
+// acc += g * w (mod 2^192): 3-limb g, 64-bit w; 20 multiply-adds in carry chains.
+__device__ __forceinline__ void wmac_w6_b2(Wide<3>& acc, const Wide<3>& g, uint32_t w0, uint32_t w1) {
+  uint32_t r[6], a[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[2 * i] = (uint32_t)acc.w[i]; r[2 * i + 1] = (uint32_t)(acc.w[i] >> 32);
+    a[2 * i] = (uint32_t)g.w[i]; a[2 * i + 1] = (uint32_t)(g.w[i] >> 32);
+  }
+  asm("{\n\t"
+      "mad.lo.cc.u32   %0, %6, %12, %0;\n\t"
+      "madc.hi.cc.u32  %1, %6, %12, %1;\n\t"
+      "madc.hi.cc.u32  %2, %7, %12, %2;\n\t"
+      "madc.hi.cc.u32  %3, %8, %12, %3;\n\t"
+      "madc.hi.cc.u32  %4, %9, %12, %4;\n\t"
+      "madc.hi.u32     %5, %10, %12, %5;\n\t"
+      "mad.lo.cc.u32   %1, %7, %12, %1;\n\t"
+      "madc.lo.cc.u32  %2, %8, %12, %2;\n\t"
+      "madc.lo.cc.u32  %3, %9, %12, %3;\n\t"
+      "madc.lo.cc.u32  %4, %10, %12, %4;\n\t"
+      "madc.lo.u32     %5, %11, %12, %5;\n\t"
+      "mad.lo.cc.u32   %1, %6, %13, %1;\n\t"
+      "madc.hi.cc.u32  %2, %6, %13, %2;\n\t"
+      "madc.hi.cc.u32  %3, %7, %13, %3;\n\t"
+      "madc.hi.cc.u32  %4, %8, %13, %4;\n\t"
+      "madc.hi.u32     %5, %9, %13, %5;\n\t"
+      "mad.lo.cc.u32   %2, %7, %13, %2;\n\t"
+      "madc.lo.cc.u32  %3, %8, %13, %3;\n\t"
+      "madc.lo.cc.u32  %4, %9, %13, %4;\n\t"
+      "madc.lo.u32     %5, %10, %13, %5;\n\t"
+      "}"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(w0), "r"(w1));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc.w[i] = ((uint64_t)r[2 * i + 1] << 32) | r[2 * i];
+}
+
+// acc += g * w (mod 2^256): 4-limb g, 64-bit w; 28 multiply-adds in carry chains.
+__device__ __forceinline__ void wmac_w8_b2(Wide<4>& acc, const Wide<4>& g, uint32_t w0, uint32_t w1) {
+  uint32_t r[8], a[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    r[2 * i] = (uint32_t)acc.w[i]; r[2 * i + 1] = (uint32_t)(acc.w[i] >> 32);
+    a[2 * i] = (uint32_t)g.w[i]; a[2 * i + 1] = (uint32_t)(g.w[i] >> 32);
+  }
+  asm("{\n\t"
+      "mad.lo.cc.u32   %0, %8, %16, %0;\n\t"
+      "madc.hi.cc.u32  %1, %8, %16, %1;\n\t"
+      "madc.hi.cc.u32  %2, %9, %16, %2;\n\t"
+      "madc.hi.cc.u32  %3, %10, %16, %3;\n\t"
+      "madc.hi.cc.u32  %4, %11, %16, %4;\n\t"
+      "madc.hi.cc.u32  %5, %12, %16, %5;\n\t"
+      "madc.hi.cc.u32  %6, %13, %16, %6;\n\t"
+      "madc.hi.u32     %7, %14, %16, %7;\n\t"
+      "mad.lo.cc.u32   %1, %9, %16, %1;\n\t"
+      "madc.lo.cc.u32  %2, %10, %16, %2;\n\t"
+      "madc.lo.cc.u32  %3, %11, %16, %3;\n\t"
+      "madc.lo.cc.u32  %4, %12, %16, %4;\n\t"
+      "madc.lo.cc.u32  %5, %13, %16, %5;\n\t"
+      "madc.lo.cc.u32  %6, %14, %16, %6;\n\t"
+      "madc.lo.u32     %7, %15, %16, %7;\n\t"
+      "mad.lo.cc.u32   %1, %8, %17, %1;\n\t"
+      "madc.hi.cc.u32  %2, %8, %17, %2;\n\t"
+      "madc.hi.cc.u32  %3, %9, %17, %3;\n\t"
+      "madc.hi.cc.u32  %4, %10, %17, %4;\n\t"
+      "madc.hi.cc.u32  %5, %11, %17, %5;\n\t"
+      "madc.hi.cc.u32  %6, %12, %17, %6;\n\t"
+      "madc.hi.u32     %7, %13, %17, %7;\n\t"
+      "mad.lo.cc.u32   %2, %9, %17, %2;\n\t"
+      "madc.lo.cc.u32  %3, %10, %17, %3;\n\t"
+      "madc.lo.cc.u32  %4, %11, %17, %4;\n\t"
+      "madc.lo.cc.u32  %5, %12, %17, %5;\n\t"
+      "madc.lo.cc.u32  %6, %13, %17, %6;\n\t"
+      "madc.lo.u32     %7, %14, %17, %7;\n\t"
+      "}"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(w0), "r"(w1));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.w[i] = ((uint64_t)r[2 * i + 1] << 32) | r[2 * i];
+}
+
+// acc += g * w (mod 2^128): 2-limb g, 128-bit w; 16 multiply-adds in carry chains.
+__device__ __forceinline__ void wmac_w4_b4(Wide<2>& acc, const Wide<2>& g, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  uint32_t r[4], a[4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    r[2 * i] = (uint32_t)acc.w[i]; r[2 * i + 1] = (uint32_t)(acc.w[i] >> 32);
+    a[2 * i] = (uint32_t)g.w[i]; a[2 * i + 1] = (uint32_t)(g.w[i] >> 32);
+  }
+  asm("{\n\t"
+      "mad.lo.cc.u32   %0, %4, %8, %0;\n\t"
+      "madc.hi.cc.u32  %1, %4, %8, %1;\n\t"
+      "madc.hi.cc.u32  %2, %5, %8, %2;\n\t"
+      "madc.hi.u32     %3, %6, %8, %3;\n\t"
+      "mad.lo.cc.u32   %1, %5, %8, %1;\n\t"
+      "madc.lo.cc.u32  %2, %6, %8, %2;\n\t"
+      "madc.lo.u32     %3, %7, %8, %3;\n\t"
+      "mad.lo.cc.u32   %1, %4, %9, %1;\n\t"
+      "madc.hi.cc.u32  %2, %4, %9, %2;\n\t"
+      "madc.hi.u32     %3, %5, %9, %3;\n\t"
+      "mad.lo.cc.u32   %2, %5, %9, %2;\n\t"
+      "madc.lo.u32     %3, %6, %9, %3;\n\t"
+      "mad.lo.cc.u32   %2, %4, %10, %2;\n\t"
+      "madc.hi.u32     %3, %4, %10, %3;\n\t"
+      "mad.lo.u32      %3, %5, %10, %3;\n\t"
+      "mad.lo.u32      %3, %4, %11, %3;\n\t"
+      "}"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(w0), "r"(w1), "r"(w2), "r"(w3));
+#pragma unroll
+  for (int i = 0; i < 2; ++i) acc.w[i] = ((uint64_t)r[2 * i + 1] << 32) | r[2 * i];
+}
+
+// acc += g * w (mod 2^192): 3-limb g, 128-bit w; 32 multiply-adds in carry chains.
+__device__ __forceinline__ void wmac_w6_b4(Wide<3>& acc, const Wide<3>& g, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  uint32_t r[6], a[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[2 * i] = (uint32_t)acc.w[i]; r[2 * i + 1] = (uint32_t)(acc.w[i] >> 32);
+    a[2 * i] = (uint32_t)g.w[i]; a[2 * i + 1] = (uint32_t)(g.w[i] >> 32);
+  }
+  asm("{\n\t"
+      "mad.lo.cc.u32   %0, %6, %12, %0;\n\t"
+      "madc.hi.cc.u32  %1, %6, %12, %1;\n\t"
+      "madc.hi.cc.u32  %2, %7, %12, %2;\n\t"
+      "madc.hi.cc.u32  %3, %8, %12, %3;\n\t"
+      "madc.hi.cc.u32  %4, %9, %12, %4;\n\t"
+      "madc.hi.u32     %5, %10, %12, %5;\n\t"
+      "mad.lo.cc.u32   %1, %7, %12, %1;\n\t"
+      "madc.lo.cc.u32  %2, %8, %12, %2;\n\t"
+      "madc.lo.cc.u32  %3, %9, %12, %3;\n\t"
+      "madc.lo.cc.u32  %4, %10, %12, %4;\n\t"
+      "madc.lo.u32     %5, %11, %12, %5;\n\t"
+      "mad.lo.cc.u32   %1, %6, %13, %1;\n\t"
+      "madc.hi.cc.u32  %2, %6, %13, %2;\n\t"
+      "madc.hi.cc.u32  %3, %7, %13, %3;\n\t"
+      "madc.hi.cc.u32  %4, %8, %13, %4;\n\t"
+      "madc.hi.u32     %5, %9, %13, %5;\n\t"
+      "mad.lo.cc.u32   %2, %7, %13, %2;\n\t"
+      "madc.lo.cc.u32  %3, %8, %13, %3;\n\t"
+      "madc.lo.cc.u32  %4, %9, %13, %4;\n\t"
+      "madc.lo.u32     %5, %10, %13, %5;\n\t"
+      "mad.lo.cc.u32   %2, %6, %14, %2;\n\t"
+      "madc.hi.cc.u32  %3, %6, %14, %3;\n\t"
+      "madc.hi.cc.u32  %4, %7, %14, %4;\n\t"
+      "madc.hi.u32     %5, %8, %14, %5;\n\t"
+      "mad.lo.cc.u32   %3, %7, %14, %3;\n\t"
+      "madc.lo.cc.u32  %4, %8, %14, %4;\n\t"
+      "madc.lo.u32     %5, %9, %14, %5;\n\t"
+      "mad.lo.cc.u32   %3, %6, %15, %3;\n\t"
+      "madc.hi.cc.u32  %4, %6, %15, %4;\n\t"
+      "madc.hi.u32     %5, %7, %15, %5;\n\t"
+      "mad.lo.cc.u32   %4, %7, %15, %4;\n\t"
+      "madc.lo.u32     %5, %8, %15, %5;\n\t"
+      "}"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(w0), "r"(w1), "r"(w2), "r"(w3));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) acc.w[i] = ((uint64_t)r[2 * i + 1] << 32) | r[2 * i];
+}
+
+// acc += g * w (mod 2^256): 4-limb g, 128-bit w; 48 multiply-adds in carry chains.
+__device__ __forceinline__ void wmac_w8_b4(Wide<4>& acc, const Wide<4>& g, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  uint32_t r[8], a[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    r[2 * i] = (uint32_t)acc.w[i]; r[2 * i + 1] = (uint32_t)(acc.w[i] >> 32);
+    a[2 * i] = (uint32_t)g.w[i]; a[2 * i + 1] = (uint32_t)(g.w[i] >> 32);
+  }
+  asm("{\n\t"
+      "mad.lo.cc.u32   %0, %8, %16, %0;\n\t"
+      "madc.hi.cc.u32  %1, %8, %16, %1;\n\t"
+      "madc.hi.cc.u32  %2, %9, %16, %2;\n\t"
+      "madc.hi.cc.u32  %3, %10, %16, %3;\n\t"
+      "madc.hi.cc.u32  %4, %11, %16, %4;\n\t"
+      "madc.hi.cc.u32  %5, %12, %16, %5;\n\t"
+      "madc.hi.cc.u32  %6, %13, %16, %6;\n\t"
+      "madc.hi.u32     %7, %14, %16, %7;\n\t"
+      "mad.lo.cc.u32   %1, %9, %16, %1;\n\t"
+      "madc.lo.cc.u32  %2, %10, %16, %2;\n\t"
+      "madc.lo.cc.u32  %3, %11, %16, %3;\n\t"
+      "madc.lo.cc.u32  %4, %12, %16, %4;\n\t"
+      "madc.lo.cc.u32  %5, %13, %16, %5;\n\t"
+      "madc.lo.cc.u32  %6, %14, %16, %6;\n\t"
+      "madc.lo.u32     %7, %15, %16, %7;\n\t"
+      "mad.lo.cc.u32   %1, %8, %17, %1;\n\t"
+      "madc.hi.cc.u32  %2, %8, %17, %2;\n\t"
+      "madc.hi.cc.u32  %3, %9, %17, %3;\n\t"
+      "madc.hi.cc.u32  %4, %10, %17, %4;\n\t"
+      "madc.hi.cc.u32  %5, %11, %17, %5;\n\t"
+      "madc.hi.cc.u32  %6, %12, %17, %6;\n\t"
+      "madc.hi.u32     %7, %13, %17, %7;\n\t"
+      "mad.lo.cc.u32   %2, %9, %17, %2;\n\t"
+      "madc.lo.cc.u32  %3, %10, %17, %3;\n\t"
+      "madc.lo.cc.u32  %4, %11, %17, %4;\n\t"
+      "madc.lo.cc.u32  %5, %12, %17, %5;\n\t"
+      "madc.lo.cc.u32  %6, %13, %17, %6;\n\t"
+      "madc.lo.u32     %7, %14, %17, %7;\n\t"
+      "mad.lo.cc.u32   %2, %8, %18, %2;\n\t"
+      "madc.hi.cc.u32  %3, %8, %18, %3;\n\t"
+      "madc.hi.cc.u32  %4, %9, %18, %4;\n\t"
+      "madc.hi.cc.u32  %5, %10, %18, %5;\n\t"
+      "madc.hi.cc.u32  %6, %11, %18, %6;\n\t"
+      "madc.hi.u32     %7, %12, %18, %7;\n\t"
+      "mad.lo.cc.u32   %3, %9, %18, %3;\n\t"
+      "madc.lo.cc.u32  %4, %10, %18, %4;\n\t"
+      "madc.lo.cc.u32  %5, %11, %18, %5;\n\t"
+      "madc.lo.cc.u32  %6, %12, %18, %6;\n\t"
+      "madc.lo.u32     %7, %13, %18, %7;\n\t"
+      "mad.lo.cc.u32   %3, %8, %19, %3;\n\t"
+      "madc.hi.cc.u32  %4, %8, %19, %4;\n\t"
+      "madc.hi.cc.u32  %5, %9, %19, %5;\n\t"
+      "madc.hi.cc.u32  %6, %10, %19, %6;\n\t"
+      "madc.hi.u32     %7, %11, %19, %7;\n\t"
+      "mad.lo.cc.u32   %4, %9, %19, %4;\n\t"
+      "madc.lo.cc.u32  %5, %10, %19, %5;\n\t"
+      "madc.lo.cc.u32  %6, %11, %19, %6;\n\t"
+      "madc.lo.u32     %7, %12, %19, %7;\n\t"
+      "}"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(w0), "r"(w1), "r"(w2), "r"(w3));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.w[i] = ((uint64_t)r[2 * i + 1] << 32) | r[2 * i];
+}
+
 // acc += g * w (mod 2^128) for a two-limb g and a 32-bit w (seven partial products).
 __device__ __forceinline__ void wmac2_u32(Wide<2>& acc, const Wide<2>& g, uint32_t w0) {
   uint32_t r0 = (uint32_t)acc.w[0], r1 = (uint32_t)(acc.w[0] >> 32);

@@ -54,10 +54,16 @@ template <> struct WeightT<3> { using T = ulonglong2; };
 template <int L, typename WT>
 __device__ __forceinline__ void mac_weight(Wide<L>& acc, const Wide<L>& gv, const WT w) {
   if constexpr (sizeof(WT) == 16) {
-    wmac128<L>(acc, gv, w.x, w.y);
-  } else if constexpr (L == 2 && sizeof(WT) == 8) {
-    wmac2_u64(acc, gv, w);
-  } else if constexpr (L == 2 && sizeof(WT) == 4) {
+    if constexpr (L == 1) wmac<1>(acc, gv, w.x);
+    else if constexpr (L == 2) wmac_w4_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
+    else if constexpr (L == 3) wmac_w6_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
+    else wmac_w8_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
+  } else if constexpr (sizeof(WT) == 8) {
+    if constexpr (L == 1) wmac<1>(acc, gv, w);
+    else if constexpr (L == 2) wmac2_u64(acc, gv, w);
+    else if constexpr (L == 3) wmac_w6_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
+    else wmac_w8_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
+  } else if constexpr (L == 2) {
     wmac2_u32(acc, gv, w);
   } else {
     wmac<L>(acc, gv, (uint64_t)w);
@@ -139,6 +145,74 @@ __device__ __forceinline__ void fill_n2_order(unsigned char* order) {
     }
 }
 
+// n = 3: w_j = (-1)^(j1+j2+j3+j4) 3^m, m = #{i : j_i in {1, 2}}.  The taps are
+// visited in ten groups, by m and then by the parity of sum j (group size
+// binom(4,m) 8 each), each group summed without its weight and then added
+// with it.
+__host__ __device__ constexpr int n3_group_begin(int g) {
+  return g <= 0 ? 0 : g == 1 ? 8 : g == 2 ? 16 : g == 3 ? 48 : g == 4 ? 80 : g == 5 ? 128 : g == 6 ? 176
+         : g == 7 ? 208 : g == 8 ? 240 : g == 9 ? 248 : 256;
+}
+
+// Tap order for n = 3 (one thread): slot -> natural tap index t = j1 + 4 j3 + 16 j2 + 64 j4.
+__device__ __forceinline__ void fill_n3_order(unsigned char* order) {
+  int c = 0;
+  for (int m = 0; m <= 4; ++m)
+    for (int par = 0; par <= 1; ++par)
+      for (int t = 0; t < 256; ++t) {
+        int mm = 0, sum = 0;
+        for (int u = t, i = 0; i < 4; ++i, u /= 4) {
+          mm += (u % 4 == 1 || u % 4 == 2);
+          sum += u % 4;
+        }
+        if (mm == m && (sum & 1) == par) order[c++] = (unsigned char)t;
+      }
+}
+
+// One pixel's numerator share for n = 3.  The 69 stencil neighbours do not
+// fit a warp, so the (tap, neighbour) pairs of a group are dealt to the lanes
+// in order: lane i starts at neighbour i of the group's first tap and steps by
+// 32 pairs.  taps[s] = (g offset of the tap's lattice point, table offset,
+// lattice row); s_off[c] = dy_c Gp + dx_c.  CHECK drops reads of rows below 0.
+template <int L, bool CHECK>
+__device__ __forceinline__ void n3_pixel(Wide<L>& acc, const int4* taps, const uint64_t* __restrict__ g,
+                                         const ulonglong2* __restrict__ table, const int* s_off, const int* s_dy,
+                                         int lane) {
+  constexpr int R = 69;
+#pragma unroll 1
+  for (int gi = 0; gi < 10; ++gi) {
+    const int tb = n3_group_begin(gi), te = n3_group_begin(gi + 1);
+    const int pairs = (te - tb) * R;
+    Wide<L> part;
+    wzero<L>(part);
+    int t = tb, c = lane;
+#pragma unroll 4
+    for (int p0 = 0; p0 < pairs; p0 += 32) {
+      if (p0 + lane < pairs) {
+        const int4 ti = taps[t];
+        if (!CHECK || ti.z + s_dy[c] >= 0) {
+          const Wide<L> gv = wload<L>(g + (ptrdiff_t)(ti.x + s_off[c]) * L);
+          const ulonglong2 wt = __ldg(table + ti.y + c);
+          mac_weight<L, ulonglong2>(part, gv, wt);
+        }
+      }
+      c += 32;
+      if (c >= R) {
+        c -= R;
+        ++t;
+      }
+    }
+    // group weight (-1)^parity 3^m, m = gi / 2
+    const int m = gi >> 1;
+    const uint64_t w3 = m == 0 ? 1 : m == 1 ? 3 : m == 2 ? 9 : m == 3 ? 27 : 81;
+    Wide<L> scaled;
+    wzero<L>(scaled);
+    wmac<L>(scaled, part, w3);
+    if (gi & 1) wsub<L>(acc, scaled);
+    else wadd<L>(acc, scaled);
+  }
+}
+
 // One pixel's numerator share for n = 2 (lane = neighbour): taps[s] holds
 // (x: g offset of the tap's lattice point from this lane's base gl, y: table
 // offset from this lane's base tl, z: the tap's lattice row).  A tap whose
@@ -168,16 +242,18 @@ __device__ __forceinline__ void n2_pixel(Wide<L>& acc, const int4* taps, const u
 
 // Mesh for the run of 32 pixels (x0 .. x0+31, y) of one image; the whole warp
 // calls it.  taps: this warp's (n+1)^4-entry shared tap table; s_dx/s_dy: the
-// order-n stencil in shared memory.  FAST (n = 2 only): lanes keep their
-// neighbour's g and table bases, taps carry plain offsets, and the FD weights
-// are applied per group (n2_pixel); s_order is then the group-sorted tap order,
-// and g offsets must fit 32 bits and the box have at least 3n rows.
+// order-n stencil in shared memory.  FAST (n = 2, 3): taps carry plain g and
+// table offsets, and the FD weights are applied per group (n2_pixel,
+// n3_pixel); s_order is then the group-sorted tap order, s_off (n = 3) the
+// neighbours' g offsets dy Gp + dx, and g offsets must fit 32 bits and the
+// box have at least 3n rows.
 template <int N, int L, bool FAST = false>
 __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __restrict__ g,
                                          const float4* __restrict__ scales, size_t scale_pitch, void* __restrict__ s,
                                          size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch,
                                          int32_t* status, int y, int x0, int4* taps, const int* s_dx,
-                                         const int* s_dy, const unsigned char* s_order = nullptr) {
+                                         const int* s_dy, const unsigned char* s_order = nullptr,
+                                         const int* s_off = nullptr) {
   using WT = typename WeightT<N>::T;
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
@@ -226,8 +302,30 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
     __syncwarp();
     Wide<L> acc;
     wzero<L>(acc);
-    if constexpr (FAST) {
-      static_assert(N == 2 && R == 32, "fast path is for n = 2");
+    if constexpr (FAST && N == 3) {
+      constexpr int kDyMin = Stencil<N>::kDmin, kDyMax = Stencil<N>::kDmin + 3 * N - 1;
+      const int gp = (int)rowpitch;
+      int strad = 0;
+      for (int slot = lane; slot < TAPS; slot += 32) {
+        const int t = s_order[slot];
+        const int j1 = t & 3, j3 = (t >> 2) & 3, j2 = (t >> 4) & 3, j4 = t >> 6;
+        const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4 + half;
+        const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4 + half;
+        const int px = Yx >> P, py = Yy >> P;
+        const int r = ((Yy & mask) << P) | (Yx & mask);
+        const bool below = py + kDyMax < 0;
+        strad |= (py + kDyMin < 0) && !below;
+        const int xf = (below ? -kDyMin : py) * gp + px + left;
+        const int tf = (below ? (1 << (2 * P)) : r) * R;
+        taps[slot] = make_int4(xf, tf, py, 0);
+      }
+      const bool check = __any_sync(0xffffffffu, strad) != 0;
+      __syncwarp();
+      const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(pv.table);
+      if (check) n3_pixel<L, true>(acc, taps, g, tab, s_off, s_dy, lane);
+      else n3_pixel<L, false>(acc, taps, g, tab, s_off, s_dy, lane);
+    } else if constexpr (FAST) {
+      static_assert(N == 2 && R == 32, "fast path is for n = 2 and n = 3");
       constexpr int kDyMin = Stencil<N>::kDmin, kDyMax = Stencil<N>::kDmin + 3 * N - 1;
       const int gp = (int)rowpitch;
       int strad = 0;
@@ -361,13 +459,16 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
-  __shared__ int s_dx[R], s_dy[R];
+  __shared__ int s_dx[R], s_dy[R], s_off[R];
   __shared__ unsigned char s_order[TAPS];
   __shared__ int4 s_tap[kMeshWarps][TAPS];
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
-    if constexpr (FAST) fill_n2_order(s_order);
+    if constexpr (FAST && N == 2) fill_n2_order(s_order);
+    if constexpr (FAST && N == 3) fill_n3_order(s_order);
   }
+  __syncthreads();
+  if (threadIdx.x < R) s_off[threadIdx.x] = s_dy[threadIdx.x] * (int)pv.Gp + s_dx[threadIdx.x];
   __syncthreads();
   const int segs = (pv.W + 31) >> 5;
   const int band = blockIdx.x / segs;
@@ -375,12 +476,12 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   if (y >= pv.H) return;
   const int x0 = (blockIdx.x - band * segs) * 32;
   mesh_run<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
-                       s_tap[threadIdx.x >> 5], s_dx, s_dy, s_order);
+                       s_tap[threadIdx.x >> 5], s_dx, s_dy, s_order, s_off);
 }
 
 // ------------------------------------------------------------------- batches
 // Many images (each its own plan: size, order n, limbs) in one persistent
-// launch per order n.  The images' units (kMeshWarps rows x 32 columns) are
+// launch per (order n, limbs, fast path).  The images' units (kMeshWarps rows x 32 columns) are
 // numbered consecutively, the most expensive images first; every CTA
 // repeatedly takes the next unit from a global counter and filters it with its
 // image's plan, so images of uneven size share the GPU without a tail of idle
@@ -397,7 +498,6 @@ struct BatchJob {
   int32_t* status;
   long long units_begin;  // first global unit index of this image
   int segs;               // 32-column runs per row
-  int fast;               // n = 2 fast path usable (mesh_fast_ok)
 };
 
 struct BatchJobs {
@@ -406,36 +506,30 @@ struct BatchJobs {
   BatchJob job[kMaxBatch];
 };
 
-template <int N, int L>
+template <int N, int L, bool FAST>
 __device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int x0, int4* taps, const int* sdx,
-                                                 const int* sdy, const unsigned char* order) {
-  if constexpr (N == 2) {
-    if (jb.fast) {
-      mesh_run<N, L, true>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0,
-                           taps, sdx, sdy, order);
-      return;
-    }
-  }
-  mesh_run<N, L>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0, taps, sdx,
-                 sdy);
+                                                 const int* sdy, const unsigned char* order, const int* soff) {
+  mesh_run<N, L, FAST>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0, taps,
+                       sdx, sdy, order, soff);
 }
 
 // A unit is the 32-column runs of kMeshWarps consecutive rows of one image (one
 // per warp of the CTA, as in the single-image launch); CTAs take units from a
 // global counter.  One kernel per order n, so that each gets its own register
 // budget; the images of one launch share n and differ in size and limbs.
-template <int N>
+template <int N, int L, bool FAST>
 __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
                                                                      unsigned long long* counter) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
-  __shared__ int s_dx[R], s_dy[R];
+  __shared__ int s_dx[R], s_dy[R], s_off[R];
   __shared__ unsigned char s_order[TAPS];
   __shared__ int4 s_tap[kMeshWarps][TAPS];
   __shared__ unsigned long long s_item;
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
-    if constexpr (N == 2) fill_n2_order(s_order);
+    if constexpr (FAST && N == 2) fill_n2_order(s_order);
+    if constexpr (FAST && N == 3) fill_n3_order(s_order);
   }
   const int warp = threadIdx.x >> 5;
   int4* taps = s_tap[warp];
@@ -452,17 +546,14 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __gri
       else hi = mid - 1;
     }
     const BatchJob& jb = jobs.job[lo];
+    if (threadIdx.x < R) s_off[threadIdx.x] = s_dy[threadIdx.x] * (int)jb.pv.Gp + s_dx[threadIdx.x];
+    __syncthreads();
     const long long u = (long long)item - jb.units_begin;
     const int band = (int)(u / jb.segs);
     const int y = band * kMeshWarps + warp;
     const int x0 = (int)(u - (long long)band * jb.segs) * 32;
     if (y >= jb.pv.H) continue;
-    switch (jb.pv.limbs) {
-      case 1: batch_dispatch_L<N, 1>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
-      case 2: batch_dispatch_L<N, 2>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
-      case 3: batch_dispatch_L<N, 3>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
-      default: batch_dispatch_L<N, 4>(jb, y, x0, taps, s_dx, s_dy, s_order); break;
-    }
+    batch_dispatch_L<N, L, FAST>(jb, y, x0, taps, s_dx, s_dy, s_order, s_off);
   }
 }
 
@@ -526,10 +617,11 @@ cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t sc
   return cudaGetLastError();
 }
 
-// The n = 2 fast path addresses g with 32-bit element offsets (rows -2 .. Gh
-// of pitch Gp) and parks taps below the image on rows 0 .. 5 of the box.
+// The fast paths (n = 2, 3) address g with 32-bit element offsets (rows
+// -3n/2 .. Gh + 3n/2 of pitch Gp) and park taps below the image on rows
+// 0 .. 3n-1 of the box.
 static bool mesh_fast_ok(const PlanView& pv) {
-  return pv.n == 2 && pv.Gh >= 6 && ((long long)pv.Gh + 8) * pv.Gp < (1ll << 31);
+  return pv.n >= 2 && pv.Gh >= 3 * pv.n && ((long long)pv.Gh + 8) * pv.Gp < (1ll << 31);
 }
 
 template <int N, int L>
@@ -538,7 +630,7 @@ static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const v
                                   cudaStream_t st) {
   const long long grid = (long long)((pv.W + 31) / 32) * ((pv.H + kMeshWarps - 1) / kMeshWarps);
   const int block = 32 * kMeshWarps;
-  if constexpr (N == 2) {
+  if constexpr (N >= 2) {
     if (mesh_fast_ok(pv)) {
       mesh_exact_kernel<N, L, true><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
                                                             num, num_pitch, status);
@@ -585,57 +677,75 @@ struct BatchIn {
 
 int batch_max_jobs() { return kMaxBatch; }
 
-template <int N>
-static cudaError_t launch_batch_N(const BatchJobs& jobs, unsigned long long* counter, cudaStream_t st) {
+template <int N, int L, bool FAST>
+static cudaError_t launch_batch_NL(const BatchJobs& jobs, unsigned long long* counter, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel<N>, 32 * kMeshWarps, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel<N, L, FAST>, 32 * kMeshWarps, 0);
   if (per_sm < 1) per_sm = 1;
-  mesh_batch_kernel<N><<<sms * per_sm, 32 * kMeshWarps, 0, st>>>(jobs, counter);
+  mesh_batch_kernel<N, L, FAST><<<sms * per_sm, 32 * kMeshWarps, 0, st>>>(jobs, counter);
   return cudaGetLastError();
 }
 
-// counter: three 64-bit counters (one per order n), device memory.
+template <int N, bool FAST>
+static cudaError_t launch_batch_N(int L, const BatchJobs& jobs, unsigned long long* counter, cudaStream_t st) {
+  switch (L) {
+    case 1: return launch_batch_NL<N, 1, FAST>(jobs, counter, st);
+    case 2: return launch_batch_NL<N, 2, FAST>(jobs, counter, st);
+    case 3: return launch_batch_NL<N, 3, FAST>(jobs, counter, st);
+    default: return launch_batch_NL<N, 4, FAST>(jobs, counter, st);
+  }
+}
+
+// One persistent launch per (order n, limbs, fast path or not) present, most
+// expensive first; counter: 32 64-bit counters (one per launch), device memory.
 cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st) {
-  auto cost = [&](int i) { return (double)in[i].pv.limbs * (double)in[i].pv.W * in[i].pv.H; };
+  auto cost = [&](int i) { return (double)in[i].pv.W * in[i].pv.H; };
+  int launch = 0;
   for (int n = 3; n >= 1; --n) {
-    int order[kMaxBatch];
-    int m = 0;
-    for (int i = 0; i < njobs; ++i)
-      if (in[i].pv.n == n) order[m++] = i;
-    if (m == 0) continue;
-    for (int i = 1; i < m; ++i)
-      for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) {
-        const int t = order[j];
-        order[j] = order[j - 1];
-        order[j - 1] = t;
+    for (int L = 4; L >= 1; --L) {
+      for (int fast = 1; fast >= 0; --fast) {
+        if (fast && n == 1) continue;
+        int order[kMaxBatch];
+        int m = 0;
+        for (int i = 0; i < njobs; ++i)
+          if (in[i].pv.n == n && in[i].pv.limbs == L && (mesh_fast_ok(in[i].pv) ? 1 : 0) == fast) order[m++] = i;
+        if (m == 0) continue;
+        for (int i = 1; i < m; ++i)
+          for (int j = i; j > 0 && cost(order[j]) > cost(order[j - 1]); --j) {
+            const int t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+          }
+        BatchJobs jobs;
+        jobs.njobs = m;
+        long long units = 0;
+        for (int k = 0; k < m; ++k) {
+          const BatchIn& b = in[order[k]];
+          BatchJob& jb = jobs.job[k];
+          jb.pv = b.pv;
+          jb.g = b.g;
+          jb.scales = (const float4*)b.scales;
+          jb.scale_pitch = b.scale_pitch;
+          jb.s = b.s;
+          jb.s_pitch = b.s_pitch;
+          jb.status = b.status;
+          jb.segs = (b.pv.W + 31) / 32;
+          jb.units_begin = units;
+          units += (long long)jb.segs * ((b.pv.H + kMeshWarps - 1) / kMeshWarps);
+        }
+        jobs.total_units = units;
+        unsigned long long* ctr = counter + launch++;
+        cudaError_t e;
+        if (n == 1) e = launch_batch_N<1, false>(L, jobs, ctr, st);
+        else if (n == 2) e = fast ? launch_batch_N<2, true>(L, jobs, ctr, st) : launch_batch_N<2, false>(L, jobs, ctr, st);
+        else e = fast ? launch_batch_N<3, true>(L, jobs, ctr, st) : launch_batch_N<3, false>(L, jobs, ctr, st);
+        if (e != cudaSuccess) return e;
       }
-    BatchJobs jobs;
-    jobs.njobs = m;
-    long long units = 0;
-    for (int k = 0; k < m; ++k) {
-      const BatchIn& b = in[order[k]];
-      BatchJob& jb = jobs.job[k];
-      jb.pv = b.pv;
-      jb.g = b.g;
-      jb.scales = (const float4*)b.scales;
-      jb.scale_pitch = b.scale_pitch;
-      jb.s = b.s;
-      jb.s_pitch = b.s_pitch;
-      jb.status = b.status;
-      jb.segs = (b.pv.W + 31) / 32;
-      jb.fast = mesh_fast_ok(b.pv) ? 1 : 0;
-      jb.units_begin = units;
-      units += (long long)jb.segs * ((b.pv.H + kMeshWarps - 1) / kMeshWarps);
     }
-    jobs.total_units = units;
-    cudaError_t e = n == 1 ? launch_batch_N<1>(jobs, counter + n - 1, st)
-                   : n == 2 ? launch_batch_N<2>(jobs, counter + n - 1, st)
-                            : launch_batch_N<3>(jobs, counter + n - 1, st);
-    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

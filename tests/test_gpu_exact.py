@@ -77,6 +77,7 @@ CASES = [
     (2, (37, 70), 4, "f32", 3),
     (2, (19, 129), 3, "u16", 4),
     (3, (14, 23), 2, "u8", 5),
+    (3, (18, 70), 2, "f32", 6),
 ]
 
 
@@ -89,7 +90,7 @@ def test_exact_small_images_all_pixels(n, shape, q, dtype, seed):
     _check_g(w, res)
 
 
-@pytest.mark.parametrize("n", [1, 2])
+@pytest.mark.parametrize("n", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(1, 1), (1, 17), (17, 1), (2, 3)])
 def test_degenerate_sizes(n, shape):
     w = _small_workload(n, shape, 3, "u8", 10 + n)
@@ -98,12 +99,14 @@ def test_degenerate_sizes(n, shape):
     _check_all_pixels(w, res)
 
 
-@pytest.mark.parametrize("shape", [(1, 40), (3, 40), (2, 70)])
-def test_order2_shallow_box(shape):
+@pytest.mark.parametrize("n,shape", [(2, (1, 40)), (2, (3, 40)), (2, (2, 70)), (3, (1, 40)), (3, (4, 40)),
+                                     (3, (2, 33))])
+def test_shallow_box_general_and_fast_paths(n, shape):
     """Scales below one leave a lattice box of fewer than 3n rows (H + above
-    < 6 for shape (1, 40)): the n = 2 mesh then runs its general path; (3, 40)
-    sits exactly at the fast path's limit of six rows."""
-    w = _small_workload(2, shape, 4, "u8", 30 + shape[0], lo=0.3, hi=0.9)
+    < 3n, e.g. shape (1, 40)): the mesh then runs its general path; (3, 40) at
+    n = 2 and (4, 40) at n = 3 sit exactly at the fast path's limit of 3n
+    rows."""
+    w = _small_workload(n, shape, 4, "u8", 30 + 10 * n + shape[0], lo=0.3, hi=0.9)
     w["min_scale"] = 0.1
     res = gu.run_exact(w)
     assert res["status"] == 0
