@@ -541,6 +541,7 @@ struct PlanView {
   double Dd;                      // D as binary64
   int table_bytes_per_w;          // 4, 8 or 16
   const void* table;              // (2^P)^2 rows of (3n)^2 weights
+  const void* table_fold;         // n = 3: the table folded by the square's symmetries, else null
 };
 
 // ------------------------------------------------------ per-pixel scale reading

@@ -169,15 +169,40 @@ __device__ __forceinline__ void fill_n3_order(unsigned char* order) {
       }
 }
 
+// Folded-table columns for the eight symmetries of the square (n = 3):
+// perm[sym 69 + c] = index of S(d_c), S = flip x (bit 0), flip y (bit 1), then
+// swap x and y (bit 2).  All threads of the CTA take part.
+__device__ __forceinline__ void fill_n3_perm(unsigned char* perm, const int* s_dx, const int* s_dy) {
+  constexpr int R = stencil_count<3>(), kD = Stencil<3>::kDmin;
+  __shared__ signed char s_idx[81];
+  for (int i = threadIdx.x; i < 81; i += blockDim.x) s_idx[i] = -1;
+  __syncthreads();
+  for (int c = threadIdx.x; c < R; c += blockDim.x) s_idx[(s_dy[c] - kD) * 9 + (s_dx[c] - kD)] = (signed char)c;
+  __syncthreads();
+  for (int k = threadIdx.x; k < 8 * R; k += blockDim.x) {
+    const int sym = k / R, c = k - sym * R;
+    int ex = (sym & 1) ? -s_dx[c] : s_dx[c], ey = (sym & 2) ? -s_dy[c] : s_dy[c];
+    if (sym & 4) {
+      const int t = ex;
+      ex = ey;
+      ey = t;
+    }
+    perm[k] = (unsigned char)s_idx[(ey - kD) * 9 + (ex - kD)];
+  }
+  __syncthreads();
+}
+
 // One pixel's numerator share for n = 3.  The 69 stencil neighbours do not
 // fit a warp, so the (tap, neighbour) pairs of a group are dealt to the lanes
 // in order: lane i starts at neighbour i of the group's first tap and steps by
-// 32 pairs.  taps[s] = (g offset of the tap's lattice point, table offset,
-// lattice row); s_off[c] = dy_c Gp + dx_c.  CHECK drops reads of rows below 0.
+// 32 pairs.  taps[s] = (g offset of the tap's lattice point, offset of its
+// row in the folded table, lattice row, symmetry); s_off[c] = dy_c Gp + dx_c;
+// s_perm[sym 69 + c] = the folded column of neighbour c.  CHECK drops reads of
+// rows below 0.
 template <int L, bool CHECK>
 __device__ __forceinline__ void n3_pixel(Wide<L>& acc, const int4* taps, const uint64_t* __restrict__ g,
                                          const ulonglong2* __restrict__ table, const int* s_off, const int* s_dy,
-                                         int lane) {
+                                         const unsigned char* s_perm, int lane) {
   constexpr int R = 69;
 #pragma unroll 1
   for (int gi = 0; gi < 10; ++gi) {
@@ -192,7 +217,7 @@ __device__ __forceinline__ void n3_pixel(Wide<L>& acc, const int4* taps, const u
         const int4 ti = taps[t];
         if (!CHECK || ti.z + s_dy[c] >= 0) {
           const Wide<L> gv = wload<L>(g + (ptrdiff_t)(ti.x + s_off[c]) * L);
-          const ulonglong2 wt = __ldg(table + ti.y + c);
+          const ulonglong2 wt = __ldg(table + ti.y + s_perm[ti.w * R + c]);
           mac_weight<L, ulonglong2>(part, gv, wt);
         }
       }
@@ -253,7 +278,7 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
                                          size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch,
                                          int32_t* status, int y, int x0, int4* taps, const int* s_dx,
                                          const int* s_dy, const unsigned char* s_order = nullptr,
-                                         const int* s_off = nullptr) {
+                                         const int* s_off = nullptr, const unsigned char* s_perm = nullptr) {
   using WT = typename WeightT<N>::T;
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
@@ -312,18 +337,23 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
         const int Yx = y0x - j1 * s1 - j2 * s2 + j4 * s4 + half;
         const int Yy = y0y - j2 * s2 - j3 * s3 - j4 * s4 + half;
         const int px = Yx >> P, py = Yy >> P;
-        const int r = ((Yy & mask) << P) | (Yx & mask);
+        // centred offset, folded onto 0 <= X <= Y <= half
+        const int ax = (Yx & mask) - half, ay = (Yy & mask) - half;
+        const int fx = ax < 0, fy = ay < 0;
+        const int X0 = fx ? -ax : ax, Y0 = fy ? -ay : ay;
+        const int sw = X0 > Y0;
+        const int X = sw ? Y0 : X0, Y = sw ? X0 : Y0;
         const bool below = py + kDyMax < 0;
         strad |= (py + kDyMin < 0) && !below;
         const int xf = (below ? -kDyMin : py) * gp + px + left;
-        const int tf = (below ? (1 << (2 * P)) : r) * R;
-        taps[slot] = make_int4(xf, tf, py, 0);
+        const int frow = below ? (half + 1) * (half + 2) / 2 : (Y * (Y + 1) >> 1) + X;
+        taps[slot] = make_int4(xf, frow * R, py, below ? 0 : (fx | (fy << 1) | (sw << 2)));
       }
       const bool check = __any_sync(0xffffffffu, strad) != 0;
       __syncwarp();
-      const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(pv.table);
-      if (check) n3_pixel<L, true>(acc, taps, g, tab, s_off, s_dy, lane);
-      else n3_pixel<L, false>(acc, taps, g, tab, s_off, s_dy, lane);
+      const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(pv.table_fold);
+      if (check) n3_pixel<L, true>(acc, taps, g, tab, s_off, s_dy, s_perm, lane);
+      else n3_pixel<L, false>(acc, taps, g, tab, s_off, s_dy, s_perm, lane);
     } else if constexpr (FAST) {
       static_assert(N == 2 && R == 32, "fast path is for n = 2 and n = 3");
       constexpr int kDyMin = Stencil<N>::kDmin, kDyMax = Stencil<N>::kDmin + 3 * N - 1;
@@ -460,7 +490,7 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R], s_off[R];
-  __shared__ unsigned char s_order[TAPS];
+  __shared__ unsigned char s_order[TAPS], s_perm[8 * R];
   __shared__ int4 s_tap[kMeshWarps][TAPS];
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
@@ -469,6 +499,7 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   }
   __syncthreads();
   if (threadIdx.x < R) s_off[threadIdx.x] = s_dy[threadIdx.x] * (int)pv.Gp + s_dx[threadIdx.x];
+  if constexpr (FAST && N == 3) fill_n3_perm(s_perm, s_dx, s_dy);
   __syncthreads();
   const int segs = (pv.W + 31) >> 5;
   const int band = blockIdx.x / segs;
@@ -476,7 +507,7 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   if (y >= pv.H) return;
   const int x0 = (blockIdx.x - band * segs) * 32;
   mesh_run<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
-                       s_tap[threadIdx.x >> 5], s_dx, s_dy, s_order, s_off);
+                       s_tap[threadIdx.x >> 5], s_dx, s_dy, s_order, s_off, s_perm);
 }
 
 // ------------------------------------------------------------------- batches
@@ -508,9 +539,10 @@ struct BatchJobs {
 
 template <int N, int L, bool FAST>
 __device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int x0, int4* taps, const int* sdx,
-                                                 const int* sdy, const unsigned char* order, const int* soff) {
+                                                 const int* sdy, const unsigned char* order, const int* soff,
+                                                 const unsigned char* perm) {
   mesh_run<N, L, FAST>(jb.pv, jb.g, jb.scales, jb.scale_pitch, jb.s, jb.s_pitch, nullptr, 0, jb.status, y, x0, taps,
-                       sdx, sdy, order, soff);
+                       sdx, sdy, order, soff, perm);
 }
 
 // A unit is the 32-column runs of kMeshWarps consecutive rows of one image (one
@@ -523,13 +555,17 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __gri
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R], s_off[R];
-  __shared__ unsigned char s_order[TAPS];
+  __shared__ unsigned char s_order[TAPS], s_perm[8 * R];
   __shared__ int4 s_tap[kMeshWarps][TAPS];
   __shared__ unsigned long long s_item;
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
     if constexpr (FAST && N == 2) fill_n2_order(s_order);
     if constexpr (FAST && N == 3) fill_n3_order(s_order);
+  }
+  if constexpr (FAST && N == 3) {
+    __syncthreads();
+    fill_n3_perm(s_perm, s_dx, s_dy);
   }
   const int warp = threadIdx.x >> 5;
   int4* taps = s_tap[warp];
@@ -553,7 +589,7 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __gri
     const int y = band * kMeshWarps + warp;
     const int x0 = (int)(u - (long long)band * jb.segs) * 32;
     if (y >= jb.pv.H) continue;
-    batch_dispatch_L<N, L, FAST>(jb, y, x0, taps, s_dx, s_dy, s_order, s_off);
+    batch_dispatch_L<N, L, FAST>(jb, y, x0, taps, s_dx, s_dy, s_order, s_off, s_perm);
   }
 }
 
@@ -621,7 +657,8 @@ cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t sc
 // -3n/2 .. Gh + 3n/2 of pitch Gp) and park taps below the image on rows
 // 0 .. 3n-1 of the box.
 static bool mesh_fast_ok(const PlanView& pv) {
-  return pv.n >= 2 && pv.Gh >= 3 * pv.n && ((long long)pv.Gh + 8) * pv.Gp < (1ll << 31);
+  return pv.n >= 2 && pv.Gh >= 3 * pv.n && ((long long)pv.Gh + 8) * pv.Gp < (1ll << 31) &&
+         (pv.n != 3 || pv.table_fold != nullptr);
 }
 
 template <int N, int L>

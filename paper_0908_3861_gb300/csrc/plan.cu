@@ -227,8 +227,74 @@ bool build_table(int n, int P, HostTable& out) {
   return true;
 }
 
+// Order-3 table folded by the symmetries of the square.  ZP^{*n} is invariant
+// under x -> -x, y -> -y and x <-> y, so D ZP^{*n}(r - d) = F[S(r)][S(d)] for
+// the symmetry S that takes the centred offset r = (Rx, Ry) 2^-P, Rx, Ry in
+// [-2^(P-1), 2^(P-1)), to 0 <= X <= Y <= 2^(P-1) (flip x if Rx < 0, flip y if
+// Ry < 0, then swap if X > Y).  F has (h+1)(h+2)/2 rows, h = 2^(P-1): row
+// Y (Y+1)/2 + X, columns in stencil order.  Rows with Y = h (r_y = +1/2) are
+// not in the full table; they come from the flipped row r_y = -1/2.  Every
+// full-table entry is checked against its folded counterpart.
+bool fold_table(const HostTable& ht, int n, int P, std::vector<uint8_t>& out) {
+  int cnt = 0, cdx[81], cdy[81], idx[9][9];
+  for (auto& row : idx)
+    for (int& v : row) v = -1;
+  if (n != 3) return false;
+  {
+    constexpr abf::Stencil<3> st{};
+    cnt = st.count;
+    for (int i = 0; i < cnt; ++i) {
+      cdx[i] = st.dx[i];
+      cdy[i] = st.dy[i];
+      idx[st.dy[i] - st.kDmin][st.dx[i] - st.kDmin] = i;
+    }
+  }
+  const int dmin = abf::Stencil<3>::kDmin;
+  auto index_of = [&](int ex, int ey) -> int {
+    if (ex < dmin || ex >= dmin + 9 || ey < dmin || ey >= dmin + 9) return -1;
+    return idx[ey - dmin][ex - dmin];
+  };
+  const int one = 1 << P, h = one / 2;
+  const size_t wb = (size_t)ht.wbytes, rowb = (size_t)cnt * wb;
+  const size_t frows = (size_t)(h + 1) * (h + 2) / 2;
+  out.assign(frows * rowb, 0);
+  auto full_row = [&](int Rx, int Ry) { return ((size_t)(Ry + h) * one + (Rx + h)) * rowb; };
+  bool ok = true;
+  for (int Y = 0; Y <= h && ok; ++Y)
+    for (int X = 0; X <= Y && ok; ++X) {
+      const bool fy = Y == h, fx = X == h;  // preimage (X or -h, Y or -h) in the full table
+      const int Rx = fx ? -h : X, Ry = fy ? -h : Y;
+      uint8_t* dst = &out[((size_t)Y * (Y + 1) / 2 + X) * rowb];
+      for (int e = 0; e < cnt; ++e) {
+        const int c = index_of(fx ? -cdx[e] : cdx[e], fy ? -cdy[e] : cdy[e]);
+        if (c < 0) { ok = false; break; }
+        std::memcpy(dst + e * wb, &ht.bytes[full_row(Rx, Ry) + c * wb], wb);
+      }
+    }
+  if (!ok) return false;
+  // check: every full entry equals its folded counterpart
+#pragma omp parallel for schedule(static) reduction(&& : ok)
+  for (int Ry = -h; Ry < h; ++Ry) {
+    for (int Rx = -h; Rx < h; ++Rx) {
+      const bool fx = Rx < 0, fy = Ry < 0;
+      int X = fx ? -Rx : Rx, Y = fy ? -Ry : Ry;
+      const bool sw = X > Y;
+      if (sw) std::swap(X, Y);
+      const uint8_t* frow = &out[((size_t)Y * (Y + 1) / 2 + X) * rowb];
+      for (int c = 0; c < cnt; ++c) {
+        int ex = fx ? -cdx[c] : cdx[c], ey = fy ? -cdy[c] : cdy[c];
+        if (sw) std::swap(ex, ey);
+        const int e = index_of(ex, ey);
+        if (e < 0 || std::memcmp(&ht.bytes[full_row(Rx, Ry) + c * wb], frow + e * wb, wb) != 0) ok = false;
+      }
+    }
+  }
+  return ok;
+}
+
 struct DeviceTable {
   void* ptr = nullptr;
+  void* fold = nullptr;  // folded order-3 table (plus a zero row), else null
   u128 D = 0;
   int wbytes = 0;
 };
@@ -259,6 +325,30 @@ abf_status get_table(int device, int n, int P, DeviceTable* out) {
       cudaMemset((char*)dt.ptr + ht.bytes.size(), 0, row_bytes) != cudaSuccess) {
     cudaFree(dt.ptr);
     return ABF_ERR_CUDA;
+  }
+  if (n == 3) {
+    std::vector<uint8_t> fb;
+    bool folded = false;
+    try {
+      folded = fold_table(ht, n, P, fb);
+    } catch (const std::bad_alloc&) {
+      cudaFree(dt.ptr);
+      return ABF_ERR_OOM;
+    }
+    if (!folded) {
+      cudaFree(dt.ptr);
+      return ABF_ERR_UNSUPPORTED;
+    }
+    if (cudaMalloc(&dt.fold, fb.size() + row_bytes) != cudaSuccess) {
+      cudaFree(dt.ptr);
+      return ABF_ERR_OOM;
+    }
+    if (cudaMemcpy(dt.fold, fb.data(), fb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset((char*)dt.fold + fb.size(), 0, row_bytes) != cudaSuccess) {
+      cudaFree(dt.ptr);
+      cudaFree(dt.fold);
+      return ABF_ERR_CUDA;
+    }
   }
   dt.D = ht.D;
   dt.wbytes = ht.wbytes;
@@ -418,6 +508,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   pv.Dd = u128_to_double(tab.D);
   pv.table_bytes_per_w = tab.wbytes;
   pv.table = tab.ptr;
+  pv.table_fold = tab.fold;
   if (exact) {
     p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
     p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, n, nullptr, nullptr);

@@ -59,10 +59,10 @@ __device__ __forceinline__ Wide<L> warp_inclusive(Wide<L> v, int lane) {
   return v;
 }
 
+// Input element -> integer f 2^F; raises ABF_DEV_BAD_INPUT (and reads 0) when
+// a floating-point value is off the 2^-F grid or beyond the value bound.
 template <typename TIn>
-__device__ __forceinline__ int64_t load_f(const TIn* row, int x, double scale, double bound,
-                                          int32_t* status) {
-  const TIn raw = row[x];
+__device__ __forceinline__ int64_t convert_f(TIn raw, double scale, double bound, int32_t* status) {
   if constexpr (sizeof(TIn) <= 2) {
     return (int64_t)raw;
   } else {
@@ -78,7 +78,7 @@ __device__ __forceinline__ int64_t load_f(const TIn* row, int x, double scale, d
 
 constexpr int kRowVec = 4;  // elements per lane per chunk
 
-template <int L, typename TIn>
+template <int L, typename TIn, int NF>
 __global__ void __launch_bounds__(256) row_scan_kernel(const PlanView pv, const TIn* __restrict__ f,
                                                        size_t f_pitch, uint64_t* __restrict__ g,
                                                        int32_t* status) {
@@ -91,21 +91,22 @@ __global__ void __launch_bounds__(256) row_scan_kernel(const PlanView pv, const 
   const TIn* frow = (y < pv.H) ? reinterpret_cast<const TIn*>(reinterpret_cast<const char*>(f) + (size_t)y * f_pitch)
                                : nullptr;
   uint64_t* grow = g + (size_t)y * (size_t)pv.Gp * L;
-  Wide<L> carry[3];
+  Wide<L> carry[NF];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) wzero<L>(carry[k]);
-  const int chunk = 32 * kRowVec;
+  for (int k = 0; k < NF; ++k) wzero<L>(carry[k]);
+  constexpr int chunk = 32 * kRowVec;
   for (int x0 = 0; x0 < pv.Gw; x0 += chunk) {
     Wide<L> v[kRowVec];
 #pragma unroll
     for (int e = 0; e < kRowVec; ++e) {
-      const int xi = x0 + lane * kRowVec + e;   // box column
-      const int x = xi - pv.left;               // image column
+      const int xi = x0 + lane * kRowVec + e;  // box column
+      const int x = xi - pv.left;              // image column
       int64_t val = 0;
-      if (frow && x >= 0 && x < pv.W && xi < pv.Gw) val = load_f<TIn>(frow, x, scale, bound, status);
+      if (frow && x >= 0 && x < pv.W && xi < pv.Gw) val = convert_f<TIn>(frow[x], scale, bound, status);
       v[e] = wfrom_i64<L>(val);
     }
-    for (int k = 0; k < pv.n; ++k) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
       // lane-local inclusive scan
 #pragma unroll
       for (int e = 1; e < kRowVec; ++e) wadd<L>(v[e], v[e - 1]);
@@ -295,7 +296,10 @@ static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch
                                int32_t* status, cudaStream_t st) {
   const int warps_per_block = 8;
   const int blocks = (pv.Gh + warps_per_block - 1) / warps_per_block;
-  row_scan_kernel<L, TIn><<<blocks, 32 * warps_per_block, 0, st>>>(pv, (const TIn*)f, f_pitch, g, status);
+  const TIn* fin = (const TIn*)f;
+  if (pv.n == 1) row_scan_kernel<L, TIn, 1><<<blocks, 32 * warps_per_block, 0, st>>>(pv, fin, f_pitch, g, status);
+  else if (pv.n == 2) row_scan_kernel<L, TIn, 2><<<blocks, 32 * warps_per_block, 0, st>>>(pv, fin, f_pitch, g, status);
+  else row_scan_kernel<L, TIn, 3><<<blocks, 32 * warps_per_block, 0, st>>>(pv, fin, f_pitch, g, status);
   return cudaGetLastError();
 }
 
