@@ -21,6 +21,11 @@ Unser, "Fast adaptive elliptical filtering using box splines"):
 * ``direct``     -- the quantity the algorithm computes, written from its
   definition: s[m] = <f, beta_a(m)(. - m)> of Sec. 6 with phi = delta
   (Sec. 7 (1)), i.e. a plain sum of the image against the box-spline kernel.
+* ``line1d``     -- the 1-D scale-adaptive B-spline filter of Sec. 3
+  (Proposition "prop"): B-splines and their dilates (Sec. 2), the projection
+  s[m] = <f, beta_a^{n2}(. - m)> from its definition by exact piecewise
+  integration, and the Proposition's two steps (running sums, then the FD
+  mask with B-spline interpolation) in exact integers.
 * ``scales``     -- the per-pixel scale readings: paper scales a_k (Sec. 7)
   to lattice steps c_k, and the ellipse-to-scales moment rule (a reading: the
   paper leaves the scale map to other work, Sec. 8; Theorem (convergence) of
