@@ -418,6 +418,141 @@ def run_batch(args):
         f.close()
 
 
+def run_line1d(args):
+    """The 1-D scale-adaptive B-spline filter of Sec. 3 on 2048 signals of
+    65536 samples (float32 on the 2^-16 grid, n1 = 1, n2 = 3, a in [1, 64]):
+    Msample/s of integrate + filter, exact form."""
+    import torch
+    import torch.distributed as dist
+    import synthetic
+    from paper_0908_3861_gb300 import AdaptiveFilter1D
+    import __graft_entry__
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    shp = _shape(args) or (2048, 65536)
+    w = synthetic.workload_1d(count=shp[0], length=shp[1], seed_offset=rank)
+    f, a = w["signals"], w["scales"]
+    count, length = f.shape
+    flt = AdaptiveFilter1D(length, count, w["n1"], w["n2"], torch.float32, q_bits=w["q_bits"],
+                           frac_bits=w["frac_bits"], max_scale=w["max_scale"], value_bound=w["value_bound"],
+                           out="f32", device=dev)
+    f_t = torch.from_numpy(f).to(dev)
+    a_t = torch.from_numpy(a).to(dev)
+    out = torch.empty((count, length), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        flt.integrate(f_t)
+        flt.filter(a_t, out)
+    torch.cuda.synchronize()
+    assert flt.device_status() == 0
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            flt.integrate(f_t)
+            ev[i][1].record(stream)
+            flt.filter(a_t, out)
+            ev[i][2].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
+    integ_ms = sum(x.elapsed_time(y) for x, y, z in ev) / K
+    mesh_ms = sum(y.elapsed_time(z) for x, y, z in ev) / K
+    assert flt.device_status() == 0
+    # end to end: pinned host buffers, copies inside the timed region
+    f_h, a_h = torch.from_numpy(f).pin_memory(), torch.from_numpy(a).pin_memory()
+    o_h = torch.empty((count, length), dtype=torch.float32).pin_memory()
+    f_d, a_d = torch.empty_like(f_t), torch.empty_like(a_t)
+
+    def e2e_step():
+        f_d.copy_(f_h, non_blocking=True)
+        a_d.copy_(a_h, non_blocking=True)
+        flt.integrate(f_d)
+        flt.filter(a_d, out)
+        o_h.copy_(out, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    samples = float(count * length)
+    value = replica_throughput(samples, K, world, total_ms)
+    L = flt.limbs
+    N = w["n1"] + w["n2"] + 1
+    K_nb = N + 1 if N % 2 else N + 2
+    macs = (w["n2"] + 2) * K_nb
+    imad = {1: 4, 2: 12, 3: 20, 4: 28}[L]
+    clk = clk.summary()
+    sm_mhz = clk["sm_mhz"] or _peaks().get("sm_max_mhz", 2070.0)
+    peak = 152 * 64 * sm_mhz * 1e6 / imad
+    achieved = macs * samples / (mesh_ms * 1e-3)
+    line = {
+        "metric": "Msample/s 1-D scale-adaptive B-spline filter (Sec. 3), exact form", "value": round(value, 3),
+        "unit": "Msample/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64x%d" % L, "data": "synthetic",
+        "config": {"workload": "%d signals x %d samples f32 (2^-16 grid), n1=1, n2=3, a in [1,64], Q=8, exact form"
+                               % (count, length), "l2": "inputs larger than L2 (signals %.0f MB, scales %.0f MB)"
+                               % (f.nbytes / 1e6, a.nbytes / 1e6), "parallelism": "replicas x%d" % world},
+        "e2e": {"value": round(replica_throughput(samples, K, world, e2e_ms), 3), "unit": "Msample/s",
+                "h2d_bytes_per_step": int(f.nbytes + a.nbytes), "d2h_bytes_per_step": int(o_h.numel() * 4)},
+        "gpu_launches": int(K * 2),
+        "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
+        "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak / 1e9, 2),
+                     "unit": "G MAC/s (%d-limb integer x 64-bit weight)" % L, "frac": round(achieved / peak, 4),
+                     "traffic": None, "kernel": "mesh1d_kernel",
+                     "peak_note": "derived: 152 SM x 64 INT32 multiply-add lanes x median SM clock / %d 32-bit "
+                                  "multiply-adds per MAC; achieved = (n2+2) x %d stencil MACs per sample"
+                                  % (imad, K_nb)},
+        "roofline_integrate": {"bound": "hbm", "achieved": round((f.nbytes + samples * 8 * L) / (integ_ms * 1e-3)
+                                                                 / 1e9, 1),
+                               "peak": _peaks().get("hbm_gbs"), "unit": "GB/s",
+                               "bytes_note": "f read once, g written once"},
+        "clocks": clk,
+    }
+    if rank == 0 and args.cpu_baseline:
+        from oracle import line1d as o
+        t_start = time.perf_counter()
+        done = 0
+        rng = np.random.default_rng(7)
+        fi = (f.astype(np.float64) * 65536.0).astype(np.int64)
+        while time.perf_counter() - t_start < args.cpu_seconds:
+            r = int(rng.integers(0, count))
+            ms = sorted(rng.integers(0, length, 64).tolist())
+            A = o.quantise(a[r], w["q_bits"])
+            o.filter_paper_at(list(fi[r]), A, w["n1"], w["n2"], w["q_bits"], w["frac_bits"], ms)
+            done += len(ms)
+        el = time.perf_counter() - t_start
+        line["cpu_baseline"] = {"value": done / el / 1e6, "unit": "Msample/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d samples (64 per signal, each signal's running sums in full), "
+                                          "exact, %.1f s" % (done, el)}
+    flt.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_serve(args):
     """Poisson-arrival stream of filter jobs (sides U{256..4096}, n U{1,2},
     float32 images on the 2^-16 grid with ellipse fields as the 2048^2 case)
@@ -593,6 +728,8 @@ def main():
         run_batch(args)
     elif args.workload == "c5":
         run_serve(args)
+    elif args.workload == "d1":
+        run_line1d(args)
     else:
         run_ours(args)
 

@@ -300,6 +300,69 @@ const char* abf_status_str(abf_status s);
 abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t out_bytes,
                                  size_t* needed_bytes, int32_t* wbytes, uint32_t* D_words4);
 
+/* ------------------------------------------------- 1-D adaptive filter (Sec. 3)
+ *
+ * The scale-adaptive B-spline filter of Sec. 3 (Proposition "prop") on a batch
+ * of 1-D signals (rows): s[m] = < f, beta_{a(m)}^{n2}( . - m) > with the model
+ * f(x) = sum_k c[k] beta^{n1}(x - k), beta_a^n(x) = beta^n(x / a) / a.  For
+ * n1 in {0, 1} the interpolation prefilter is the identity (c = f) and the
+ * result is exact: g = n2+1 causal running sums of c in wrap-around integers,
+ * then per sample the FD mask Delta_a^{n2+1} with degree N = n1+n2+1 B-spline
+ * interpolation at y_j = m + tau - a j, tau = (a-1)(n2+1)/2 (Eq. (link)):
+ *   S[m] = sum_j (-1)^j binom(n2+1, j) sum_k g[k] D beta^N(y_j - k),
+ *   s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F),  D = N! 2^(N (Q+1)),
+ * with A = rint(a 2^Q).  The signal is zero outside [0, length).  n1 >= 2
+ * (an irrational IIR prefilter) is not served (ABF_ERR_UNSUPPORTED).        */
+typedef struct {
+  int32_t length;         /* samples per signal, >= 1                           */
+  int32_t count;          /* signals (rows), >= 1                               */
+  int32_t n1;             /* model degree: 0 or 1                               */
+  int32_t n2;             /* analysis degree: 0..3                              */
+  abf_dtype in_dtype;     /* f elements                                         */
+  abf_dtype out_dtype;    /* s elements: ABF_F32 or ABF_F64                     */
+  int32_t q_bits;         /* Q: scales rounded to the 2^-Q grid, 1..10          */
+  int32_t in_frac_bits;   /* F: float f must lie on the 2^-F grid (0 for ints)  */
+  double max_scale;       /* bound on every a (>= 2^-Q)                         */
+  double value_bound;     /* bound on |f|; 0 = dtype range (integer inputs)     */
+} abf1d_desc;
+
+typedef struct abf1d_plan_s* abf1d_plan;
+
+/* Plan: validates the descriptor, picks the limb count L from the numerator
+ * bound D max_scale^(n2+1) |f|max 2^F (|s| <= |f|max: the kernel is
+ * non-negative with unit lattice sum), uploads the D beta^N table.
+ * ABF_ERR_RANGE if L would exceed 4.                                         */
+abf_status abf1d_plan_create(const abf1d_desc* desc, abf1d_plan* out);
+abf_status abf1d_plan_destroy(abf1d_plan plan);
+
+/* integrated_bytes: size of the integrated signals g (count rows of
+ * g_pitch_elems elements of L uint64 limbs); right: samples past the signal
+ * end that g holds (the adaptive step reads up to tau + (N+1)/2 beyond it).  */
+abf_status abf1d_plan_query(abf1d_plan plan, size_t* integrated_bytes, int32_t* right, int32_t* limbs,
+                            int64_t* g_pitch_elems);
+
+/* Non-adaptive step: g = u_1^{(n2+1)} * (f 2^F) per row, exact modulo
+ * 2^(64 L).  d_f: count rows of length in_dtype elements (row pitch in
+ * bytes); d_g: plan-sized, 16-byte aligned.  Off-grid or out-of-bound float
+ * inputs read as 0 and set ABF_DEV_BAD_INPUT.                                */
+abf_status abf1d_integrate(abf1d_plan plan, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t stream);
+
+/* Adaptive step: d_a holds one float32 scale a per sample (count rows, row
+ * pitch in bytes); d_s receives s (out_dtype).  Samples whose scale is
+ * invalid (non-finite, A < 1 or A > rint(max_scale 2^Q)) or whose numerator
+ * bound exceeds the limbs get NaN and set the device status.                 */
+abf_status abf1d_filter(abf1d_plan plan, const void* d_g, const float* d_a, size_t a_pitch, void* d_s,
+                        size_t s_pitch, cudaStream_t stream);
+
+/* The integer numerators S[m] (L little-endian uint64 limbs per sample, two's
+ * complement modulo 2^(64 L)), for bit-exact checks.                         */
+abf_status abf1d_filter_numerator(abf1d_plan plan, const void* d_g, const float* d_a, size_t a_pitch,
+                                  void* d_num, size_t num_pitch, cudaStream_t stream);
+
+/* Device status bits (ABF_DEV_*) of the plan's launches since the last read;
+ * synchronises the device, then clears the word.                             */
+abf_status abf1d_last_device_status(abf1d_plan plan, int32_t* code);
+
 /* Library version, for the bindings. */
 int32_t abf_version(void);
 

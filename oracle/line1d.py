@@ -186,15 +186,22 @@ def box_right(n1, n2, q_bits, A_max):
 def filter_paper(c_int, A, n1, n2, q_bits, frac_bits=0):
     """The two steps of the Proposition in exact integers: returns the
     numerators S[m] (Python ints) and s[m] (Fractions).  c_int = f 2^F."""
+    return filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, range(len(c_int)))
+
+
+def filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, ms):
+    """filter_paper at the samples ms only (the running sums still cover the
+    whole signal)."""
     n = len(c_int)
     N = n1 + n2 + 1
     P = p_bits(q_bits)
     D = denominator(N, P)
     right = box_right(n1, n2, q_bits, int(np.max(A)) if n else 0)
     g = running_sums(c_int, n2 + 1, n + right)
-    h = (N + 1) / 2
+    h = Fr(N + 1, 2)
     S_all, s_all = [], []
-    for m in range(n):
+    for m in ms:
+        m = int(m)  # Python integers throughout (numpy scalars would overflow)
         Am = int(A[m])
         tauP = (Am - (1 << q_bits)) * (n2 + 1)          # tau in units of 2^-P
         S = 0

@@ -43,6 +43,13 @@ class abf_desc(ctypes.Structure):
                 ("value_bound", ctypes.c_double), ("max_scale_product", ctypes.c_double)]
 
 
+class abf1d_desc(ctypes.Structure):
+    _fields_ = [("length", ctypes.c_int32), ("count", ctypes.c_int32), ("n1", ctypes.c_int32),
+                ("n2", ctypes.c_int32), ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+                ("q_bits", ctypes.c_int32), ("in_frac_bits", ctypes.c_int32),
+                ("max_scale", ctypes.c_double), ("value_bound", ctypes.c_double)]
+
+
 class abf_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
@@ -94,6 +101,13 @@ def lib():
         "abf_server_pause": ([vp, i32], st),
         "abf_server_stats": ([vp, P(sz), P(sz), P(i32), P(i32), P(i32)], st),
         "abf_server_destroy": ([vp], st),
+        "abf1d_plan_create": ([P(abf1d_desc), P(vp)], st),
+        "abf1d_plan_destroy": ([vp], st),
+        "abf1d_plan_query": ([vp, P(sz), P(i32), P(i32), P(ctypes.c_int64)], st),
+        "abf1d_integrate": ([vp, vp, sz, vp, vp], st),
+        "abf1d_filter": ([vp, vp, vp, sz, vp, sz, vp], st),
+        "abf1d_filter_numerator": ([vp, vp, vp, sz, vp, sz, vp], st),
+        "abf1d_last_device_status": ([vp, P(i32)], st),
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
@@ -261,3 +275,41 @@ def abf_status_str(s):
 
 def abf_version():
     return lib().abf_version()
+
+
+# ------------------------------------------------------ 1-D filter (Sec. 3)
+
+def abf1d_plan_create(desc):
+    h = ctypes.c_void_p()
+    _check(lib().abf1d_plan_create(ctypes.byref(desc), ctypes.byref(h)), "abf1d_plan_create")
+    return h
+
+
+def abf1d_plan_destroy(plan):
+    _check(lib().abf1d_plan_destroy(plan), "abf1d_plan_destroy")
+
+
+def abf1d_plan_query(plan):
+    gb, right, limbs, pitch = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().abf1d_plan_query(plan, ctypes.byref(gb), ctypes.byref(right), ctypes.byref(limbs),
+                                  ctypes.byref(pitch)), "abf1d_plan_query")
+    return dict(integrated_bytes=gb.value, right=right.value, limbs=limbs.value, g_pitch=pitch.value)
+
+
+def abf1d_integrate(plan, f, f_pitch, g, stream=None):
+    _check(lib().abf1d_integrate(plan, _ptr(f), f_pitch, _ptr(g), _stream(stream)), "abf1d_integrate")
+
+
+def abf1d_filter(plan, g, a, a_pitch, s, s_pitch, stream=None):
+    _check(lib().abf1d_filter(plan, _ptr(g), _ptr(a), a_pitch, _ptr(s), s_pitch, _stream(stream)), "abf1d_filter")
+
+
+def abf1d_filter_numerator(plan, g, a, a_pitch, num, num_pitch, stream=None):
+    _check(lib().abf1d_filter_numerator(plan, _ptr(g), _ptr(a), a_pitch, _ptr(num), num_pitch, _stream(stream)),
+           "abf1d_filter_numerator")
+
+
+def abf1d_last_device_status(plan):
+    v = ctypes.c_int32()
+    _check(lib().abf1d_last_device_status(plan, ctypes.byref(v)), "abf1d_last_device_status")
+    return v.value

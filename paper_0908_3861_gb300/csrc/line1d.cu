@@ -1,0 +1,358 @@
+// The 1-D scale-adaptive B-spline filter of Sec. 3 (Proposition "prop"), exact
+// form, on a batch of signals (one per row).
+//
+//   Non-adaptive step: g = u_1^{(n2+1)} * c, n2+1 causal running sums of
+//     c = f 2^F (c = f because the model degree n1 is 0 or 1, where the
+//     interpolation prefilter (b^{n1})^-1 is the identity).  The row pass of
+//     scan.cu runs it, on rows extended by `right` samples past the signal end
+//     (the sums keep changing there while the adaptive step reads them).
+//   Adaptive step: s[m] = Delta_a^{n2+1} F(m), F(x) = sum_k g[k] beta^N(x +
+//     tau - k), N = n1 + n2 + 1, tau = (a - 1)(n2 + 1)/2 (Eq. (link)): the FD
+//     mask d^{n2+1}_a of Eq. (FD) at the points y_j = m + tau - a j, each
+//     interpolated with the degree-N B-spline.
+//
+// Exact arithmetic: a = A 2^-Q, so y_j lies on the 2^-P grid, P = Q + 1, and
+// D beta^N is an integer there for D = N! 2^(N P).  The table holds
+// D beta^N(r - d) for r = R 2^-P in [0, 1) and the N+1 or N+2 integers d that
+// can carry weight; it is built on the host from the B-spline recurrence of
+// degree n from degree n-1 (two shifted copies weighted by linear factors) in
+// integers, and every row is checked to sum to D (partition of unity).
+//   S[m] = sum_j (-1)^j binom(n2+1, j) sum_d g[p_j + d] T[r_j][d]  (mod 2^(64 L))
+//   s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F)  in binary64.
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "abf_internal.cuh"
+
+namespace abf {
+
+cudaError_t run_row_scan(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, int32_t* status,
+                         cudaStream_t st);
+
+struct Line1dView {
+  int length, count, n1, n2, N, Q, P, F, K, dmin;
+  int Amax;
+  long long Gp;      // row pitch of g, elements
+  int limbs;
+  int out_dtype;
+  float log2_base;   // log2(D |f|max 2^F)
+  double Dd;         // D
+  const uint64_t* table;  // 2^P rows x K entries
+};
+
+// acc += g * w (mod 2^(64 L)) for a 64-bit table weight, as carry chains.
+template <int L>
+__device__ __forceinline__ void mac64(Wide<L>& acc, const Wide<L>& gv, uint64_t w) {
+  if constexpr (L == 1) wmac<1>(acc, gv, w);
+  else if constexpr (L == 2) wmac2_u64(acc, gv, w);
+  else if constexpr (L == 3) wmac_w6_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
+  else wmac_w8_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
+}
+
+template <int N2>
+__device__ __forceinline__ int binom_n2p1(int j) {
+  // binom(N2 + 1, j)
+  int c = 1;
+#pragma unroll
+  for (int i = 0; i < N2 + 1; ++i)
+    if (i < j) c = c * (N2 + 1 - i) / (i + 1);
+  return c;
+}
+
+// One thread per output sample.
+template <int L, int N2>
+__global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const uint64_t* __restrict__ g,
+                                                     const float* __restrict__ a, size_t a_pitch, void* s,
+                                                     size_t s_pitch, uint64_t* num, size_t num_pitch,
+                                                     int32_t* status) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (m >= v.length) return;
+  const float av = reinterpret_cast<const float*>(reinterpret_cast<const char*>(a) + (size_t)row * a_pitch)[m];
+  const double q = ldexp(1.0, v.Q);
+  const double x = (double)av * q;  // exact (power of two)
+  int ok = 1;
+  long long A = 0;
+  if (!(x > 0.0) || !(x < 2147483648.0)) {
+    ok = 0;
+  } else {
+    A = __double2ll_rn(x);
+    if (A < 1 || A > v.Amax) ok = 0;
+  }
+  if (ok) {
+    const float lb = v.log2_base + (float)(N2 + 1) * (__log2f((float)A) - (float)v.Q) + 0.05f;
+    if (!(lb < 64.0f * L - 1.0f)) ok = 2;
+  }
+  const bool f64 = v.out_dtype == ABF_F64;
+  if (ok != 1) {
+    raise_status(status, ok == 0 ? ABF_DEV_BAD_SCALE : ABF_DEV_RANGE);
+    if (s) {
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      char* srow = reinterpret_cast<char*>(s) + (size_t)row * s_pitch;
+      if (f64) reinterpret_cast<double*>(srow)[m] = nan;
+      else reinterpret_cast<float*>(srow)[m] = (float)nan;
+    }
+    return;
+  }
+  const int P = v.P, K = v.K;
+  const long long mask = (1ll << P) - 1;
+  const long long tauP = (A - (1ll << v.Q)) * (N2 + 1);  // tau in units of 2^-P
+  const uint64_t* grow = g + (size_t)row * (size_t)v.Gp * L;
+  Wide<L> acc;
+  wzero<L>(acc);
+#pragma unroll
+  for (int j = 0; j < N2 + 2; ++j) {
+    const long long Y = ((long long)m << P) + tauP - 2 * A * j;  // y_j in units of 2^-P
+    const long long p = Y >> P;
+    const int r = (int)(Y & mask);
+    const uint64_t* trow = v.table + (size_t)r * K;
+    Wide<L> Fj;
+    wzero<L>(Fj);
+    for (int d = 0; d < K; ++d) {
+      const long long k = p + v.dmin + d;
+      if (k < 0) continue;  // the running sums vanish before the signal
+      const Wide<L> gv = wload<L>(grow + (size_t)k * L);
+      mac64<L>(Fj, gv, __ldg(trow + d));
+    }
+    Wide<L> t;
+    wzero<L>(t);
+    wmac<L>(t, Fj, (uint64_t)binom_n2p1<N2>(j));
+    if (j & 1) wsub<L>(acc, t);
+    else wadd<L>(acc, t);
+  }
+  if (num) {
+    uint64_t* q8 = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(num) + (size_t)row * num_pitch) + (size_t)m * L;
+#pragma unroll
+    for (int i = 0; i < L; ++i) q8[i] = acc.w[i];
+  }
+  if (s) {
+    double den = v.Dd;
+#pragma unroll
+    for (int e = 0; e < N2 + 1; ++e) den *= (double)A;
+    const double val = ldexp(wto_double<L>(acc), v.Q * (N2 + 1) - v.F) / den;
+    char* srow = reinterpret_cast<char*>(s) + (size_t)row * s_pitch;
+    if (f64) reinterpret_cast<double*>(srow)[m] = val;
+    else reinterpret_cast<float*>(srow)[m] = (float)val;
+  }
+}
+
+template <int L>
+static cudaError_t launch_mesh1d_L(const Line1dView& v, const uint64_t* g, const float* a, size_t a_pitch, void* s,
+                                   size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
+                                   cudaStream_t st) {
+  dim3 grid((v.length + 255) / 256, v.count);
+  switch (v.n2) {
+    case 0: mesh1d_kernel<L, 0><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
+    case 1: mesh1d_kernel<L, 1><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
+    case 2: mesh1d_kernel<L, 2><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
+    default: mesh1d_kernel<L, 3><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t run_mesh1d(const Line1dView& v, const uint64_t* g, const float* a, size_t a_pitch, void* s,
+                              size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
+  switch (v.limbs) {
+    case 1: return launch_mesh1d_L<1>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
+    case 2: return launch_mesh1d_L<2>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
+    case 3: return launch_mesh1d_L<3>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
+    default: return launch_mesh1d_L<4>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
+  }
+}
+
+}  // namespace abf
+
+using i128 = __int128;
+
+// D beta^N(R 2^-P - d) for R in [0, 2^P) and d = dmin .. dmin + K - 1, by the
+// degree recurrence in integers: with B_n(X) = n! 2^(n P) beta^n(X 2^-P),
+//   B_0(X) = 1 on (-2^(P-1), 2^(P-1)]  (beta^0 of Sec. 2),
+//   B_n(X) = (X + (n+1) 2^(P-1)) B_{n-1}(X + 2^(P-1)) + ((n+1) 2^(P-1) - X) B_{n-1}(X - 2^(P-1)).
+static bool build_table_1d(int N, int P, int K, int dmin, std::vector<uint64_t>& out, unsigned long long* D) {
+  const long long h = 1ll << (P - 1);
+  // B_n tabulated on X in [-(N+1) h - h, (N+1) h + h]
+  const long long lo = -(N + 2) * h, hi = (N + 2) * h;
+  const size_t span = (size_t)(hi - lo + 1);
+  std::vector<i128> prev(span, 0), cur(span, 0);
+  for (long long X = lo; X <= hi; ++X) prev[(size_t)(X - lo)] = (X > -h && X <= h) ? 1 : 0;
+  for (int n = 1; n <= N; ++n) {
+    for (long long X = lo; X <= hi; ++X) {
+      const long long Xa = X + h, Xb = X - h;
+      const i128 ba = (Xa >= lo && Xa <= hi) ? prev[(size_t)(Xa - lo)] : 0;
+      const i128 bb = (Xb >= lo && Xb <= hi) ? prev[(size_t)(Xb - lo)] : 0;
+      cur[(size_t)(X - lo)] = (i128)(X + (n + 1) * h) * ba + (i128)((n + 1) * h - X) * bb;
+    }
+    prev.swap(cur);
+  }
+  i128 Dv = 1;
+  for (int i = 2; i <= N; ++i) Dv *= i;
+  Dv <<= (N * P);
+  if (Dv >= ((i128)1 << 63)) return false;
+  const long long rows = 1ll << P;
+  out.assign((size_t)rows * K, 0);
+  for (long long R = 0; R < rows; ++R) {
+    i128 sum = 0;
+    for (int c = 0; c < K; ++c) {
+      const long long X = R - (long long)(dmin + c) * (1ll << P);
+      const i128 w = (X >= lo && X <= hi) ? prev[(size_t)(X - lo)] : 0;
+      if (w < 0) return false;
+      out[(size_t)R * K + c] = (uint64_t)w;
+      sum += w;
+    }
+    if (sum != Dv) return false;  // partition of unity, and no weight outside the K neighbours
+  }
+  *D = (unsigned long long)Dv;
+  return true;
+}
+
+struct abf1d_plan_s {
+  abf1d_desc desc;
+  abf::Line1dView v;
+  abf::PlanView rows;   // the row pass over the extended signals
+  uint64_t* d_table = nullptr;
+  int32_t* d_status = nullptr;
+  size_t g_bytes = 0;
+  int right = 0;
+};
+
+extern "C" {
+
+abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
+  if (!d || !out) return ABF_ERR_INVALID;
+  *out = nullptr;
+  if (d->length < 1 || d->count < 1 || d->count > 65535) return ABF_ERR_INVALID;
+  if (d->n1 < 0 || d->n2 < 0 || d->n2 > 3) return ABF_ERR_INVALID;
+  if (d->n1 > 1) return ABF_ERR_UNSUPPORTED;
+  if (d->in_dtype < ABF_U8 || d->in_dtype > ABF_F64) return ABF_ERR_INVALID;
+  if (d->out_dtype != ABF_F32 && d->out_dtype != ABF_F64) return ABF_ERR_INVALID;
+  if (d->q_bits < 1 || d->q_bits > 10 || d->in_frac_bits < 0 || d->in_frac_bits > 40) return ABF_ERR_INVALID;
+  const double qd = std::ldexp(1.0, d->q_bits);
+  if (!(d->max_scale > 0) || !(d->max_scale * qd < 1e9)) return ABF_ERR_INVALID;
+  const int Amax = (int)std::lrint(d->max_scale * qd);
+  if (Amax < 1) return ABF_ERR_INVALID;
+  double vb = d->value_bound;
+  if (!(vb > 0)) {
+    if (d->in_dtype == ABF_U8) vb = 255.0;
+    else if (d->in_dtype == ABF_U16) vb = 65535.0;
+    else return ABF_ERR_INVALID;
+  }
+  const int N = d->n1 + d->n2 + 1, P = d->q_bits + 1;
+  // neighbours d with beta^N(r - d) != 0 for some r in [0, 1): -(N+1)/2 < d < (N+3)/2
+  const int dmin = (N % 2) ? -(N + 1) / 2 + 1 : -N / 2;
+  const int K = (N % 2) ? N + 1 : N + 2;
+  std::vector<uint64_t> tab;
+  unsigned long long D = 0;
+  try {
+    if (!build_table_1d(N, P, K, dmin, tab, &D)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  // |s| <= |f|max (non-negative kernel, unit lattice sum), so
+  // |S| <= D max_scale^(n2+1) |f|max 2^F.
+  const double lb = std::log2((double)D) + (d->n2 + 1) * std::log2((double)Amax / qd) + std::log2(vb) +
+                    d->in_frac_bits + 1e-6;
+  const int L = (int)std::floor((lb + 1.0) / 64.0) + 1;
+  if (L > abf::kMaxLimbs) return ABF_ERR_RANGE;
+  abf1d_plan p = new (std::nothrow) abf1d_plan_s();
+  if (!p) return ABF_ERR_OOM;
+  p->desc = *d;
+  // samples past the end read by the adaptive step: tau_max + (N+1)/2, plus margin
+  const double tau_max = std::max(0.0, ((double)Amax / qd - 1.0) * (d->n2 + 1) / 2.0);
+  p->right = (int)std::ceil(tau_max + (N + 1) / 2.0) + 2;
+  abf::Line1dView& v = p->v;
+  v.length = d->length; v.count = d->count; v.n1 = d->n1; v.n2 = d->n2; v.N = N; v.Q = d->q_bits; v.P = P;
+  v.F = d->in_frac_bits; v.K = K; v.dmin = dmin; v.Amax = Amax; v.limbs = L; v.out_dtype = d->out_dtype;
+  v.log2_base = (float)(std::log2((double)D) + std::log2(vb) + d->in_frac_bits);
+  v.Dd = (double)D;
+  const long long Gw = (long long)d->length + p->right;
+  v.Gp = (Gw + 3) / 4 * 4;
+  abf::PlanView& r = p->rows;
+  r = abf::PlanView{};
+  r.W = d->length; r.H = d->count; r.n = d->n2 + 1; r.Q = d->q_bits; r.P = P; r.F = d->in_frac_bits;
+  r.left = 0; r.right = p->right; r.above = 0; r.Gw = (int)Gw; r.Gh = d->count; r.Gp = v.Gp;
+  r.in_dtype = d->in_dtype; r.out_dtype = d->out_dtype; r.limbs = L; r.value_bound = vb;
+  p->g_bytes = (size_t)v.Gp * (size_t)d->count * (size_t)L * 8;
+  if (cudaMalloc(&p->d_table, tab.size() * sizeof(uint64_t)) != cudaSuccess) {
+    delete p;
+    return ABF_ERR_OOM;
+  }
+  if (cudaMemcpy(p->d_table, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) {
+    cudaFree(p->d_table);
+    delete p;
+    return ABF_ERR_CUDA;
+  }
+  if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+    cudaFree(p->d_table);
+    cudaFree(p->d_status);
+    delete p;
+    return ABF_ERR_CUDA;
+  }
+  v.table = p->d_table;
+  *out = p;
+  return ABF_OK;
+}
+
+abf_status abf1d_plan_destroy(abf1d_plan p) {
+  if (!p) return ABF_ERR_INVALID;
+  if (p->d_table) cudaFree(p->d_table);
+  if (p->d_status) cudaFree(p->d_status);
+  delete p;
+  return ABF_OK;
+}
+
+abf_status abf1d_plan_query(abf1d_plan p, size_t* integrated_bytes, int32_t* right, int32_t* limbs,
+                            int64_t* g_pitch_elems) {
+  if (!p) return ABF_ERR_INVALID;
+  if (integrated_bytes) *integrated_bytes = p->g_bytes;
+  if (right) *right = p->right;
+  if (limbs) *limbs = p->v.limbs;
+  if (g_pitch_elems) *g_pitch_elems = p->v.Gp;
+  return ABF_OK;
+}
+
+abf_status abf1d_integrate(abf1d_plan p, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t st) {
+  if (!p || !d_f || !d_g) return ABF_ERR_INVALID;
+  const int dt = p->desc.in_dtype;
+  const size_t esz = dt == ABF_U8 ? 1 : dt == ABF_U16 ? 2 : dt == ABF_F32 ? 4 : 8;
+  if (f_pitch < (size_t)p->desc.length * esz || ((uintptr_t)d_g & 15)) return ABF_ERR_INVALID;
+  return abf::run_row_scan(p->rows, d_f, f_pitch, (uint64_t*)d_g, p->d_status, st) == cudaSuccess ? ABF_OK
+                                                                                                   : ABF_ERR_CUDA;
+}
+
+static abf_status filter1d(abf1d_plan p, const void* d_g, const float* d_a, size_t a_pitch, void* d_s,
+                           size_t s_pitch, void* d_num, size_t num_pitch, cudaStream_t st) {
+  if (!p || !d_g || !d_a || (!d_s && !d_num)) return ABF_ERR_INVALID;
+  if (a_pitch < (size_t)p->desc.length * sizeof(float) || ((uintptr_t)d_g & 15)) return ABF_ERR_INVALID;
+  if (d_s && s_pitch < (size_t)p->desc.length * (p->desc.out_dtype == ABF_F64 ? 8 : 4)) return ABF_ERR_INVALID;
+  if (d_num && num_pitch < (size_t)p->desc.length * 8 * p->v.limbs) return ABF_ERR_INVALID;
+  return abf::run_mesh1d(p->v, (const uint64_t*)d_g, d_a, a_pitch, d_s, s_pitch, (uint64_t*)d_num, num_pitch,
+                         p->d_status, st) == cudaSuccess
+             ? ABF_OK
+             : ABF_ERR_CUDA;
+}
+
+abf_status abf1d_filter(abf1d_plan p, const void* d_g, const float* d_a, size_t a_pitch, void* d_s, size_t s_pitch,
+                        cudaStream_t st) {
+  if (!d_s) return ABF_ERR_INVALID;
+  return filter1d(p, d_g, d_a, a_pitch, d_s, s_pitch, nullptr, 0, st);
+}
+
+abf_status abf1d_filter_numerator(abf1d_plan p, const void* d_g, const float* d_a, size_t a_pitch, void* d_num,
+                                  size_t num_pitch, cudaStream_t st) {
+  if (!d_num) return ABF_ERR_INVALID;
+  return filter1d(p, d_g, d_a, a_pitch, nullptr, 0, d_num, num_pitch, st);
+}
+
+abf_status abf1d_last_device_status(abf1d_plan p, int32_t* code) {
+  if (!p || !code) return ABF_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return ABF_ERR_CUDA;
+  int32_t val = 0;
+  if (cudaMemcpy(&val, p->d_status, sizeof(val), cudaMemcpyDeviceToHost) != cudaSuccess) return ABF_ERR_CUDA;
+  if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) return ABF_ERR_CUDA;
+  *code = val;
+  return ABF_OK;
+}
+
+}  // extern "C"

@@ -14,9 +14,10 @@
 // linearly along the line), which the FD of the mesh along v4 annihilates.
 //
 // Kernels:
-//   row_scan   : one warp per row, input conversion (a0) fused, all n folds of
-//                v1 in one pass (lane-local scans + warp shuffles, a running
-//                carry per fold).
+//   row_scan   : one CTA per row, its warps on contiguous segments; input
+//                conversion (a0) fused, all n folds of v1 together (lane-local
+//                scans + warp shuffles, a running state per fold); segment
+//                states composed through shared memory (affine carries).
 //   line_scan  : v2 / v3 / v4, one thread per line (sheared so that a warp reads
 //                consecutive addresses), lines cut into bands of R rows; bands
 //                are chained by decoupled look-back on per-line flags, with a
@@ -60,72 +61,154 @@ __device__ __forceinline__ Wide<L> warp_inclusive(Wide<L> v, int lane) {
 }
 
 // Input element -> integer f 2^F; raises ABF_DEV_BAD_INPUT (and reads 0) when
-// a floating-point value is off the 2^-F grid or beyond the value bound.
+// a floating-point value is off the 2^-F grid or beyond the value bound
+// (bound_i = floor(value_bound 2^F)).  binary32 inputs are checked in binary32
+// (scaling by 2^F is exact, rintf is exact) and integers, keeping the per-sample
+// work off the slow binary64 pipe.
 template <typename TIn>
-__device__ __forceinline__ int64_t convert_f(TIn raw, double scale, double bound, int32_t* status) {
+__device__ __forceinline__ int64_t convert_f(TIn raw, double scale, long long bound_i, int32_t* status) {
   if constexpr (sizeof(TIn) <= 2) {
     return (int64_t)raw;
-  } else {
-    const double v = (double)raw * scale;  // exact: scale is a power of two
-    const double r = rint(v);
-    if (!(r == v) || !(fabs(r) <= bound)) {
+  } else if constexpr (sizeof(TIn) == 4) {
+    const float v = raw * (float)scale;  // exact: scale is a power of two (inf if it overflows)
+    if (!(rintf(v) == v) || !(fabsf(v) < 4.0e18f)) {
       raise_status(status, ABF_DEV_BAD_INPUT);
       return 0;
     }
-    return (int64_t)r;
+    const long long r = __float2ll_rn(v);
+    if (r > bound_i || r < -bound_i) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    return r;
+  } else {
+    const double v = (double)raw * scale;  // exact: scale is a power of two
+    const double r = rint(v);
+    if (!(r == v) || !(fabs(r) < 4.0e18)) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    const long long ri = (long long)r;
+    if (ri > bound_i || ri < -bound_i) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    return ri;
   }
 }
 
-constexpr int kRowVec = 4;  // elements per lane per chunk
+constexpr int kRowVec = 4;     // elements per lane per chunk
+constexpr int kRowWarps = 8;   // warps per row (one CTA per row)
 
+// acc_k += sum_{j <= k} binom(t + k - j - 1, k - j) c_j: the zero-input
+// evolution of the cascaded-sum state c over t samples, added to acc.
+template <int L, int NF>
+__device__ __forceinline__ void transport_add(Wide<L>* acc, const Wide<L>* c, long long t) {
+  const uint64_t b1 = (uint64_t)t, b2 = (uint64_t)(t * (t + 1) / 2), b3 = (uint64_t)(t * (t + 1) / 2 * (t + 2) / 3);
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    wadd<L>(acc[k], c[k]);
+    if (k >= 1) wmac<L>(acc[k], c[k - 1], b1);
+    if (k >= 2) wmac<L>(acc[k], c[k - 2], b2);
+    if (k >= 3) wmac<L>(acc[k], c[k - 3], b3);
+  }
+}
+
+// One chunk of 32 x kRowVec samples: load (a0 fused), NF cascaded scans with
+// the running state carry[] (carry[k] = fold k's sum so far), optional store
+// through the warp's shared-memory tile (lane i holds samples 4i..4i+3; the
+// store writes 32 consecutive samples per instruction).
+template <int L, typename TIn, int NF, bool STORE>
+__device__ __forceinline__ void row_chunk(const PlanView& pv, const TIn* frow, uint64_t* grow, int x0, int lane,
+                                          double scale, long long bound, int32_t* status, Wide<L>* carry,
+                                          Wide<L>* tile) {
+  Wide<L> v[kRowVec];
+#pragma unroll
+  for (int e = 0; e < kRowVec; ++e) {
+    const int xi = x0 + lane * kRowVec + e;  // box column
+    const int x = xi - pv.left;              // image column
+    int64_t val = 0;
+    if (frow && x >= 0 && x < pv.W && xi < pv.Gw) val = convert_f<TIn>(frow[x], scale, bound, status);
+    v[e] = wfrom_i64<L>(val);
+  }
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    // lane-local inclusive scan
+#pragma unroll
+    for (int e = 1; e < kRowVec; ++e) wadd<L>(v[e], v[e - 1]);
+    Wide<L> tot = v[kRowVec - 1];
+    Wide<L> incl = warp_inclusive<L>(tot, lane);
+    Wide<L> excl = shfl_up_wide<L>(incl, 1);
+    if (lane == 0) wzero<L>(excl);
+    wadd<L>(excl, carry[k]);
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) wadd<L>(v[e], excl);
+    Wide<L> last = shfl_wide<L>(incl, 31);
+    wadd<L>(carry[k], last);
+  }
+  if constexpr (STORE) {
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) tile[lane * kRowVec + e] = v[e];
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) {
+      const int xi = x0 + e * 32 + lane;
+      if (xi < pv.Gw) wstore<L>(grow + (size_t)xi * L, tile[e * 32 + lane]);
+    }
+    __syncwarp();
+  }
+}
+
+// One CTA per row, kRowWarps warps each taking a contiguous segment of whole
+// chunks.  Phase 1: every warp scans its segment from a zero state and keeps
+// the final state (its aggregate).  Then warp w's incoming state is composed
+// from the aggregates of warps 0..w-1 by the zero-input evolution (the
+// cascaded sums are affine in the incoming state).  Phase 2: every warp
+// rescans its segment from its incoming state and stores g.  f is read
+// twice; g is written once.
 template <int L, typename TIn, int NF>
-__global__ void __launch_bounds__(256) row_scan_kernel(const PlanView pv, const TIn* __restrict__ f,
-                                                       size_t f_pitch, uint64_t* __restrict__ g,
-                                                       int32_t* status) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int y = warp;
-  if (y >= pv.Gh) return;
+__global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView pv, const TIn* __restrict__ f,
+                                                                  size_t f_pitch, uint64_t* __restrict__ g,
+                                                                  int32_t* status) {
+  __shared__ Wide<L> s_agg[kRowWarps][NF];
+  __shared__ Wide<L> s_tile[kRowWarps][32 * kRowVec];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.x;
   const double scale = ldexp(1.0, pv.F);
-  const double bound = pv.value_bound * scale;
+  const double bd = floor(pv.value_bound * scale);
+  const long long bound = bd < 4.0e18 ? (long long)bd : 4000000000000000000ll;
   const TIn* frow = (y < pv.H) ? reinterpret_cast<const TIn*>(reinterpret_cast<const char*>(f) + (size_t)y * f_pitch)
                                : nullptr;
   uint64_t* grow = g + (size_t)y * (size_t)pv.Gp * L;
+  constexpr int chunk = 32 * kRowVec;
+  const int nchunks = (pv.Gw + chunk - 1) / chunk;
+  const int per = (nchunks + kRowWarps - 1) / kRowWarps;
+  const int c0 = min(nchunks, warp * per), c1 = min(nchunks, c0 + per);
   Wide<L> carry[NF];
 #pragma unroll
   for (int k = 0; k < NF; ++k) wzero<L>(carry[k]);
-  constexpr int chunk = 32 * kRowVec;
-  for (int x0 = 0; x0 < pv.Gw; x0 += chunk) {
-    Wide<L> v[kRowVec];
+  for (int c = c0; c < c1; ++c)
+    row_chunk<L, TIn, NF, false>(pv, frow, grow, c * chunk, lane, scale, bound, status, carry, nullptr);
+  if (lane == 0) {
 #pragma unroll
-    for (int e = 0; e < kRowVec; ++e) {
-      const int xi = x0 + lane * kRowVec + e;  // box column
-      const int x = xi - pv.left;              // image column
-      int64_t val = 0;
-      if (frow && x >= 0 && x < pv.W && xi < pv.Gw) val = convert_f<TIn>(frow[x], scale, bound, status);
-      v[e] = wfrom_i64<L>(val);
-    }
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-      // lane-local inclusive scan
-#pragma unroll
-      for (int e = 1; e < kRowVec; ++e) wadd<L>(v[e], v[e - 1]);
-      Wide<L> tot = v[kRowVec - 1];
-      Wide<L> incl = warp_inclusive<L>(tot, lane);
-      Wide<L> excl = shfl_up_wide<L>(incl, 1);
-      if (lane == 0) wzero<L>(excl);
-      wadd<L>(excl, carry[k]);
-#pragma unroll
-      for (int e = 0; e < kRowVec; ++e) wadd<L>(v[e], excl);
-      Wide<L> last = shfl_wide<L>(incl, 31);
-      wadd<L>(carry[k], last);
-    }
-#pragma unroll
-    for (int e = 0; e < kRowVec; ++e) {
-      const int xi = x0 + lane * kRowVec + e;
-      if (xi < pv.Gw) wstore<L>(grow + (size_t)xi * L, v[e]);
-    }
+    for (int k = 0; k < NF; ++k) s_agg[warp][k] = carry[k];
   }
+  __syncthreads();
+  // incoming state: state_{w+1} = T_len(state_w) + agg_w; every segment
+  // before this warp's is full (per chunks)
+  Wide<L> st[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) wzero<L>(st[k]);
+  for (int w = 0; w < warp; ++w) {
+    Wide<L> nx[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) nx[k] = s_agg[w][k];
+    transport_add<L, NF>(nx, st, (long long)per * chunk);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) st[k] = nx[k];
+  }
+  for (int c = c0; c < c1; ++c)
+    row_chunk<L, TIn, NF, true>(pv, frow, grow, c * chunk, lane, scale, bound, status, st, s_tile[warp]);
 }
 
 // ---------------------------------------------------------- lines (v2, v3, v4)
@@ -294,13 +377,37 @@ __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView 
 template <int L, typename TIn>
 static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g,
                                int32_t* status, cudaStream_t st) {
-  const int warps_per_block = 8;
-  const int blocks = (pv.Gh + warps_per_block - 1) / warps_per_block;
+  const int blocks = pv.Gh;  // one CTA per row
+  const int threads = 32 * kRowWarps;
   const TIn* fin = (const TIn*)f;
-  if (pv.n == 1) row_scan_kernel<L, TIn, 1><<<blocks, 32 * warps_per_block, 0, st>>>(pv, fin, f_pitch, g, status);
-  else if (pv.n == 2) row_scan_kernel<L, TIn, 2><<<blocks, 32 * warps_per_block, 0, st>>>(pv, fin, f_pitch, g, status);
-  else row_scan_kernel<L, TIn, 3><<<blocks, 32 * warps_per_block, 0, st>>>(pv, fin, f_pitch, g, status);
+  if (pv.n == 1) row_scan_kernel<L, TIn, 1><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+  else if (pv.n == 2) row_scan_kernel<L, TIn, 2><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+  else if (pv.n == 3) row_scan_kernel<L, TIn, 3><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+  else row_scan_kernel<L, TIn, 4><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
   return cudaGetLastError();
+}
+
+// The row pass alone (pv.n cascaded sums, 1..4, along rows of the box), for
+// the 1-D filter: rows are signals, W the signal length, left = 0.
+template <int L>
+static cudaError_t rows_L(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, int32_t* status,
+                          cudaStream_t st) {
+  switch (pv.in_dtype) {
+    case ABF_U8: return launch_rows<L, uint8_t>(pv, f, f_pitch, g, status, st);
+    case ABF_U16: return launch_rows<L, uint16_t>(pv, f, f_pitch, g, status, st);
+    case ABF_F32: return launch_rows<L, float>(pv, f, f_pitch, g, status, st);
+    default: return launch_rows<L, double>(pv, f, f_pitch, g, status, st);
+  }
+}
+
+cudaError_t run_row_scan(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, int32_t* status,
+                         cudaStream_t st) {
+  switch (pv.limbs) {
+    case 1: return rows_L<1>(pv, f, f_pitch, g, status, st);
+    case 2: return rows_L<2>(pv, f, f_pitch, g, status, st);
+    case 3: return rows_L<3>(pv, f, f_pitch, g, status, st);
+    default: return rows_L<4>(pv, f, f_pitch, g, status, st);
+  }
 }
 
 template <int L, int DIR, int NF>

@@ -197,3 +197,73 @@ class Server:
         if self.h is not None:
             C.abf_server_destroy(self.h)
             self.h = None
+
+
+class AdaptiveFilter1D:
+    """The 1-D scale-adaptive B-spline filter of Sec. 3 on `count` signals of
+    `length` samples (abf1d_integrate + abf1d_filter)."""
+
+    def __init__(self, length, count, n1, n2, in_dtype, q_bits=8, frac_bits=0, max_scale=8.0, value_bound=0.0,
+                 out="f64", device=None):
+        self.device = torch.device(device or "cuda")
+        self.length, self.count = int(length), int(count)
+        self.in_dtype = in_dtype
+        self.out_code, self.out_dtype = _OUT[out]
+        d = C.abf1d_desc()
+        d.length, d.count, d.n1, d.n2 = self.length, self.count, int(n1), int(n2)
+        d.in_dtype, d.out_dtype = _DT[in_dtype], self.out_code
+        d.q_bits, d.in_frac_bits = int(q_bits), int(frac_bits)
+        d.max_scale, d.value_bound = float(max_scale), float(value_bound)
+        self.desc = d
+        self.plan = None
+        with torch.cuda.device(self.device):
+            self.plan = C.abf1d_plan_create(d)
+        self.info = C.abf1d_plan_query(self.plan)
+        self.limbs = self.info["limbs"]
+        self.g = torch.empty(max(self.info["integrated_bytes"], 16), dtype=torch.uint8, device=self.device)
+
+    def close(self):
+        if self.plan is not None:
+            C.abf1d_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, t, dtype, what):
+        if t.device != self.device or t.dtype != dtype or tuple(t.shape) != (self.count, self.length) \
+                or t.stride(1) != 1:
+            raise ValueError("%s must be a (%d, %d) %s tensor on %s" % (what, self.count, self.length, dtype,
+                                                                        self.device))
+
+    def integrate(self, f, stream=None):
+        self._check(f, self.in_dtype, "f")
+        C.abf1d_integrate(self.plan, f, f.stride(0) * f.element_size(), self.g, stream)
+
+    def filter(self, a, out=None, stream=None):
+        self._check(a, torch.float32, "a")
+        if out is None:
+            out = torch.empty((self.count, self.length), dtype=self.out_dtype, device=self.device)
+        C.abf1d_filter(self.plan, self.g, a, a.stride(0) * 4, out, out.stride(0) * out.element_size(), stream)
+        return out
+
+    def __call__(self, f, a, out=None, stream=None):
+        self.integrate(f, stream)
+        return self.filter(a, out, stream)
+
+    def numerators(self, a, stream=None):
+        self._check(a, torch.float32, "a")
+        num = torch.empty((self.count, self.length, self.limbs), dtype=torch.int64, device=self.device)
+        C.abf1d_filter_numerator(self.plan, self.g, a, a.stride(0) * 4, num, self.length * self.limbs * 8, stream)
+        return num
+
+    def integrated(self):
+        """g as (count, pitch, limbs) int64 (a view of the buffer)."""
+        pitch = self.info["g_pitch"]
+        return self.g[: self.count * pitch * self.limbs * 8].view(torch.int64).view(self.count, pitch, self.limbs)
+
+    def device_status(self):
+        return C.abf1d_last_device_status(self.plan)

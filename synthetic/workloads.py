@@ -10,6 +10,11 @@
   fields; or ellipse fields (sigma, elongation, cos theta, sin theta) with
   sigma = 1 + 23 S(64), elongation = 1 + 5 S(64), theta = pi frac(4 S(96)).
 
+* 1-D signals (Sec. 3 filter): rows of smooth + step noise, each row its own
+  smooth field along its length (Gaussian of s samples, FFT per row) plus K
+  random steps, on the 2^-16 grid (float32); scales a = lo + (hi - lo) S(s)
+  per sample.
+
 Every draw uses numpy's PCG64 generator seeded from SEED_BASE + a workload
 index (+ an image index).
 """
@@ -123,3 +128,38 @@ def batch_workload(count=64, lo=128, hi=2048, seed_offset=0):
         jobs.append(dict(image=img, frac_bits=16, scale_kind="a4", scales=sc, n=n, q_bits=8,
                          cmax=32.0, value_bound=255.0))
     return jobs
+
+
+def smooth_rows(rng, count, length, sigma):
+    """Each row an independent smooth field along its length, in [0, 1]."""
+    noise = rng.standard_normal((count, length))
+    fx = np.fft.rfftfreq(length)[None, :]
+    gain = np.exp(-2.0 * (np.pi * sigma) ** 2 * fx * fx)
+    out = np.fft.irfft(np.fft.rfft(noise, axis=1) * gain, n=length, axis=1)
+    lo, hi = out.min(axis=1, keepdims=True), out.max(axis=1, keepdims=True)
+    return (out - lo) / np.where(hi > lo, hi - lo, 1.0)
+
+
+def signals_1d(rng, count, length, smooth=64.0, steps=8, frac_bits=16):
+    """255 clip(0.7 S + steps) on the 2^-frac_bits grid, float32 rows."""
+    v = 0.7 * smooth_rows(rng, count, length, smooth)
+    for _ in range(steps):
+        at = rng.integers(0, length, count)
+        amp = rng.uniform(0.1, 0.3, count) * np.where(rng.uniform(size=count) < 0.5, 1.0, -1.0)
+        v += amp[:, None] * (np.arange(length)[None, :] >= at[:, None])
+    q = float(1 << frac_bits)
+    return (np.round(255.0 * np.clip(v, 0, 1) * q) / q).astype(np.float32)
+
+
+def scales_1d(rng, count, length, lo, hi, smooth):
+    return (lo + (hi - lo) * smooth_rows(rng, count, length, smooth)).astype(np.float32)
+
+
+def workload_1d(count=2048, length=65536, seed_offset=0):
+    """The 1-D filter workload: float32 signals on the 2^-16 grid, model degree
+    n1 = 1, analysis degree n2 = 3, scales a in [1, 64] varying smoothly
+    (S(2048)) along each signal, Q = 8."""
+    rng = np.random.default_rng(SEED_BASE + 5 + seed_offset)
+    f = signals_1d(rng, count, length)
+    a = scales_1d(rng, count, length, 1.0, 64.0, 2048.0)
+    return dict(signals=f, scales=a, n1=1, n2=3, q_bits=8, frac_bits=16, max_scale=64.0, value_bound=255.0)
