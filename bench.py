@@ -198,6 +198,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    tuned_rows, tuned_ms = filt.autotune(s_t, out)
+    torch.cuda.synchronize()
     assert filt.device_status() == 0
 
     K = args.steps
@@ -310,6 +312,7 @@ def run_ours(args):
         # (v2, v3, v4), one mesh launch
         "gpu_launches": int(K * (1 + 3 + 1)),
         "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
+        "autotune": {"rows_per_cta": tuned_rows, "candidates": [4, 8, 16], "ms": [round(t, 3) for t in tuned_ms]},
         "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak_macs / 1e9, 2),
                      "unit": "G MAC/s (%d-limb integer x %d-bit weight)" % (L, 32 * wwords),
                      "frac": round(achieved / peak_macs, 4),
@@ -377,6 +380,8 @@ def run_batch(args):
             batch(imgs, scs, outs)
     torch.cuda.current_stream(dev).wait_stream(side)
     torch.cuda.synchronize()
+    tuned_rows, tuned_ms = batch.autotune(imgs, scs, outs)
+    torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         batch(imgs, scs, outs)
@@ -402,7 +407,9 @@ def run_batch(args):
     torch.cuda.synchronize()
     single_ms = t0.elapsed_time(t1)
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
-    n_launch = sum(1 + 3 * w["n"] for w in jobs) + 1
+    # per image a row scan and three line scans, then one batch launch per
+    # (order, limbs) group present
+    n_launch = 4 * len(jobs) + len(set((w["n"], f.limbs) for w, f in zip(jobs, fl)))
     line = {"metric": METRIC, "value": round(pix / (batch_ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(batch_ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64 limbs (2 or 4 per image)", "data": "synthetic",
@@ -412,6 +419,8 @@ def run_batch(args):
             "gpu_launches": int(K * n_launch),
             "batched_vs_single": {"batched_ms": round(batch_ms, 3), "single_ms": round(single_ms, 3),
                                   "speedup": round(single_ms / batch_ms, 3), "bit_identical": bool(same)},
+            "autotune": {"rows_per_cta": tuned_rows, "candidates": [4, 8, 16],
+                         "ms": [round(t, 3) for t in tuned_ms]},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     for f in fl:
@@ -718,7 +727,7 @@ def main():
     ap.add_argument("--inflight", type=int, default=4, help="c5: concurrent jobs (slots)")
     ap.add_argument("--jobs", type=int, default=200, help="c5: measured jobs per load")
     ap.add_argument("--sat-jobs", dest="sat_jobs", type=int, default=48, help="c5: jobs of the saturation burst")
-    ap.add_argument("--compare", default="plain_f64",
+    ap.add_argument("--compare", default="plain_f64,tile_f32",
                     help="comma-separated forms timed beside the exact form ('' for none)")
     args = ap.parse_args()
     args.compare = [c for c in args.compare.split(",") if c]

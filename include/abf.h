@@ -200,6 +200,22 @@ abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size
                             cudaStream_t stream);
 int32_t abf_batch_max_jobs(void);
 
+/* Autotuner (no counterpart in the paper: a launch-shape choice).  The exact
+ * mesh runs a CTA over R consecutive rows of 32-pixel runs (R warps; their
+ * taps share g patches in L1).  These calls time R = 4, 8, 16 on the caller's
+ * own data (one untimed and one timed run each, CUDA events on `stream`,
+ * which they synchronise) and keep the fastest: abf_plan_autotune in the plan
+ * (used by later abf_filter / abf_filter_numerator calls), abf_batch_autotune
+ * in a process-wide cache keyed by the batch's composition (the sorted
+ * (n, limbs, width, height) of its images; used by later abf_filter_batch
+ * calls on batches of that composition).  Outputs are written as by
+ * abf_filter / abf_filter_batch.  *warps_out = the choice; ms3 (optional):
+ * the three times in ms.                                                     */
+abf_status abf_plan_autotune(abf_plan plan, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_s,
+                             size_t s_pitch, cudaStream_t stream, int32_t* warps_out, float* ms3);
+abf_status abf_batch_autotune(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                              int32_t* warps_out, float* ms3);
+
 /* ------------------------------------------------------------------ serving
  * A request loop for filter jobs (image + per-pixel scale field, host memory)
  * on one GPU.  A worker thread admits queued jobs in arrival order as long as

@@ -94,6 +94,8 @@ def lib():
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
         "abf_batch_max_jobs": ([], i32),
+        "abf_plan_autotune": ([vp, vp, vp, sz, vp, sz, vp, P(i32), P(ctypes.c_float)], st),
+        "abf_batch_autotune": ([P(abf_job), i32, vp, sz, vp, P(i32), P(ctypes.c_float)], st),
         "abf_server_create": ([P(abf_server_cfg), P(vp)], st),
         "abf_submit": ([vp, P(abf_request), P(ctypes.c_uint64)], st),
         "abf_poll": ([vp, ctypes.c_uint64, P(i32), P(abf_job_stats)], st),
@@ -313,3 +315,21 @@ def abf1d_last_device_status(plan):
     v = ctypes.c_int32()
     _check(lib().abf1d_last_device_status(plan, ctypes.byref(v)), "abf1d_last_device_status")
     return v.value
+
+
+# ----------------------------------------------------------------- autotuner
+
+def abf_plan_autotune(plan, g, scales, scale_pitch, s, s_pitch, stream=None):
+    """Times 4, 8 and 16 rows per CTA on this data; returns (choice, [ms x 3])."""
+    w, ms = ctypes.c_int32(), (ctypes.c_float * 3)()
+    _check(lib().abf_plan_autotune(plan, _ptr(g), _ptr(scales), scale_pitch, _ptr(s), s_pitch, _stream(stream),
+                                   ctypes.byref(w), ms), "abf_plan_autotune")
+    return w.value, list(ms)
+
+
+def abf_batch_autotune(jobs, ws, stream=None):
+    arr = (abf_job * len(jobs))(*jobs)
+    w, ms = ctypes.c_int32(), (ctypes.c_float * 3)()
+    _check(lib().abf_batch_autotune(arr, len(jobs), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
+                                    ctypes.byref(w), ms), "abf_batch_autotune")
+    return w.value, list(ms)

@@ -638,4 +638,5 @@ struct abf_plan_s {
   int device;
   int32_t* d_status = nullptr;
   size_t g_bytes = 0, ws_bytes = 0;
+  int mesh_warps = 8;          // rows per CTA of the exact mesh (abf_plan_autotune)
 };

@@ -103,7 +103,8 @@ __device__ __forceinline__ void store_out(void* s, size_t s_pitch, int x, int y,
 // with the sign choosing one of two accumulators.  Each lane accumulates
 // w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
 // numerator, which lane i keeps for its own pixel and stores at the end.
-constexpr int kMeshWarps = 8;
+constexpr int kMeshWarps = 8;      // default rows (warps) per CTA
+constexpr int kMeshWarpsMax = 16;  // largest CTA the kernels are compiled for
 
 // The stencil's neighbours, in the same order as the table rows (one thread).
 template <int N>
@@ -481,17 +482,19 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
 // with the sign choosing one of two accumulators.  Each lane accumulates
 // w_j g[p_j + d] W(r_j - d) modulo 2^(64 L); a warp reduction gives the
 // numerator, which lane i keeps for its own pixel and stores at the end.
-// A CTA takes the 32-column runs of kMeshWarps consecutive rows: neighbouring
-// rows have nearby taps, so their g patches are shared in L1.
+// A CTA takes the 32-column runs of blockDim.x / 32 consecutive rows (a
+// launch parameter, 4 to 16, chosen by the plan's autotuner): neighbouring
+// rows have nearby taps, so their g patches are shared in L1.  Each warp's tap
+// table lives in dynamic shared memory.
 template <int N, int L, bool FAST>
-__global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
+__global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_exact_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R], s_off[R];
   __shared__ unsigned char s_order[TAPS], s_perm[8 * R];
-  __shared__ int4 s_tap[kMeshWarps][TAPS];
+  extern __shared__ int4 s_tap[];
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
     if constexpr (FAST && N == 2) fill_n2_order(s_order);
@@ -501,18 +504,19 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_exact_kernel(
   if (threadIdx.x < R) s_off[threadIdx.x] = s_dy[threadIdx.x] * (int)pv.Gp + s_dx[threadIdx.x];
   if constexpr (FAST && N == 3) fill_n3_perm(s_perm, s_dx, s_dy);
   __syncthreads();
+  const int rows = blockDim.x >> 5;
   const int segs = (pv.W + 31) >> 5;
   const int band = blockIdx.x / segs;
-  const int y = band * kMeshWarps + (threadIdx.x >> 5);
+  const int y = band * rows + (threadIdx.x >> 5);
   if (y >= pv.H) return;
   const int x0 = (blockIdx.x - band * segs) * 32;
   mesh_run<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
-                       s_tap[threadIdx.x >> 5], s_dx, s_dy, s_order, s_off, s_perm);
+                       s_tap + (threadIdx.x >> 5) * TAPS, s_dx, s_dy, s_order, s_off, s_perm);
 }
 
 // ------------------------------------------------------------------- batches
 // Many images (each its own plan: size, order n, limbs) in one persistent
-// launch per (order n, limbs, fast path).  The images' units (kMeshWarps rows x 32 columns) are
+// launch per (order n, limbs, fast path).  The images' units (rows x 32 columns) are
 // numbered consecutively, the most expensive images first; every CTA
 // repeatedly takes the next unit from a global counter and filters it with its
 // image's plan, so images of uneven size share the GPU without a tail of idle
@@ -545,18 +549,18 @@ __device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int 
                        sdx, sdy, order, soff, perm);
 }
 
-// A unit is the 32-column runs of kMeshWarps consecutive rows of one image (one
-// per warp of the CTA, as in the single-image launch); CTAs take units from a
+// A unit is the 32-column runs of blockDim.x / 32 consecutive rows of one image
+// (one per warp of the CTA, as in the single-image launch); CTAs take units from a
 // global counter.  One kernel per order n, so that each gets its own register
 // budget; the images of one launch share n and differ in size and limbs.
 template <int N, int L, bool FAST>
-__global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
-                                                                     unsigned long long* counter) {
+__global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
+                                                                        unsigned long long* counter) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R], s_off[R];
   __shared__ unsigned char s_order[TAPS], s_perm[8 * R];
-  __shared__ int4 s_tap[kMeshWarps][TAPS];
+  extern __shared__ int4 s_tap[];
   __shared__ unsigned long long s_item;
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
@@ -567,8 +571,8 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __gri
     __syncthreads();
     fill_n3_perm(s_perm, s_dx, s_dy);
   }
-  const int warp = threadIdx.x >> 5;
-  int4* taps = s_tap[warp];
+  const int warp = threadIdx.x >> 5, rows = blockDim.x >> 5;
+  int4* taps = s_tap + warp * TAPS;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
     __syncthreads();
@@ -586,7 +590,7 @@ __global__ void __launch_bounds__(32 * kMeshWarps) mesh_batch_kernel(const __gri
     __syncthreads();
     const long long u = (long long)item - jb.units_begin;
     const int band = (int)(u / jb.segs);
-    const int y = band * kMeshWarps + warp;
+    const int y = band * rows + warp;
     const int x0 = (int)(u - (long long)band * jb.segs) * 32;
     if (y >= jb.pv.H) continue;
     batch_dispatch_L<N, L, FAST>(jb, y, x0, taps, s_dx, s_dy, s_order, s_off, s_perm);
@@ -661,42 +665,60 @@ static bool mesh_fast_ok(const PlanView& pv) {
          (pv.n != 3 || pv.table_fold != nullptr);
 }
 
+// Dynamic shared memory of a launch with `warps` rows per CTA: one tap table
+// per warp; above 48 KB the kernel must opt in.
+template <typename K>
+static cudaError_t tap_smem(K kernel, int taps, int warps, size_t* bytes) {
+  *bytes = (size_t)warps * taps * sizeof(int4);
+  if (*bytes > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+  return cudaSuccess;
+}
+
 template <int N, int L>
 static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch,
                                   void* s, size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
-                                  cudaStream_t st) {
-  const long long grid = (long long)((pv.W + 31) / 32) * ((pv.H + kMeshWarps - 1) / kMeshWarps);
-  const int block = 32 * kMeshWarps;
+                                  int warps, cudaStream_t st) {
+  constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
+  const long long grid = (long long)((pv.W + 31) / 32) * ((pv.H + warps - 1) / warps);
+  const int block = 32 * warps;
+  size_t smem = 0;
+  cudaError_t e;
   if constexpr (N >= 2) {
     if (mesh_fast_ok(pv)) {
-      mesh_exact_kernel<N, L, true><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
-                                                            num, num_pitch, status);
+      if ((e = tap_smem(mesh_exact_kernel<N, L, true>, TAPS, warps, &smem)) != cudaSuccess) return e;
+      mesh_exact_kernel<N, L, true><<<grid, block, smem, st>>>(pv, g, (const float4*)scales, scale_pitch, s,
+                                                               s_pitch, num, num_pitch, status);
       return cudaGetLastError();
     }
   }
-  mesh_exact_kernel<N, L, false><<<grid, block, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch, num,
-                                                         num_pitch, status);
+  if ((e = tap_smem(mesh_exact_kernel<N, L, false>, TAPS, warps, &smem)) != cudaSuccess) return e;
+  mesh_exact_kernel<N, L, false><<<grid, block, smem, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
+                                                            num, num_pitch, status);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t launch_mesh_N(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch,
                                  void* s, size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
-                                 cudaStream_t st) {
+                                 int warps, cudaStream_t st) {
   switch (pv.limbs) {
-    case 1: return launch_mesh_NL<N, 1>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-    case 2: return launch_mesh_NL<N, 2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-    case 3: return launch_mesh_NL<N, 3>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-    default: return launch_mesh_NL<N, 4>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    case 1: return launch_mesh_NL<N, 1>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
+    case 2: return launch_mesh_NL<N, 2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
+    case 3: return launch_mesh_NL<N, 3>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
+    default: return launch_mesh_NL<N, 4>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
   }
 }
 
+// warps: rows per CTA (4..16; out of range falls back to the default).
 cudaError_t run_mesh_exact(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
-                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
+                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, int warps,
+                           cudaStream_t st) {
+  if (warps < 1 || warps > kMeshWarpsMax) warps = kMeshWarps;
   switch (pv.n) {
-    case 1: return launch_mesh_N<1>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-    case 2: return launch_mesh_N<2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-    default: return launch_mesh_N<3>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    case 1: return launch_mesh_N<1>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
+    case 2: return launch_mesh_N<2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
+    default: return launch_mesh_N<3>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, warps, st);
   }
 }
 
@@ -715,31 +737,37 @@ struct BatchIn {
 int batch_max_jobs() { return kMaxBatch; }
 
 template <int N, int L, bool FAST>
-static cudaError_t launch_batch_NL(const BatchJobs& jobs, unsigned long long* counter, cudaStream_t st) {
+static cudaError_t launch_batch_NL(const BatchJobs& jobs, unsigned long long* counter, int warps,
+                                   cudaStream_t st) {
+  constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  size_t smem = 0;
+  if ((e = tap_smem(mesh_batch_kernel<N, L, FAST>, TAPS, warps, &smem)) != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel<N, L, FAST>, 32 * kMeshWarps, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel<N, L, FAST>, 32 * warps, smem);
   if (per_sm < 1) per_sm = 1;
-  mesh_batch_kernel<N, L, FAST><<<sms * per_sm, 32 * kMeshWarps, 0, st>>>(jobs, counter);
+  mesh_batch_kernel<N, L, FAST><<<sms * per_sm, 32 * warps, smem, st>>>(jobs, counter);
   return cudaGetLastError();
 }
 
 template <int N, bool FAST>
-static cudaError_t launch_batch_N(int L, const BatchJobs& jobs, unsigned long long* counter, cudaStream_t st) {
+static cudaError_t launch_batch_N(int L, const BatchJobs& jobs, unsigned long long* counter, int warps,
+                                  cudaStream_t st) {
   switch (L) {
-    case 1: return launch_batch_NL<N, 1, FAST>(jobs, counter, st);
-    case 2: return launch_batch_NL<N, 2, FAST>(jobs, counter, st);
-    case 3: return launch_batch_NL<N, 3, FAST>(jobs, counter, st);
-    default: return launch_batch_NL<N, 4, FAST>(jobs, counter, st);
+    case 1: return launch_batch_NL<N, 1, FAST>(jobs, counter, warps, st);
+    case 2: return launch_batch_NL<N, 2, FAST>(jobs, counter, warps, st);
+    case 3: return launch_batch_NL<N, 3, FAST>(jobs, counter, warps, st);
+    default: return launch_batch_NL<N, 4, FAST>(jobs, counter, warps, st);
   }
 }
 
 // One persistent launch per (order n, limbs, fast path or not) present, most
 // expensive first; counter: 32 64-bit counters (one per launch), device memory.
-cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st) {
+cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, int warps, cudaStream_t st) {
+  if (warps < 1 || warps > kMeshWarpsMax) warps = kMeshWarps;
   auto cost = [&](int i) { return (double)in[i].pv.W * in[i].pv.H; };
   int launch = 0;
   for (int n = 3; n >= 1; --n) {
@@ -772,14 +800,16 @@ cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* cou
           jb.status = b.status;
           jb.segs = (b.pv.W + 31) / 32;
           jb.units_begin = units;
-          units += (long long)jb.segs * ((b.pv.H + kMeshWarps - 1) / kMeshWarps);
+          units += (long long)jb.segs * ((b.pv.H + warps - 1) / warps);
         }
         jobs.total_units = units;
         unsigned long long* ctr = counter + launch++;
         cudaError_t e;
-        if (n == 1) e = launch_batch_N<1, false>(L, jobs, ctr, st);
-        else if (n == 2) e = fast ? launch_batch_N<2, true>(L, jobs, ctr, st) : launch_batch_N<2, false>(L, jobs, ctr, st);
-        else e = fast ? launch_batch_N<3, true>(L, jobs, ctr, st) : launch_batch_N<3, false>(L, jobs, ctr, st);
+        if (n == 1) e = launch_batch_N<1, false>(L, jobs, ctr, warps, st);
+        else if (n == 2) e = fast ? launch_batch_N<2, true>(L, jobs, ctr, warps, st)
+                                  : launch_batch_N<2, false>(L, jobs, ctr, warps, st);
+        else e = fast ? launch_batch_N<3, true>(L, jobs, ctr, warps, st)
+                      : launch_batch_N<3, false>(L, jobs, ctr, warps, st);
         if (e != cudaSuccess) return e;
       }
     }

@@ -33,7 +33,8 @@ cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uin
                           uint32_t* epoch, int32_t* status, cudaStream_t st);
 size_t line_ws_bytes(int Gw, int Gh, int L, int n, int* nbands_out, int* nlines_out);
 cudaError_t run_mesh_exact(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
-                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st);
+                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, int warps,
+                           cudaStream_t st);
 cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t scale_pitch, void* C, size_t C_pitch,
                                int32_t* status, cudaStream_t st);
 cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t scale_pitch,
@@ -49,7 +50,7 @@ struct BatchIn {
   int32_t* status;
 };
 int batch_max_jobs();
-cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, cudaStream_t st);
+cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, int warps, cudaStream_t st);
 size_t tile_ws_bytes(const PlanView& pv, int real_bytes, int* slots_out, size_t* slot_elems_out, size_t* off_bmax,
                      size_t* off_tiles, size_t* off_cnt, size_t* off_scratch);
 cudaError_t run_tiles(const PlanView& pv, bool f64, const void* f, size_t f_pitch, const void* scales,
@@ -599,7 +600,7 @@ abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const voi
                                       scale_pitch, d_s, s_pitch, d_ws, p->real_table, p->d_status, st));
   }
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_src, d_scales, scale_pitch, d_s, s_pitch,
-                                         nullptr, 0, p->d_status, st));
+                                         nullptr, 0, p->d_status, p->mesh_warps, st));
 }
 
 abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_num,
@@ -610,15 +611,21 @@ abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scale
   if (scale_pitch < (size_t)p->pv.W * 16 || num_pitch < (size_t)p->pv.W * 8 * p->pv.limbs) return ABF_ERR_INVALID;
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, nullptr, 0,
-                                         (uint64_t*)d_num, num_pitch, p->d_status, st));
+                                         (uint64_t*)d_num, num_pitch, p->d_status, p->mesh_warps, st));
 }
 
 int32_t abf_batch_max_jobs(void) { return abf::batch_max_jobs(); }
 
-abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t st) {
-  if (!jobs || njobs < 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
-  if (njobs == 0) return ABF_OK;
-  std::vector<abf::BatchIn> in((size_t)njobs);
+}  // extern "C"
+
+// Batch tuning cache: the rows per CTA chosen for a batch composition (the
+// sorted (n, limbs, width, height) of its images), process-wide.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_batch_tuned;
+
+static abf_status batch_inputs(const abf_job* jobs, int32_t njobs, std::vector<abf::BatchIn>& in, std::string* key) {
+  in.resize((size_t)njobs);
+  std::vector<std::tuple<int, int, int, int>> sig;
   for (int i = 0; i < njobs; ++i) {
     const abf_job& j = jobs[i];
     abf_plan p = j.plan;
@@ -628,13 +635,120 @@ abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size
     if (j.scale_pitch < (size_t)p->pv.W * 16 || j.s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
     if (((uintptr_t)j.d_scales & 15) || (j.scale_pitch & 15)) return ABF_ERR_INVALID;
     in[i] = abf::BatchIn{p->pv, (const uint64_t*)j.d_g, j.d_scales, j.scale_pitch, j.d_s, j.s_pitch, p->d_status};
+    sig.emplace_back(p->pv.n, p->pv.limbs, p->pv.W, p->pv.H);
   }
+  if (key) {
+    std::sort(sig.begin(), sig.end());
+    key->clear();
+    for (auto& t : sig) {
+      char buf[64];
+      std::snprintf(buf, sizeof buf, "%d.%d.%d.%d;", std::get<0>(t), std::get<1>(t), std::get<2>(t), std::get<3>(t));
+      *key += buf;
+    }
+  }
+  return ABF_OK;
+}
+
+static cudaError_t batch_launch(const std::vector<abf::BatchIn>& in, void* d_ws, int warps, cudaStream_t st) {
   const int chunk = abf::batch_max_jobs();
+  const int njobs = (int)in.size();
   for (int b = 0; b < njobs; b += chunk) {
     const int k = std::min(chunk, njobs - b);
-    cudaError_t e = abf::run_mesh_batch(in.data() + b, k, (unsigned long long*)d_ws, st);
-    if (e != cudaSuccess) return ABF_ERR_CUDA;
+    cudaError_t e = abf::run_mesh_batch(in.data() + b, k, (unsigned long long*)d_ws, warps, st);
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+// The tuner's candidates: rows (warps) per CTA of the mesh.
+static const int kTuneWarps[3] = {4, 8, 16};
+
+// Times fn(warps) for every candidate (one untimed run, then one timed run
+// with CUDA events on the stream) and returns the fastest; ms[3] gets the
+// times (ms).  Synchronises the stream.
+template <typename F>
+static abf_status tune_warps(F fn, cudaStream_t st, int* best, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return ABF_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ABF_ERR_CUDA;
+  }
+  abf_status res = ABF_OK;
+  float bestms = 0;
+  for (int i = 0; i < 3 && res == ABF_OK; ++i) {
+    if (fn(kTuneWarps[i]) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
+        fn(kTuneWarps[i]) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+        cudaEventSynchronize(e1) != cudaSuccess) {
+      res = ABF_ERR_CUDA;
+      break;
+    }
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (ms) ms[i] = t;
+    if (i == 0 || t < bestms) {
+      bestms = t;
+      *best = kTuneWarps[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return res;
+}
+
+extern "C" {
+
+abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t st) {
+  if (!jobs || njobs < 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  if (njobs == 0) return ABF_OK;
+  std::vector<abf::BatchIn> in;
+  std::string key;
+  abf_status s = batch_inputs(jobs, njobs, in, &key);
+  if (s != ABF_OK) return s;
+  int warps = 8;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_batch_tuned.find(key);
+    if (it != g_batch_tuned.end()) warps = it->second;
+  }
+  return batch_launch(in, d_ws, warps, st) == cudaSuccess ? ABF_OK : ABF_ERR_CUDA;
+}
+
+abf_status abf_plan_autotune(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_s,
+                             size_t s_pitch, cudaStream_t st, int32_t* warps_out, float* ms3) {
+  if (!p || !d_g || !d_scales || !d_s) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
+  if (scale_pitch < (size_t)p->pv.W * 16 || s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  int best = p->mesh_warps;
+  abf_status s = tune_warps(
+      [&](int w) {
+        return abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, d_s, s_pitch, nullptr, 0,
+                                   p->d_status, w, st);
+      },
+      st, &best, ms3);
+  if (s != ABF_OK) return s;
+  p->mesh_warps = best;
+  if (warps_out) *warps_out = best;
+  return ABF_OK;
+}
+
+abf_status abf_batch_autotune(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t st,
+                              int32_t* warps_out, float* ms3) {
+  if (!jobs || njobs <= 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  std::vector<abf::BatchIn> in;
+  std::string key;
+  abf_status s = batch_inputs(jobs, njobs, in, &key);
+  if (s != ABF_OK) return s;
+  int best = 8;
+  s = tune_warps([&](int w) { return batch_launch(in, d_ws, w, st); }, st, &best, ms3);
+  if (s != ABF_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_batch_tuned[key] = best;
+  }
+  if (warps_out) *warps_out = best;
   return ABF_OK;
 }
 

@@ -86,6 +86,14 @@ class AdaptiveFilter:
             return self.filter(scales, out, stream)
         return self.filter(scales, out, stream, f=f)
 
+    def autotune(self, scales, out=None, stream=None):
+        """Exact form: time 4, 8 and 16 rows per CTA on the integrated image and
+        these scales, keep the fastest; returns (rows, [ms x 3])."""
+        sp = self._check_scales(scales)
+        if out is None:
+            out = torch.empty((self.H, self.W), dtype=self.out_dtype, device=self.device)
+        return C.abf_plan_autotune(self.plan, self.g, scales, sp, out, self.W * out.element_size(), stream)
+
     def numerators(self, scales, stream=None):
         sp = self._check_scales(scales)
         num = torch.empty((self.H, self.W, self.limbs), dtype=torch.int64, device=self.device)
@@ -130,6 +138,17 @@ class Batch:
                                   flt.W * o.element_size()))
         C.abf_filter_batch(jobs, self.ws, stream)
         return outs
+
+    def autotune(self, images, scales, outs, stream=None):
+        """Integrate, then time the batch launch at 4, 8 and 16 rows per CTA and
+        cache the fastest for batches of this composition; returns (rows, [ms x 3])."""
+        jobs = []
+        for flt, f, sc, o in zip(self.filters, images, scales, outs):
+            flt.integrate(f, stream)
+            flt._check_scales(sc)
+            jobs.append(C.abf_job(flt.plan.value, flt.g.data_ptr(), sc.data_ptr(), flt.W * 16, o.data_ptr(),
+                                  flt.W * o.element_size()))
+        return C.abf_batch_autotune(jobs, self.ws, stream)
 
 
 def make_desc(width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0, max_scale=8.0, out="f64",

@@ -94,3 +94,33 @@ def test_batch_replays_from_cuda_graph():
     torch.cuda.synchronize()
     for r, o in zip(ref, outs):
         assert torch.equal(r, o)
+
+
+def test_autotuned_launch_shapes_give_identical_results():
+    """The autotuner's candidates (4, 8, 16 rows per CTA) change only the
+    launch shape: the single-image and the batched outputs stay bit-identical
+    to the default launch, and the tuned choice is used afterwards."""
+    import torch
+    from paper_0908_3861_gb300 import Batch
+    dev = "cuda:0"
+    jobs = _jobs(6, 30, 140, 11)
+    fl = _filters(jobs, dev)
+    imgs = [gu.to_device(w["image"], dev) for w in jobs]
+    scs = [gu.to_device(w["scales"], dev) for w in jobs]
+    ref = [f(i, s).clone() for f, i, s in zip(fl, imgs, scs)]
+    for f, s, r in zip(fl, scs, ref):
+        rows, ms = f.autotune(s)
+        assert rows in (4, 8, 16) and len(ms) == 3 and all(t > 0 for t in ms)
+        assert torch.equal(f.filter(s), r)
+    b = Batch(fl, dev)
+    outs = [torch.full_like(r, -1.0) for r in ref]
+    rows, ms = b.autotune(imgs, scs, outs)
+    assert rows in (4, 8, 16)
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    outs2 = [torch.full_like(r, -1.0) for r in ref]
+    b(imgs, scs, outs2)
+    torch.cuda.synchronize()
+    for o, r in zip(outs2, ref):
+        assert torch.equal(o, r)
+    assert all(f.device_status() == 0 for f in fl)
