@@ -105,6 +105,11 @@ __device__ __forceinline__ void store_out(void* s, size_t s_pitch, int x, int y,
 // numerator, which lane i keeps for its own pixel and stores at the end.
 constexpr int kMeshWarps = 8;      // default rows (warps) per CTA
 constexpr int kMeshWarpsMax = 16;  // largest CTA the kernels are compiled for
+// Per order: the largest CTA (rows) and the CTAs per SM the register budget is
+// set for -- order 3 keeps its wide accumulators in up to 85 registers with
+// CTAs of at most 8 rows, orders 1 and 2 fit 64 registers at 16 rows.
+__host__ __device__ constexpr int mesh_max_warps(int n) { return n == 3 ? 8 : 16; }
+__host__ __device__ constexpr int mesh_min_ctas(int n) { return n == 3 ? 3 : 2; }
 
 // The stencil's neighbours, in the same order as the table rows (one thread).
 template <int N>
@@ -193,39 +198,77 @@ __device__ __forceinline__ void fill_n3_perm(unsigned char* perm, const int* s_d
   __syncthreads();
 }
 
-// One pixel's numerator share for n = 3.  The 69 stencil neighbours do not
-// fit a warp, so the (tap, neighbour) pairs of a group are dealt to the lanes
-// in order: lane i starts at neighbour i of the group's first tap and steps by
-// 32 pairs.  taps[s] = (g offset of the tap's lattice point, offset of its
-// row in the folded table, lattice row, symmetry); s_off[c] = dy_c Gp + dx_c;
-// s_perm[sym 69 + c] = the folded column of neighbour c.  CHECK drops reads of
-// rows below 0.
+// A lane's fixed share of the order-3 stencil: neighbours A = lane, B = 32 +
+// lane (two full passes per tap) and C = 64 + lane % 5 (the packed pass that
+// covers neighbours 64..68 of four taps with lanes 0..19): their g offsets
+// dy Gp + dx, rows dy, and folded-table columns under the eight symmetries
+// (byte sym of perm*).
+struct N3Lane {
+  int offA, offB, offC, dyA, dyB, dyC;
+  uint32_t permA[2], permB[2], permC[2];
+};
+
+__device__ __forceinline__ int perm_col(const uint32_t (&pk)[2], int sym) {
+  const uint32_t w = (sym & 4) ? pk[1] : pk[0];  // a select, not an indexed (local-memory) load
+  return (int)((w >> ((sym & 3) * 8)) & 0xffu);
+}
+
+__device__ __forceinline__ N3Lane n3_lane(int lane, const int* s_off, const int* s_dy, const unsigned char* s_perm) {
+  constexpr int R = 69;
+  N3Lane ln;
+  const int cA = lane, cB = 32 + lane, cC = 64 + lane % 5;
+  ln.offA = s_off[cA]; ln.offB = s_off[cB]; ln.offC = s_off[cC];
+  ln.dyA = s_dy[cA]; ln.dyB = s_dy[cB]; ln.dyC = s_dy[cC];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t a = 0, b = 0, c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int sym = 4 * h + k;
+      a |= (uint32_t)s_perm[sym * R + cA] << (8 * k);
+      b |= (uint32_t)s_perm[sym * R + cB] << (8 * k);
+      c |= (uint32_t)s_perm[sym * R + cC] << (8 * k);
+    }
+    ln.permA[h] = a; ln.permB[h] = b; ln.permC[h] = c;
+  }
+  return ln;
+}
+
+// One pixel's numerator share for n = 3.  taps[s] = (g offset of the tap's
+// lattice point, offset of its row in the folded table, lattice row,
+// symmetry).  Every group of taps is taken four at a time: each tap in two
+// full passes (neighbours 0..31 and 32..63, lane = neighbour, the tap record
+// broadcast), then one packed pass in which lanes 0..19 cover neighbours
+// 64..68 of the four taps (276 of 288 lane slots busy).  CHECK drops this
+// lane's read where its own row is below 0.
 template <int L, bool CHECK>
 __device__ __forceinline__ void n3_pixel(Wide<L>& acc, const int4* taps, const uint64_t* __restrict__ g,
-                                         const ulonglong2* __restrict__ table, const int* s_off, const int* s_dy,
-                                         const unsigned char* s_perm, int lane) {
-  constexpr int R = 69;
+                                         const ulonglong2* __restrict__ table, const N3Lane& ln, int lane) {
 #pragma unroll 1
   for (int gi = 0; gi < 10; ++gi) {
     const int tb = n3_group_begin(gi), te = n3_group_begin(gi + 1);
-    const int pairs = (te - tb) * R;
     Wide<L> part;
     wzero<L>(part);
-    int t = tb, c = lane;
-#pragma unroll 4
-    for (int p0 = 0; p0 < pairs; p0 += 32) {
-      if (p0 + lane < pairs) {
-        const int4 ti = taps[t];
-        if (!CHECK || ti.z + s_dy[c] >= 0) {
-          const Wide<L> gv = wload<L>(g + (ptrdiff_t)(ti.x + s_off[c]) * L);
-          const ulonglong2 wt = __ldg(table + ti.y + s_perm[ti.w * R + c]);
-          mac_weight<L, ulonglong2>(part, gv, wt);
+#pragma unroll 1
+    for (int t0 = tb; t0 < te; t0 += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int4 ti = taps[t0 + u];
+        if (!CHECK || ti.z + ln.dyA >= 0) {
+          const Wide<L> gv = wload<L>(g + (ptrdiff_t)(ti.x + ln.offA) * L);
+          mac_weight<L, ulonglong2>(part, gv, __ldg(table + ti.y + perm_col(ln.permA, ti.w)));
+        }
+        if (!CHECK || ti.z + ln.dyB >= 0) {
+          const Wide<L> gv = wload<L>(g + (ptrdiff_t)(ti.x + ln.offB) * L);
+          mac_weight<L, ulonglong2>(part, gv, __ldg(table + ti.y + perm_col(ln.permB, ti.w)));
         }
       }
-      c += 32;
-      if (c >= R) {
-        c -= R;
-        ++t;
+      if (lane < 20) {
+        const int4 ti = taps[t0 + lane / 5];
+        if (!CHECK || ti.z + ln.dyC >= 0) {
+          const Wide<L> gv = wload<L>(g + (ptrdiff_t)(ti.x + ln.offC) * L);
+          mac_weight<L, ulonglong2>(part, gv, __ldg(table + ti.y + perm_col(ln.permC, ti.w)));
+        }
       }
     }
     // group weight (-1)^parity 3^m, m = gi / 2
@@ -308,9 +351,11 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
   const long long rowpitch = pv.Gp;
   const int left = pv.left;
 
-  // for n = 2 a lane keeps one neighbour for every tap
+  // for n = 2 a lane keeps one neighbour for every tap; for n = 3 (fast) three
   const int my_dx = (R == 32) ? s_dx[lane] : 0;
   const int my_dy = (R == 32) ? s_dy[lane] : 0;
+  N3Lane n3ln{};
+  if constexpr (FAST && N == 3) n3ln = n3_lane(lane, s_off, s_dy, s_perm);
 
   Wide<L> mine;
   wzero<L>(mine);
@@ -353,8 +398,8 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
       const bool check = __any_sync(0xffffffffu, strad) != 0;
       __syncwarp();
       const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(pv.table_fold);
-      if (check) n3_pixel<L, true>(acc, taps, g, tab, s_off, s_dy, s_perm, lane);
-      else n3_pixel<L, false>(acc, taps, g, tab, s_off, s_dy, s_perm, lane);
+      if (check) n3_pixel<L, true>(acc, taps, g, tab, n3ln, lane);
+      else n3_pixel<L, false>(acc, taps, g, tab, n3ln, lane);
     } else if constexpr (FAST) {
       static_assert(N == 2 && R == 32, "fast path is for n = 2 and n = 3");
       constexpr int kDyMin = Stencil<N>::kDmin, kDyMax = Stencil<N>::kDmin + 3 * N - 1;
@@ -487,9 +532,10 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
 // rows have nearby taps, so their g patches are shared in L1.  Each warp's tap
 // table lives in dynamic shared memory.
 template <int N, int L, bool FAST>
-__global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_exact_kernel(
-    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
-    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+__device__ __forceinline__ void mesh_exact_body(const PlanView& pv, const uint64_t* __restrict__ g,
+                                                const float4* __restrict__ scales, size_t scale_pitch,
+                                                void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num,
+                                                size_t num_pitch, int32_t* status) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R], s_off[R];
@@ -512,6 +558,23 @@ __global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_exact_kernel(
   const int x0 = (blockIdx.x - band * segs) * 32;
   mesh_run<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
                        s_tap + (threadIdx.x >> 5) * TAPS, s_dx, s_dy, s_order, s_off, s_perm);
+}
+
+// Orders 1, 2: CTAs of up to 16 rows, the compiler's register choice for
+// 512-thread blocks.  Order 3: up to 8 rows, three CTAs per SM (85 registers
+// for its wide accumulators).
+template <int N, int L, bool FAST>
+__global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_exact_kernel(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  mesh_exact_body<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status);
+}
+
+template <int L, bool FAST>
+__global__ void __launch_bounds__(32 * mesh_max_warps(3), mesh_min_ctas(3)) mesh_exact_kernel3(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  mesh_exact_body<3, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status);
 }
 
 // ------------------------------------------------------------------- batches
@@ -554,8 +617,7 @@ __device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int 
 // global counter.  One kernel per order n, so that each gets its own register
 // budget; the images of one launch share n and differ in size and limbs.
 template <int N, int L, bool FAST>
-__global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
-                                                                        unsigned long long* counter) {
+__device__ __forceinline__ void mesh_batch_body(const BatchJobs& jobs, unsigned long long* counter) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   __shared__ int s_dx[R], s_dy[R], s_off[R];
@@ -595,6 +657,18 @@ __global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_batch_kernel(const __
     if (y >= jb.pv.H) continue;
     batch_dispatch_L<N, L, FAST>(jb, y, x0, taps, s_dx, s_dy, s_order, s_off, s_perm);
   }
+}
+
+template <int N, int L, bool FAST>
+__global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
+                                                                        unsigned long long* counter) {
+  mesh_batch_body<N, L, FAST>(jobs, counter);
+}
+
+template <int L, bool FAST>
+__global__ void __launch_bounds__(32 * mesh_max_warps(3), mesh_min_ctas(3)) mesh_batch_kernel3(
+    const __grid_constant__ BatchJobs jobs, unsigned long long* counter) {
+  mesh_batch_body<3, L, FAST>(jobs, counter);
 }
 
 __global__ void prepare_scales_kernel(const PlanView pv, const float4* __restrict__ scales, size_t scale_pitch,
@@ -680,22 +754,20 @@ static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const v
                                   void* s, size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
                                   int warps, cudaStream_t st) {
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
+  if (warps > mesh_max_warps(N)) warps = mesh_max_warps(N);
   const long long grid = (long long)((pv.W + 31) / 32) * ((pv.H + warps - 1) / warps);
   const int block = 32 * warps;
-  size_t smem = 0;
-  cudaError_t e;
-  if constexpr (N >= 2) {
-    if (mesh_fast_ok(pv)) {
-      if ((e = tap_smem(mesh_exact_kernel<N, L, true>, TAPS, warps, &smem)) != cudaSuccess) return e;
-      mesh_exact_kernel<N, L, true><<<grid, block, smem, st>>>(pv, g, (const float4*)scales, scale_pitch, s,
-                                                               s_pitch, num, num_pitch, status);
-      return cudaGetLastError();
-    }
-  }
-  if ((e = tap_smem(mesh_exact_kernel<N, L, false>, TAPS, warps, &smem)) != cudaSuccess) return e;
-  mesh_exact_kernel<N, L, false><<<grid, block, smem, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch,
-                                                            num, num_pitch, status);
-  return cudaGetLastError();
+  const bool fast = N >= 2 && mesh_fast_ok(pv);
+  auto go = [&](auto kernel) -> cudaError_t {
+    size_t smem = 0;
+    cudaError_t e = tap_smem(kernel, TAPS, warps, &smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, block, smem, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch, num, num_pitch, status);
+    return cudaGetLastError();
+  };
+  if constexpr (N == 3) return fast ? go(mesh_exact_kernel3<L, true>) : go(mesh_exact_kernel3<L, false>);
+  else if constexpr (N == 2) return fast ? go(mesh_exact_kernel<N, L, true>) : go(mesh_exact_kernel<N, L, false>);
+  else return go(mesh_exact_kernel<N, L, false>);
 }
 
 template <int N>
@@ -742,15 +814,20 @@ static cudaError_t launch_batch_NL(const BatchJobs& jobs, unsigned long long* co
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  size_t smem = 0;
-  if ((e = tap_smem(mesh_batch_kernel<N, L, FAST>, TAPS, warps, &smem)) != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mesh_batch_kernel<N, L, FAST>, 32 * warps, smem);
-  if (per_sm < 1) per_sm = 1;
-  mesh_batch_kernel<N, L, FAST><<<sms * per_sm, 32 * warps, smem, st>>>(jobs, counter);
-  return cudaGetLastError();
+  auto go = [&](auto kernel) -> cudaError_t {
+    size_t smem = 0;
+    cudaError_t e2 = tap_smem(kernel, TAPS, warps, &smem);
+    if (e2 != cudaSuccess) return e2;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);
+    if (per_sm < 1) per_sm = 1;
+    kernel<<<sms * per_sm, 32 * warps, smem, st>>>(jobs, counter);
+    return cudaGetLastError();
+  };
+  if constexpr (N == 3) return go(mesh_batch_kernel3<L, FAST>);
+  else return go(mesh_batch_kernel<N, L, FAST>);
 }
 
 template <int N, bool FAST>
@@ -771,6 +848,7 @@ cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* cou
   auto cost = [&](int i) { return (double)in[i].pv.W * in[i].pv.H; };
   int launch = 0;
   for (int n = 3; n >= 1; --n) {
+    const int wn = warps < mesh_max_warps(n) ? warps : mesh_max_warps(n);  // rows per unit
     for (int L = 4; L >= 1; --L) {
       for (int fast = 1; fast >= 0; --fast) {
         if (fast && n == 1) continue;
@@ -800,16 +878,16 @@ cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* cou
           jb.status = b.status;
           jb.segs = (b.pv.W + 31) / 32;
           jb.units_begin = units;
-          units += (long long)jb.segs * ((b.pv.H + warps - 1) / warps);
+          units += (long long)jb.segs * ((b.pv.H + wn - 1) / wn);
         }
         jobs.total_units = units;
         unsigned long long* ctr = counter + launch++;
         cudaError_t e;
-        if (n == 1) e = launch_batch_N<1, false>(L, jobs, ctr, warps, st);
-        else if (n == 2) e = fast ? launch_batch_N<2, true>(L, jobs, ctr, warps, st)
-                                  : launch_batch_N<2, false>(L, jobs, ctr, warps, st);
-        else e = fast ? launch_batch_N<3, true>(L, jobs, ctr, warps, st)
-                      : launch_batch_N<3, false>(L, jobs, ctr, warps, st);
+        if (n == 1) e = launch_batch_N<1, false>(L, jobs, ctr, wn, st);
+        else if (n == 2) e = fast ? launch_batch_N<2, true>(L, jobs, ctr, wn, st)
+                                  : launch_batch_N<2, false>(L, jobs, ctr, wn, st);
+        else e = fast ? launch_batch_N<3, true>(L, jobs, ctr, wn, st)
+                      : launch_batch_N<3, false>(L, jobs, ctr, wn, st);
         if (e != cudaSuccess) return e;
       }
     }
