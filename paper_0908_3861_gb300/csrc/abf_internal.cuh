@@ -65,6 +65,45 @@ __device__ __forceinline__ void wsub(Wide<L>& a, const Wide<L>& b) {
   }
 }
 
+// a += b (mod 2^(64L)) as one add-with-carry chain (the scans: fewer ALU
+// operations than the compare-and-carry form, which the mesh schedules better).
+template <int L>
+__device__ __forceinline__ void waddc(Wide<L>& a, const Wide<L>& b) {
+  if constexpr (L == 1) {
+    a.w[0] += b.w[0];
+  } else if constexpr (L == 2) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.w[0]), "+l"(a.w[1]) : "l"(b.w[0]), "l"(b.w[1]));
+  } else if constexpr (L == 3) {
+    asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+        : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2])
+        : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]));
+  } else {
+    static_assert(L == 4, "1..4 limbs");
+    asm("add.cc.u64 %0, %0, %4;\n\taddc.cc.u64 %1, %1, %5;\n\taddc.cc.u64 %2, %2, %6;\n\taddc.u64 %3, %3, %7;"
+        : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3])
+        : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]));
+  }
+}
+
+// a -= b (mod 2^(64L)) as one subtract-with-borrow chain.
+template <int L>
+__device__ __forceinline__ void wsubc(Wide<L>& a, const Wide<L>& b) {
+  if constexpr (L == 1) {
+    a.w[0] -= b.w[0];
+  } else if constexpr (L == 2) {
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(a.w[0]), "+l"(a.w[1]) : "l"(b.w[0]), "l"(b.w[1]));
+  } else if constexpr (L == 3) {
+    asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
+        : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2])
+        : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]));
+  } else {
+    static_assert(L == 4, "1..4 limbs");
+    asm("sub.cc.u64 %0, %0, %4;\n\tsubc.cc.u64 %1, %1, %5;\n\tsubc.cc.u64 %2, %2, %6;\n\tsubc.u64 %3, %3, %7;"
+        : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3])
+        : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]));
+  }
+}
+
 // acc += g * w (mod 2^(64L)), w an unsigned 64-bit factor.
 template <int L>
 __device__ __forceinline__ void wmac(Wide<L>& acc, const Wide<L>& g, uint64_t w) {

@@ -55,7 +55,7 @@ __device__ __forceinline__ Wide<L> warp_inclusive(Wide<L> v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     Wide<L> o = shfl_up_wide<L>(v, d);
-    if (lane >= d) wadd<L>(v, o);
+    if (lane >= d) waddc<L>(v, o);
   }
   return v;
 }
@@ -107,7 +107,7 @@ __device__ __forceinline__ void transport_add(Wide<L>* acc, const Wide<L>* c, lo
   const uint64_t b1 = (uint64_t)t, b2 = (uint64_t)(t * (t + 1) / 2), b3 = (uint64_t)(t * (t + 1) / 2 * (t + 2) / 3);
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
-    wadd<L>(acc[k], c[k]);
+    waddc<L>(acc[k], c[k]);
     if (k >= 1) wmac<L>(acc[k], c[k - 1], b1);
     if (k >= 2) wmac<L>(acc[k], c[k - 2], b2);
     if (k >= 3) wmac<L>(acc[k], c[k - 3], b3);
@@ -118,33 +118,39 @@ __device__ __forceinline__ void transport_add(Wide<L>* acc, const Wide<L>* c, lo
 // the running state carry[] (carry[k] = fold k's sum so far), optional store
 // through the warp's shared-memory tile (lane i holds samples 4i..4i+3; the
 // store writes 32 consecutive samples per instruction).
-template <int L, typename TIn, int NF, bool STORE>
-__device__ __forceinline__ void row_chunk(const PlanView& pv, const TIn* frow, uint64_t* grow, int x0, int lane,
-                                          double scale, long long bound, int32_t* status, Wide<L>* carry,
-                                          Wide<L>* tile) {
-  Wide<L> v[kRowVec];
+// The raw input of one chunk (zeros outside the image), fetched ahead of its
+// scan so that the next chunk's loads are in flight during this one's.
+template <typename TIn>
+__device__ __forceinline__ void row_fetch(const PlanView& pv, const TIn* frow, int x0, int lane, TIn (&raw)[kRowVec]) {
 #pragma unroll
   for (int e = 0; e < kRowVec; ++e) {
     const int xi = x0 + lane * kRowVec + e;  // box column
     const int x = xi - pv.left;              // image column
-    int64_t val = 0;
-    if (frow && x >= 0 && x < pv.W && xi < pv.Gw) val = convert_f<TIn>(frow[x], scale, bound, status);
-    v[e] = wfrom_i64<L>(val);
+    raw[e] = (frow && x >= 0 && x < pv.W && xi < pv.Gw) ? frow[x] : (TIn)0;
   }
+}
+
+template <int L, typename TIn, int NF, bool STORE>
+__device__ __forceinline__ void row_chunk(const PlanView& pv, const TIn (&raw)[kRowVec], uint64_t* grow, int x0,
+                                          int lane, double scale, long long bound, int32_t* status, Wide<L>* carry,
+                                          Wide<L>* tile) {
+  Wide<L> v[kRowVec];
+#pragma unroll
+  for (int e = 0; e < kRowVec; ++e) v[e] = wfrom_i64<L>(convert_f<TIn>(raw[e], scale, bound, status));
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     // lane-local inclusive scan
 #pragma unroll
-    for (int e = 1; e < kRowVec; ++e) wadd<L>(v[e], v[e - 1]);
+    for (int e = 1; e < kRowVec; ++e) waddc<L>(v[e], v[e - 1]);
     Wide<L> tot = v[kRowVec - 1];
     Wide<L> incl = warp_inclusive<L>(tot, lane);
     Wide<L> excl = shfl_up_wide<L>(incl, 1);
     if (lane == 0) wzero<L>(excl);
-    wadd<L>(excl, carry[k]);
+    waddc<L>(excl, carry[k]);
 #pragma unroll
-    for (int e = 0; e < kRowVec; ++e) wadd<L>(v[e], excl);
+    for (int e = 0; e < kRowVec; ++e) waddc<L>(v[e], excl);
     Wide<L> last = shfl_wide<L>(incl, 31);
-    wadd<L>(carry[k], last);
+    waddc<L>(carry[k], last);
   }
   if constexpr (STORE) {
 #pragma unroll
@@ -187,8 +193,14 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
   Wide<L> carry[NF];
 #pragma unroll
   for (int k = 0; k < NF; ++k) wzero<L>(carry[k]);
-  for (int c = c0; c < c1; ++c)
-    row_chunk<L, TIn, NF, false>(pv, frow, grow, c * chunk, lane, scale, bound, status, carry, nullptr);
+  TIn raw[kRowVec], nxt[kRowVec];
+  if (c0 < c1) row_fetch<TIn>(pv, frow, c0 * chunk, lane, nxt);
+  for (int c = c0; c < c1; ++c) {
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) raw[e] = nxt[e];
+    if (c + 1 < c1) row_fetch<TIn>(pv, frow, (c + 1) * chunk, lane, nxt);
+    row_chunk<L, TIn, NF, false>(pv, raw, grow, c * chunk, lane, scale, bound, status, carry, nullptr);
+  }
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NF; ++k) s_agg[warp][k] = carry[k];
@@ -207,8 +219,13 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
 #pragma unroll
     for (int k = 0; k < NF; ++k) st[k] = nx[k];
   }
-  for (int c = c0; c < c1; ++c)
-    row_chunk<L, TIn, NF, true>(pv, frow, grow, c * chunk, lane, scale, bound, status, st, s_tile[warp]);
+  if (c0 < c1) row_fetch<TIn>(pv, frow, c0 * chunk, lane, nxt);
+  for (int c = c0; c < c1; ++c) {
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) raw[e] = nxt[e];
+    if (c + 1 < c1) row_fetch<TIn>(pv, frow, (c + 1) * chunk, lane, nxt);
+    row_chunk<L, TIn, NF, true>(pv, raw, grow, c * chunk, lane, scale, bound, status, st, s_tile[warp]);
+  }
 }
 
 // ---------------------------------------------------------- lines (v2, v3, v4)
@@ -255,21 +272,21 @@ __device__ __forceinline__ void st_zero(LineState<L, NF>& a) {
 
 template <int L, int NF>
 __device__ __forceinline__ void st_step(LineState<L, NF>& a, const Wide<L>& x) {
-  wadd<L>(a.s[0], x);
+  waddc<L>(a.s[0], x);
 #pragma unroll
-  for (int k = 1; k < NF; ++k) wadd<L>(a.s[k], a.s[k - 1]);
+  for (int k = 1; k < NF; ++k) waddc<L>(a.s[k], a.s[k - 1]);
 }
 
 // acc += T_t(c): the zero-input evolution of state c over t steps.
 template <int L, int NF>
 __device__ __forceinline__ void st_add_transported(LineState<L, NF>& acc, const LineState<L, NF>& c, long long t) {
-  wadd<L>(acc.s[0], c.s[0]);
+  waddc<L>(acc.s[0], c.s[0]);
   if constexpr (NF >= 2) {
-    wadd<L>(acc.s[1], c.s[1]);
+    waddc<L>(acc.s[1], c.s[1]);
     wmac<L>(acc.s[1], c.s[0], (uint64_t)t);
   }
   if constexpr (NF >= 3) {
-    wadd<L>(acc.s[2], c.s[2]);
+    waddc<L>(acc.s[2], c.s[2]);
     wmac<L>(acc.s[2], c.s[1], (uint64_t)t);
     wmac<L>(acc.s[2], c.s[0], (uint64_t)(t * (t + 1) / 2));
   }
