@@ -379,6 +379,13 @@ abf_status abf1d_filter_numerator(abf1d_plan plan, const void* d_g, const float*
  * synchronises the device, then clears the word.                             */
 abf_status abf1d_last_device_status(abf1d_plan plan, int32_t* code);
 
+/* Host-only: the B-spline weight table abf1d_plan_create uploads, without
+ * touching a device.  2^(Q+1) rows (r = R 2^-(Q+1) in [0, 1)) of *K entries
+ * D beta^N(r - d), d = *dmin .. *dmin + *K - 1, N = n1 + n2 + 1,
+ * D = N! 2^(N (Q+1)).  With out = NULL only the sizes and D are returned.   */
+abf_status abf1d_weight_table_host(int32_t n1, int32_t n2, int32_t q_bits, uint64_t* out, size_t out_elems,
+                                   size_t* needed_elems, int32_t* K, int32_t* dmin, uint64_t* D);
+
 /* Library version, for the bindings. */
 int32_t abf_version(void);
 

@@ -110,6 +110,8 @@ def lib():
         "abf1d_filter": ([vp, vp, vp, sz, vp, sz, vp], st),
         "abf1d_filter_numerator": ([vp, vp, vp, sz, vp, sz, vp], st),
         "abf1d_last_device_status": ([vp, P(i32)], st),
+        "abf1d_weight_table_host": ([i32, i32, i32, P(ctypes.c_uint64), sz, P(sz), P(i32), P(i32),
+                                     P(ctypes.c_uint64)], st),
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
@@ -333,3 +335,16 @@ def abf_batch_autotune(jobs, ws, stream=None):
     _check(lib().abf_batch_autotune(arr, len(jobs), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
                                     ctypes.byref(w), ms), "abf_batch_autotune")
     return w.value, list(ms)
+
+
+def abf1d_weight_table_host(n1, n2, q_bits):
+    """(rows x K table as a list of lists, dmin, D) of the 1-D B-spline weights."""
+    need, K, dmin, D = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
+    _check(lib().abf1d_weight_table_host(n1, n2, q_bits, None, 0, ctypes.byref(need), ctypes.byref(K),
+                                         ctypes.byref(dmin), ctypes.byref(D)), "abf1d_weight_table_host")
+    buf = (ctypes.c_uint64 * need.value)()
+    _check(lib().abf1d_weight_table_host(n1, n2, q_bits, buf, need.value, None, None, None, None),
+           "abf1d_weight_table_host")
+    k = K.value
+    vals = list(buf)
+    return [vals[i:i + k] for i in range(0, len(vals), k)], dmin.value, D.value

@@ -19,6 +19,7 @@
 // integers, and every row is checked to sum to D (partition of unity).
 //   S[m] = sum_j (-1)^j binom(n2+1, j) sum_d g[p_j + d] T[r_j][d]  (mod 2^(64 L))
 //   s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F)  in binary64.
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -343,6 +344,30 @@ abf_status abf1d_filter_numerator(abf1d_plan p, const void* d_g, const float* d_
                                   size_t num_pitch, cudaStream_t st) {
   if (!d_num) return ABF_ERR_INVALID;
   return filter1d(p, d_g, d_a, a_pitch, nullptr, 0, d_num, num_pitch, st);
+}
+
+abf_status abf1d_weight_table_host(int32_t n1, int32_t n2, int32_t q_bits, uint64_t* out, size_t out_elems,
+                                   size_t* needed_elems, int32_t* K, int32_t* dmin, uint64_t* D) {
+  if (n1 < 0 || n1 > 1 || n2 < 0 || n2 > 3 || q_bits < 1 || q_bits > 10) return ABF_ERR_INVALID;
+  const int N = n1 + n2 + 1, P = q_bits + 1;
+  const int dm = (N % 2) ? -(N + 1) / 2 + 1 : -N / 2;
+  const int k = (N % 2) ? N + 1 : N + 2;
+  std::vector<uint64_t> tab;
+  unsigned long long Dv = 0;
+  try {
+    if (!build_table_1d(N, P, k, dm, tab, &Dv)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  if (needed_elems) *needed_elems = tab.size();
+  if (K) *K = k;
+  if (dmin) *dmin = dm;
+  if (D) *D = Dv;
+  if (out) {
+    if (out_elems < tab.size()) return ABF_ERR_INVALID;
+    std::copy(tab.begin(), tab.end(), out);
+  }
+  return ABF_OK;
 }
 
 abf_status abf1d_last_device_status(abf1d_plan p, int32_t* code) {

@@ -98,3 +98,19 @@ def test_plan_rejects_bad_descriptors(lib):
     d.width = 0
     with pytest.raises(_abf.AbfError):
         _abf.abf_plan_create(d)
+
+
+@pytest.mark.parametrize("n1,n2,q", [(0, 0, 3), (1, 1, 2), (0, 2, 4), (1, 3, 3), (1, 2, 8)])
+def test_line1d_host_table_matches_oracle(n1, n2, q):
+    """The 1-D B-spline table (built by the degree recurrence) against the
+    oracle's truncated-power B-spline, entry by entry."""
+    from oracle import line1d as o
+    from paper_0908_3861_gb300 import _abf
+    rows, dmin, D = _abf.abf1d_weight_table_host(n1, n2, q)
+    N, P = n1 + n2 + 1, q + 1
+    assert D == o.denominator(N, P)
+    assert len(rows) == 1 << P
+    for R, row in enumerate(rows):
+        ref = [o.dbspline_int(N, P, R - ((dmin + c) << P)) for c in range(len(row))]
+        assert row == ref, R
+        assert sum(row) == D
