@@ -26,6 +26,9 @@ Unser, "Fast adaptive elliptical filtering using box splines"):
   s[m] = <f, beta_a^{n2}(. - m)> from its definition by exact piecewise
   integration, and the Proposition's two steps (running sums, then the FD
   mask with B-spline interpolation) in exact integers.
+* ``structure``  -- scale-map estimation (the paper defers it, Sec. 8): a
+  reading, the structure tensor of the image turned into an edge-following
+  ellipse per pixel (binary64).
 * ``scales``     -- the per-pixel scale readings: paper scales a_k (Sec. 7)
   to lattice steps c_k, and the ellipse-to-scales moment rule (a reading: the
   paper leaves the scale map to other work, Sec. 8; Theorem (convergence) of
