@@ -562,6 +562,70 @@ def run_line1d(args):
         dist.destroy_process_group()
 
 
+def run_scale_map(args):
+    """Scale-map estimation (structure tensor -> ellipse per pixel) on the
+    2048x2048 order-2 image, then the exact filter driven by that field:
+    Mpixel/s of estimate + integrate + filter, and of the estimator alone."""
+    import torch
+    import synthetic
+    from paper_0908_3861_gb300 import AdaptiveFilter, estimate_ellipses
+    import __graft_entry__
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    shp = _shape(args) or (2048, 2048)
+    w = synthetic.workload("c2", shape=shp, seed_offset=rank)
+    img = w["image"]
+    H, W = img.shape
+    f_t = torch.from_numpy(img).to(dev)
+    filt = AdaptiveFilter(W, H, 2, torch.float32, scale_kind="ellipse", q_bits=8, frac_bits=16, max_scale=64.0,
+                          out="f32", value_bound=255.0, device=dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+
+    def step():
+        field = estimate_ellipses(f_t, rho=2.0, sigma0=6.0, e_max=4.0)
+        filt.integrate(f_t)
+        filt.filter(field, out)
+        return field
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert filt.device_status() == 0
+    stream = torch.cuda.current_stream(dev)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            field = estimate_ellipses(f_t, rho=2.0, sigma0=6.0, e_max=4.0)
+            ev[i][1].record(stream)
+            filt.integrate(f_t)
+            filt.filter(field, out)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1) / K
+    est_ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    assert filt.device_status() == 0
+    pix = float(H * W)
+    line = {"metric": "Mpixel/s scale-map estimation + exact adaptive filter (ellipse per pixel from the structure "
+                      "tensor)", "value": round(pix / (total_ms * 1e-3) / 1e6, 3), "unit": "Mpixel/s", "n_gpus": 1,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 tensor, f64 eigen, int64x%d filter" % filt.limbs,
+            "data": "synthetic",
+            "config": {"workload": "%dx%d f32 (2^-16 grid) image of the order-2 recipe; rho 2, sigma0 6, e_max 4; "
+                                   "exact order-2 filter, Q=8" % (H, W)},
+            "estimator": {"ms": round(est_ms, 4), "mpix_s": round(pix / (est_ms * 1e-3) / 1e6, 1),
+                          "hbm_bytes_note": "f read, 3 planes written, read and written (row pass), read (column "
+                                            "pass), float4 written: %.0f MB" % ((4 + 12 + 24 + 12 + 16) * pix / 1e6)},
+            "gpu_launches": int(K * (3 + 5)),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    filt.close()
+
+
 def run_serve(args):
     """Poisson-arrival stream of filter jobs (sides U{256..4096}, n U{1,2},
     float32 images on the 2^-16 grid with ellipse fields as the 2048^2 case)
@@ -739,6 +803,8 @@ def main():
         run_serve(args)
     elif args.workload == "d1":
         run_line1d(args)
+    elif args.workload == "s2":
+        run_scale_map(args)
     else:
         run_ours(args)
 

@@ -316,6 +316,25 @@ const char* abf_status_str(abf_status s);
 abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t out_bytes,
                                  size_t* needed_bytes, int32_t* wbytes, uint32_t* D_words4);
 
+/* --------------------------------------------------- scale-map estimation
+ * The paper leaves the scale map a: Z^2 -> R^4_+ to other work (Sec. 8).  This
+ * builds one from the image (a reading of the build, not the paper's): the
+ * structure tensor J = G_rho * (g g^T) of the central-difference gradient g
+ * (zero outside the image; sampled Gaussian of std rho, |k| <= ceil(3 rho),
+ * normalised, applied separably in binary32), its eigenvalues l1 >= l2 and
+ * coherence ((l1 - l2) / (l1 + l2 + 1e-12))^2 (binary64), and per pixel the
+ * ellipse (sigma0, 1 + (e_max - 1) coherence, cos t, sin t) with (cos t, sin t)
+ * the unit eigenvector of l2, sin t >= 0 ((1, 0) where l1 == l2): the input of
+ * ABF_SCALES_ELLIPSE, so the filter smooths along edges.
+ *   d_f   : height rows of width in_dtype elements, row pitch in bytes.
+ *   d_ws  : device workspace of abf_ellipse_ws_bytes(width, height) bytes.
+ *   d_out : height rows of width float4, row pitch in bytes (16-aligned).
+ *   rho in (0, 10], sigma0 > 0, e_max >= 1.                                 */
+size_t abf_ellipse_ws_bytes(int32_t width, int32_t height);
+abf_status abf_estimate_ellipses(const void* d_f, size_t f_pitch, abf_dtype in_dtype, int32_t width, int32_t height,
+                                 double rho, double sigma0, double e_max, void* d_ws, size_t ws_bytes, void* d_out,
+                                 size_t out_pitch, cudaStream_t stream);
+
 /* ------------------------------------------------- 1-D adaptive filter (Sec. 3)
  *
  * The scale-adaptive B-spline filter of Sec. 3 (Proposition "prop") on a batch

@@ -10,11 +10,12 @@ does the same for the 1-D scale-adaptive B-spline filter of Sec. 3.
 from . import _abf
 from ._abf import AbfError
 
-__all__ = ["_abf", "AbfError", "AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc"]
+__all__ = ["_abf", "AbfError", "AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc",
+           "estimate_ellipses"]
 
 
 def __getattr__(name):
-    if name in ("AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc"):
+    if name in ("AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc", "estimate_ellipses"):
         from . import filter as _f
         return getattr(_f, name)
     raise AttributeError(name)

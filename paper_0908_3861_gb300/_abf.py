@@ -112,6 +112,9 @@ def lib():
         "abf1d_last_device_status": ([vp, P(i32)], st),
         "abf1d_weight_table_host": ([i32, i32, i32, P(ctypes.c_uint64), sz, P(sz), P(i32), P(i32),
                                      P(ctypes.c_uint64)], st),
+        "abf_ellipse_ws_bytes": ([i32, i32], sz),
+        "abf_estimate_ellipses": ([vp, sz, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, sz,
+                                   vp, sz, vp], st),
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
@@ -348,3 +351,15 @@ def abf1d_weight_table_host(n1, n2, q_bits):
     k = K.value
     vals = list(buf)
     return [vals[i:i + k] for i in range(0, len(vals), k)], dmin.value, D.value
+
+
+# ---------------------------------------------------- scale-map estimation
+
+def abf_ellipse_ws_bytes(width, height):
+    return lib().abf_ellipse_ws_bytes(width, height)
+
+
+def abf_estimate_ellipses(f, f_pitch, in_dtype, width, height, rho, sigma0, e_max, ws, out, out_pitch, stream=None):
+    _check(lib().abf_estimate_ellipses(_ptr(f), f_pitch, in_dtype, width, height, rho, sigma0, e_max, _ptr(ws),
+                                       ws.numel() * ws.element_size(), _ptr(out), out_pitch, _stream(stream)),
+           "abf_estimate_ellipses")

@@ -286,3 +286,17 @@ class AdaptiveFilter1D:
 
     def device_status(self):
         return C.abf1d_last_device_status(self.plan)
+
+
+def estimate_ellipses(f, rho=2.0, sigma0=4.0, e_max=4.0, stream=None):
+    """Per-pixel ellipses (sigma, elongation, cos t, sin t) from the image's
+    structure tensor (abf_estimate_ellipses): an (H, W, 4) float32 tensor for
+    the filter's "ellipse" scale kind."""
+    if f.dim() != 2 or f.stride(1) != 1:
+        raise ValueError("f must be a 2-D row-major tensor")
+    H, W = f.shape
+    ws = torch.empty(max(C.abf_ellipse_ws_bytes(W, H), 16), dtype=torch.uint8, device=f.device)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=f.device)
+    C.abf_estimate_ellipses(f, f.stride(0) * f.element_size(), _DT[f.dtype], W, H, float(rho), float(sigma0),
+                            float(e_max), ws, out, W * 16, stream)
+    return out
