@@ -50,7 +50,7 @@ typedef enum {
   ABF_ERR_INVALID = 1,      /* bad argument or descriptor                         */
   ABF_ERR_OOM = 2,          /* device or host allocation failed                   */
   ABF_ERR_CUDA = 3,         /* CUDA runtime error (no device, launch failure)     */
-  ABF_ERR_UNSUPPORTED = 4,  /* valid request this build does not serve            */
+  ABF_ERR_UNSUPPORTED = 4,  /* valid request the library does not serve          */
   ABF_ERR_RANGE = 5,        /* exact form: numerator would exceed 64*limbs bits   */
   ABF_ERR_TIMEOUT = 6,      /* a bounded device or host wait ran out              */
   ABF_ERR_BUSY = 7          /* serving: admission refused (over the HBM budget)   */
@@ -318,7 +318,7 @@ abf_status abf_weight_table_host(int32_t n, int32_t q_bits, void* out, size_t ou
 
 /* --------------------------------------------------- scale-map estimation
  * The paper leaves the scale map a: Z^2 -> R^4_+ to other work (Sec. 8).  This
- * builds one from the image (a reading of the build, not the paper's): the
+ * builds one from the image (a reading, not the paper's): the
  * structure tensor J = G_rho * (g g^T) of the central-difference gradient g
  * (zero outside the image; sampled Gaussian of std rho, |k| <= ceil(3 rho),
  * normalised, applied separably in binary32), its eigenvalues l1 >= l2 and

@@ -34,7 +34,7 @@ Unser, "Fast adaptive elliptical filtering using box splines"):
   paper leaves the scale map to other work, Sec. 8; Theorem (convergence) of
   Sec. 4 fixes the isotropic case).
 
-Readings of the paper that the oracle fixes (each is listed in the design doc):
+Readings of the paper that the oracle fixes:
   * order n >= 1 means every one of the four directional B-splines is the
     n-fold self-convolution of the box (n=1 is Sec. 7 exactly); the mesh then
     has (n+1)^4 vertices with binomial weights, tau scales by n, the

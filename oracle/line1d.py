@@ -26,7 +26,7 @@ integer there for D = N! 2^(N P).  The numerator
     S[m] = sum_j (-1)^j binom(n2+1, j) sum_k g[k] D beta^N(y_j - k)
 is an integer and s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F).
 
-Readings (listed in DESIGN.md): zero signal outside [0, len) (as in 2-D);
+Readings: zero signal outside [0, len) (as in 2-D);
 beta^0 is 1 on (-1/2, 1/2] (Sec. 2); a_m is rounded to A = rint(a 2^Q), ties
 to even, as the 2-D steps are.
 """

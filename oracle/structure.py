@@ -2,8 +2,8 @@
 ONLY (see the package header).
 
 The paper leaves the computation of the scale map to other work (Sec. 8); this
-is the reading the build takes (listed in the design doc), an edge-following
-ellipse per pixel from the image's structure tensor:
+is the reading taken here, an edge-following ellipse per pixel from the
+image's structure tensor:
 
   1. gradient by central differences, the image zero outside its support:
          gx[y,x] = (f[y,x+1] - f[y,x-1]) / 2,   gy[y,x] = (f[y+1,x] - f[y-1,x]) / 2;

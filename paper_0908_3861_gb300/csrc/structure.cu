@@ -1,6 +1,6 @@
 // Scale-map estimation: an edge-following ellipse per pixel from the image's
 // structure tensor, the input of the filter's ellipse scale kind.  The paper
-// leaves the scale map to other work (Sec. 8); this is the build's reading:
+// leaves the scale map to other work (Sec. 8); this is the reading taken here:
 //
 //   gradient by central differences (zero outside the image),
 //   J = G_rho * (g g^T), a separable sampled Gaussian (|k| <= ceil(3 rho),
@@ -114,11 +114,14 @@ static cudaError_t run_ellipses(const void* f, size_t pitch, int dtype, int W, i
   float* a = (float*)ws;
   float* b = a + (size_t)3 * W * H;
   dim3 blk(256), grid((W + 255) / 256, H);
+  float* j11 = a;
+  float* j12 = a + (size_t)W * H;
+  float* j22 = a + (size_t)2 * W * H;
   switch (dtype) {
-    case ABF_U8: st_products_kernel<uint8_t><<<grid, blk, 0, st>>>((const uint8_t*)f, pitch, W, H, a, a + (size_t)W * H, a + (size_t)2 * W * H); break;
-    case ABF_U16: st_products_kernel<uint16_t><<<grid, blk, 0, st>>>((const uint16_t*)f, pitch, W, H, a, a + (size_t)W * H, a + (size_t)2 * W * H); break;
-    case ABF_F32: st_products_kernel<float><<<grid, blk, 0, st>>>((const float*)f, pitch, W, H, a, a + (size_t)W * H, a + (size_t)2 * W * H); break;
-    default: st_products_kernel<double><<<grid, blk, 0, st>>>((const double*)f, pitch, W, H, a, a + (size_t)W * H, a + (size_t)2 * W * H); break;
+    case ABF_U8: st_products_kernel<<<grid, blk, 0, st>>>((const uint8_t*)f, pitch, W, H, j11, j12, j22); break;
+    case ABF_U16: st_products_kernel<<<grid, blk, 0, st>>>((const uint16_t*)f, pitch, W, H, j11, j12, j22); break;
+    case ABF_F32: st_products_kernel<<<grid, blk, 0, st>>>((const float*)f, pitch, W, H, j11, j12, j22); break;
+    default: st_products_kernel<<<grid, blk, 0, st>>>((const double*)f, pitch, W, H, j11, j12, j22); break;
   }
   st_hblur_kernel<<<dim3(grid.x, H, 3), blk, 0, st>>>(a, b, W, H, taps);
   st_vblur_ellipse_kernel<<<grid, blk, 0, st>>>(b, W, H, taps, sigma0, e_max, (float4*)out, out_pitch);
