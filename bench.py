@@ -123,7 +123,7 @@ def _shape(args):
     return int(h), int(w)
 
 
-MESH_DRAM_BYTES = 158916096 + 15363072
+MESH_DRAM_BYTES = 158725888 + 15484160
 
 
 def _algorithmic_macs(n):
