@@ -405,6 +405,15 @@ abf_status abf1d_last_device_status(abf1d_plan plan, int32_t* code);
 abf_status abf1d_weight_table_host(int32_t n1, int32_t n2, int32_t q_bits, uint64_t* out, size_t out_elems,
                                    size_t* needed_elems, int32_t* K, int32_t* dmin, uint64_t* D);
 
+/* Test hook for the failure path of the scans (no counterpart in the paper):
+ * runs one line pass (direction v3) of the non-adaptive step with the CTAs of
+ * its first band skipped, so the next band's look-back waits on flags that
+ * nothing sets.  That wait is bounded: it gives up (about a second), sets
+ * ABF_DEV_TIMEOUT in the plan's status word and the pass completes; the
+ * context stays usable.  Every later band may wait out the limit too, so use
+ * it on small plans.  d_g is left undefined.  Exact form only.              */
+abf_status abf_debug_starved_lookback(abf_plan plan, void* d_g, void* d_ws, cudaStream_t stream);
+
 /* Library version, for the bindings. */
 int32_t abf_version(void);
 

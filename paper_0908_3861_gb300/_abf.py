@@ -115,6 +115,7 @@ def lib():
         "abf_ellipse_ws_bytes": ([i32, i32], sz),
         "abf_estimate_ellipses": ([vp, sz, i32, i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, sz,
                                    vp, sz, vp], st),
+        "abf_debug_starved_lookback": ([vp, vp, vp, vp], st),
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
@@ -363,3 +364,7 @@ def abf_estimate_ellipses(f, f_pitch, in_dtype, width, height, rho, sigma0, e_ma
     _check(lib().abf_estimate_ellipses(_ptr(f), f_pitch, in_dtype, width, height, rho, sigma0, e_max, _ptr(ws),
                                        ws.numel() * ws.element_size(), _ptr(out), out_pitch, _stream(stream)),
            "abf_estimate_ellipses")
+
+
+def abf_debug_starved_lookback(plan, g, ws, stream=None):
+    _check(lib().abf_debug_starved_lookback(plan, _ptr(g), _ptr(ws), _stream(stream)), "abf_debug_starved_lookback")

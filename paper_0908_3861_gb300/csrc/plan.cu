@@ -50,6 +50,8 @@ struct BatchIn {
   int32_t* status;
 };
 int batch_max_jobs();
+cudaError_t run_lookback_starved(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
+                                 cudaStream_t st);
 cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, int warps, cudaStream_t st);
 size_t tile_ws_bytes(const PlanView& pv, int real_bytes, int* slots_out, size_t* slot_elems_out, size_t* off_bmax,
                      size_t* off_tiles, size_t* off_cnt, size_t* off_scratch);
@@ -571,6 +573,14 @@ abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g,
   if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
   uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
   return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, p->d_status, st));
+}
+
+abf_status abf_debug_starved_lookback(abf_plan p, void* d_g, void* d_ws, cudaStream_t st) {
+  if (!p || !d_g || !d_ws) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  uint32_t ep = reserve_epochs(1u);
+  return cuda_status(abf::run_lookback_starved(p->pv, (uint64_t*)d_g, d_ws, &ep, p->d_status, st));
 }
 
 abf_status abf_integrate_noalloc(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t st) {

@@ -427,10 +427,19 @@ cudaError_t run_row_scan(const PlanView& pv, const void* f, size_t f_pitch, uint
   }
 }
 
+__global__ void set_ticket_kernel(uint32_t* ticket, uint32_t value) { *ticket = value; }
+
+// first_ticket > 0 skips the first tickets (test hook: their bands never run).
 template <int L, int DIR, int NF>
 static cudaError_t launch_lines(const PlanView& pv, uint64_t* g, const LineWs& ws, uint32_t epoch,
-                                int32_t* status, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), st);
+                                int32_t* status, cudaStream_t st, uint32_t first_ticket = 0) {
+  cudaError_t e;
+  if (first_ticket == 0) {
+    e = cudaMemsetAsync(ws.ticket, 0, sizeof(uint32_t), st);
+  } else {
+    set_ticket_kernel<<<1, 1, 0, st>>>(ws.ticket, first_ticket);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   const int ctas = ws.nbands * ws.ngroups;
   line_scan_kernel<L, DIR, NF><<<ctas, kLinesPerCta, 0, st>>>(pv, g, ws, epoch, status);
@@ -510,6 +519,39 @@ static cudaError_t integrate_L(const PlanView& pv, const void* f, size_t f_pitch
     case 1: return lines_NF<L, 1>(pv, g, ws, epoch, status, st);
     case 2: return lines_NF<L, 2>(pv, g, ws, epoch, status, st);
     default: return lines_NF<L, 3>(pv, g, ws, epoch, status, st);
+  }
+}
+
+// Test hook for the bounded look-back wait: one v3 pass whose band-0 CTAs
+// never run, so band 1 waits on flags nothing sets, gives up after its bounded
+// spin (ABF_DEV_TIMEOUT) and the pass completes.  g is left undefined.
+template <int L, int NF>
+static cudaError_t starved_NF(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
+                              cudaStream_t st) {
+  const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
+  const LineWs w = carve(ws, pv.Gw, pv.Gh, L, NF, 3);
+  return launch_lines<L, 3, NF>(pv, g, w, ep, status, st, (uint32_t)w.ngroups);
+}
+
+template <int L>
+static cudaError_t starved_L(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
+                             cudaStream_t st) {
+  switch (pv.n) {
+    case 1: return starved_NF<L, 1>(pv, g, ws, epoch, status, st);
+    case 2: return starved_NF<L, 2>(pv, g, ws, epoch, status, st);
+    default: return starved_NF<L, 3>(pv, g, ws, epoch, status, st);
+  }
+}
+
+cudaError_t run_lookback_starved(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
+                                 cudaStream_t st) {
+  const cudaError_t e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
+  if (e != cudaSuccess) return e;
+  switch (pv.limbs) {
+    case 1: return starved_L<1>(pv, g, ws, epoch, status, st);
+    case 2: return starved_L<2>(pv, g, ws, epoch, status, st);
+    case 3: return starved_L<3>(pv, g, ws, epoch, status, st);
+    default: return starved_L<4>(pv, g, ws, epoch, status, st);
   }
 }
 

@@ -263,3 +263,23 @@ def test_two_plans_share_one_workspace():
             got = f.numerators(gu.to_device(w["scales"].astype(np.float32), "cuda:0"))
             torch.cuda.synchronize()
             assert (got.cpu().numpy().astype(np.uint64) == ref).all()
+
+
+def test_lookback_wait_times_out_then_the_context_recovers():
+    """Failure path of the scans: a line pass whose first band never runs
+    leaves the next band waiting on a flag nothing sets.  The wait is bounded:
+    the pass completes with ABF_DEV_TIMEOUT in the status word, and the same
+    process then filters correctly."""
+    import torch
+    from paper_0908_3861_gb300 import AdaptiveFilter, _abf
+    w = _small_workload(1, (40, 60), 4, "u8", 77)
+    H, W = w["image"].shape
+    filt = AdaptiveFilter(W, H, 1, torch.uint8, scale_kind="a4", q_bits=4, frac_bits=0, max_scale=w["cmax"],
+                          out="f64", value_bound=255.0, device="cuda:0")
+    _abf.abf_debug_starved_lookback(filt.plan, filt.g, filt.ws)
+    torch.cuda.synchronize()
+    assert filt.device_status() & _abf.ABF_DEV_TIMEOUT
+    filt.close()
+    res = gu.run_exact(w)
+    assert res["status"] == 0
+    _check_all_pixels(w, res)
