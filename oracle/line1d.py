@@ -26,6 +26,15 @@ integer there for D = N! 2^(N P).  The numerator
     S[m] = sum_j (-1)^j binom(n2+1, j) sum_k g[k] D beta^N(y_j - k)
 is an integer and s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F).
 
+Model degree n1 >= 2: the interpolation filter b^{n1} is no longer the unit
+impulse and c = f * (b^{n1})^-1 has infinite support and irrational values.
+The oracle takes the convolution inverse from its definition (the solution of
+b^{n1} * h = delta on a wide window, exact rationals), convolves, and keeps c
+to 2^-200.  The exact form rounds c to the 2^-F grid (c_q = rint(c 2^F), ties
+to even) and runs the Proposition's two steps on c_q exactly; since the
+kernel of s in terms of c has unit lattice sum and is non-negative, that
+rounding moves s by at most 2^-(F+1).
+
 Readings: zero signal outside [0, len) (as in 2-D);
 beta^0 is 1 on (-1/2, 1/2] (Sec. 2); a_m is rounded to A = rint(a 2^Q), ties
 to even, as the 2-D steps are.
@@ -125,18 +134,97 @@ def quantise(a, q_bits):
     return np.rint(np.asarray(a, dtype=np.float64) * float(1 << q_bits)).astype(np.int64)
 
 
-def filter_direct(c, A, n2, q_bits, n1):
-    """s[m] = sum_k c[k] K(m - k) for the quantised scales a_m = A_m 2^-Q
-    (c = f for n1 in {0, 1}); exact Fractions."""
+def filter_direct(c, A, n2, q_bits, n1, k_first=0, ms=None):
+    """s[m] = sum_k c[k] K(m - k) for the quantised scales a_m = A_m 2^-Q,
+    exact Fractions.  c holds the model coefficients at k = k_first,
+    k_first + 1, ... (c = f for n1 in {0, 1}; `prefilter` for n1 >= 2), zero
+    elsewhere; the outputs are the samples m of the signal (len(A) of them),
+    or the samples ms."""
     c = [Fr(v) for v in c]
-    n = len(c)
+    kl, kh = k_first, k_first + len(c) - 1
     out = []
-    for m in range(n):
+    for m in (range(len(A)) if ms is None else ms):
+        m = int(m)
         a = Fr(int(A[m]), 1 << q_bits)
         reach = Fr(n1 + 1, 2) + a * Fr(n2 + 1, 2)
-        k0, k1 = max(0, floor(m - reach)), min(n - 1, ceil(m + reach))
-        out.append(sum(c[k] * kernel(n1, n2, a, m - k) for k in range(k0, k1 + 1)))
+        k0, k1 = max(kl, floor(m - reach)), min(kh, ceil(m + reach))
+        out.append(sum(c[k - k_first] * kernel(n1, n2, a, m - k) for k in range(k0, k1 + 1)))
     return out
+
+
+# ------------------------------------ the interpolation prefilter (n1 >= 2)
+
+def interp_filter(n1):
+    """b^{n1}[k] = beta^{n1}(k) on its support |k| <= n1 // 2 (exact)."""
+    M = n1 // 2
+    return {k: bspline(n1, k) for k in range(-M, M + 1)}
+
+
+_INVERSE = {}
+
+
+def inverse_filter(n1, E=160):
+    """The convolution inverse (b^{n1})^-1 on [-E, E]: the solution h of
+    sum_j b[k - j] h[j] = delta[k] for |k| <= E with h = 0 outside, by banded
+    Gaussian elimination in exact rationals (the matrix is symmetric Toeplitz
+    and strictly diagonally dominant for n1 >= 2, so no pivoting).  It differs
+    from the bounded inverse on Z by O(|z|^(E - |k|)), |z| < 0.44 the largest
+    root of the filter's symbol: below 2^-190 at the centre taps used here."""
+    key = (n1, E)
+    if key in _INVERSE:
+        return _INVERSE[key]
+    b = interp_filter(n1)
+    M = max(b)
+    n = 2 * E + 1
+    rows = [{j: b[i - j] for j in range(max(0, i - M), min(n, i + M + 1))} for i in range(n)]
+    rhs = [Fr(1) if i == E else Fr(0) for i in range(n)]
+    for i in range(n):
+        piv = rows[i][i]
+        for r in range(i + 1, min(n, i + M + 1)):
+            if rows[r].get(i, 0) == 0:
+                continue
+            fct = rows[r][i] / piv
+            for j, v in rows[i].items():
+                if j >= i:
+                    rows[r][j] = rows[r].get(j, Fr(0)) - fct * v
+            rhs[r] -= fct * rhs[i]
+    h = [Fr(0)] * n
+    for i in reversed(range(n)):
+        acc = rhs[i] - sum(v * h[j] for j, v in rows[i].items() if j > i)
+        h[i] = acc / rows[i][i]
+    out = {k: h[k + E] for k in range(-E, E + 1)}
+    _INVERSE[key] = out
+    return out
+
+
+def rint_shift(v, bits):
+    """rint(v 2^-bits) for an integer v, ties to even."""
+    q, r = divmod(v, 1 << bits)
+    half = 1 << (bits - 1)
+    if r > half or (r == half and q & 1):
+        q += 1
+    return q
+
+
+def prefilter(x_int, n1, bits=200):
+    """c = f * (b^{n1})^-1 for f zero outside [0, len), f 2^F = x_int:
+    returns (k_first, cs) with cs[i] = rint(c[k_first + i] 2^(F + bits)), the
+    coefficients for k in [k_first, len - k_first).  Taps of the inverse below
+    2^-(bits+1) are dropped; c beyond the returned range is below 2^-bits |x|."""
+    h = inverse_filter(n1)
+    taps = {k: round(v * (1 << bits)) for k, v in h.items()}  # Fraction rounding: ties to even
+    E = max(abs(k) for k, t in taps.items() if t != 0)
+    hk = np.array([taps[k] for k in range(-E, E + 1)], dtype=object)
+    xs = np.array([int(v) for v in x_int], dtype=object)
+    cs = np.convolve(xs, hk)  # index i <-> k = i - E
+    return -E, [int(v) for v in cs]
+
+
+def prefilter_quantised(x_int, n1, bits=200):
+    """(k_first, c_q): c_q = rint(c 2^F), ties to even, on the range of
+    `prefilter` (the exact form's model coefficients)."""
+    k_first, cs = prefilter(x_int, n1, bits)
+    return k_first, [rint_shift(v, bits) for v in cs]
 
 
 # -------------------------------------------------- the Proposition, exact
@@ -165,7 +253,8 @@ def dbspline_int(N, P, X):
 
 def running_sums(c, times, length):
     """g = u_1^{(times)} * c on [0, length): `times` causal running sums, with
-    c = 0 outside its support (zero signal outside [0, len))."""
+    c = 0 outside its support (zero signal outside [0, len)).  Index 0 is the
+    first coefficient of c, wherever it sits on the signal axis."""
     g = [int(v) for v in c] + [0] * (length - len(c))
     for _ in range(times):
         acc = 0
@@ -183,21 +272,23 @@ def box_right(n1, n2, q_bits, A_max):
     return int(ceil(tau_max + Fr(N + 1, 2))) + 2
 
 
-def filter_paper(c_int, A, n1, n2, q_bits, frac_bits=0):
+def filter_paper(c_int, A, n1, n2, q_bits, frac_bits=0, k_first=0):
     """The two steps of the Proposition in exact integers: returns the
-    numerators S[m] (Python ints) and s[m] (Fractions).  c_int = f 2^F."""
-    return filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, range(len(c_int)))
+    numerators S[m] (Python ints) and s[m] (Fractions) for the len(A) samples
+    of the signal.  c_int = c 2^F at k = k_first, k_first + 1, ... (c = f for
+    n1 in {0, 1}; `prefilter_quantised` for n1 >= 2)."""
+    return filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, range(len(A)), k_first)
 
 
-def filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, ms):
+def filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, ms, k_first=0):
     """filter_paper at the samples ms only (the running sums still cover the
     whole signal)."""
-    n = len(c_int)
+    n = len(A)
     N = n1 + n2 + 1
     P = p_bits(q_bits)
     D = denominator(N, P)
     right = box_right(n1, n2, q_bits, int(np.max(A)) if n else 0)
-    g = running_sums(c_int, n2 + 1, n + right)
+    g = running_sums(c_int[: n + right - k_first], n2 + 1, n + right - k_first)  # g[i] <-> k = k_first + i
     h = Fr(N + 1, 2)
     S_all, s_all = [], []
     for m in ms:
@@ -210,8 +301,8 @@ def filter_paper_at(c_int, A, n1, n2, q_bits, frac_bits, ms):
             y = Fr(Y, 1 << P)
             k0, k1 = floor(y - h), ceil(y + h)
             F = 0
-            for k in range(max(k0, 0), k1 + 1):
-                F += g[k] * dbspline_int(N, P, Y - (k << P))
+            for k in range(max(k0, k_first), k1 + 1):
+                F += g[k - k_first] * dbspline_int(N, P, Y - (k << P))
             S += (-1) ** j * comb(n2 + 1, j) * F
         S_all.append(S)
         s_all.append(Fr(S * (1 << (q_bits * (n2 + 1))), D * Am ** (n2 + 1) * (1 << frac_bits)))

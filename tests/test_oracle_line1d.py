@@ -133,3 +133,115 @@ def test_planted_error_in_fd_weights_is_caught():
         F = sum(g[k] * o.dbspline_int(N, P, Y - (k << P)) for k in range(max(0, (Y >> P) - 3), (Y >> P) + 4))
         wrong += comb(2, j) * F
     assert Fr(wrong * (1 << 4), D * Am ** 2) != ref[5]
+
+
+# ------------------------------------ the interpolation prefilter (n1 >= 2)
+
+def _dec(fr):
+    from decimal import Decimal
+    return Decimal(fr.numerator) / Decimal(fr.denominator)
+
+
+def test_inverse_filter_matches_the_closed_forms():
+    # quadratic and cubic B-spline interpolation: the inverse of
+    # (z + 6 + 1/z)/8 is sqrt(2) (2 sqrt(2) - 3)^|k|, the inverse of
+    # (z + 4 + 1/z)/6 is sqrt(3) (sqrt(3) - 2)^|k| (one pole each, from the
+    # partial fractions of the symbol)
+    from decimal import Decimal, getcontext
+    getcontext().prec = 80
+    r2, r3 = Decimal(2).sqrt(), Decimal(3).sqrt()
+    h2, h3 = o.inverse_filter(2), o.inverse_filter(3)
+    tol = Decimal(10) ** -50
+    for k in range(-30, 31):
+        assert abs(_dec(h2[k]) - r2 * (2 * r2 - 3) ** abs(k)) < tol
+        assert abs(_dec(h3[k]) - r3 * (r3 - 2) ** abs(k)) < tol
+
+
+# Poles of the B-spline interpolation filters as published (Unser, "Splines:
+# a perfect fit for signal and image processing", IEEE SPM 1999, Table 1).
+_POLES = {
+    2: [-0.171572875253809902],
+    3: [-0.267949192431122706],
+    4: [-0.361341225900220177, -0.0137254292973391195],
+    5: [-0.430575347099973792, -0.0430962882032647440],
+}
+
+
+@pytest.mark.parametrize("n1", [2, 3, 4, 5])
+def test_inverse_filter_decays_with_the_published_poles(n1):
+    # for k >= 1 the inverse is a sum of z_p^k: it satisfies the recurrence
+    # whose characteristic roots are the poles, h[k+2] = (z1 + z2) h[k+1] - z1 z2 h[k]
+    # (one pole: h[k+1] = z1 h[k]); checked relative to |h[k]|
+    h = o.inverse_filter(n1)
+    z = _POLES[n1]
+    for k in range(1, 12):
+        if len(z) == 1:
+            pred = z[0] * float(h[k])
+            got = float(h[k + 1])
+        else:
+            pred = (z[0] + z[1]) * float(h[k + 1]) - z[0] * z[1] * float(h[k])
+            got = float(h[k + 2])
+        assert abs(got - pred) <= 1e-14 * abs(float(h[k])), (k, got, pred)
+        assert h[k] == h[-k]
+
+
+@pytest.mark.parametrize("n1", [2, 3, 4, 5])
+def test_prefilter_interpolates_the_samples(n1):
+    # the model f(x) = sum_j c[j] beta^{n1}(x - j) passes through f[k] at every
+    # integer (inside the window the oracle keeps, and zero outside the signal)
+    rng = np.random.default_rng(40 + n1)
+    F = 6
+    x = [int(v) for v in rng.integers(-300 << F, 300 << F, 25)]
+    kf, cs = o.prefilter(x, n1)
+    c = {kf + i: Fr(v, 1 << (200 + F)) for i, v in enumerate(cs)}
+    b = {k: o.bspline(n1, k) for k in range(-3, 4)}
+    for k in range(-40, 65):
+        val = sum(c.get(k - d, 0) * w for d, w in b.items())
+        want = Fr(x[k], 1 << F) if 0 <= k < len(x) else 0
+        assert abs(val - want) < Fr(1, 1 << 150), k
+
+
+def test_prefilter_commutes_with_reversal_and_is_linear():
+    rng = np.random.default_rng(8)
+    x = [int(v) for v in rng.integers(-1000, 1000, 19)]
+    y = [int(v) for v in rng.integers(-1000, 1000, 19)]
+    kf, cx = o.prefilter(x, 3)
+    _, cr = o.prefilter(x[::-1], 3)
+    assert cr == cx[::-1]
+    _, cy = o.prefilter(y, 3)
+    _, cxy = o.prefilter([a + b for a, b in zip(x, y)], 3)
+    assert all(abs(a + b - s) <= 2 for a, b, s in zip(cx, cy, cxy))
+
+
+@pytest.mark.parametrize("n1,n2", [(2, 0), (2, 2), (3, 1), (4, 1), (5, 0)])
+def test_quantised_model_moves_s_by_at_most_half_a_grid_step(n1, n2):
+    # the Proposition on c_q = rint(c 2^F) against the definition on the exact c:
+    # |s_q - s| <= 2^-(F+1) sum_k K(m - k) = 2^-(F+1) (K >= 0, unit lattice sum)
+    rng = np.random.default_rng(70 + 10 * n1 + n2)
+    q, F = 3, 5
+    x = [int(v) for v in rng.integers(-60 << F, 60 << F, 24)]
+    A = o.quantise(rng.uniform(0.5, 4.0, 24), q)
+    kf, cs = o.prefilter(x, n1)
+    s = o.filter_direct([Fr(v, 1 << (200 + F)) for v in cs], A, n2, q, n1, k_first=kf)
+    kq, cq = o.prefilter_quantised(x, n1)
+    assert kq == kf
+    _, sq = o.filter_paper(cq, A, n1, n2, q, F, k_first=kq)
+    assert max(abs(a - b) for a, b in zip(s, sq)) <= Fr(1, 1 << (F + 1))
+
+
+@pytest.mark.parametrize("n1,n2", [(2, 0), (2, 1), (3, 0), (3, 2)])
+def test_kernel_at_unit_scale_is_a_bspline_higher_model_degree(n1, n2):
+    for t in (Fr(0), Fr(1, 4), Fr(3, 2), Fr(-9, 8)):
+        assert o.kernel(n1, n2, 1, t) == o.bspline(n1 + n2 + 1, t)
+
+
+def test_planted_causal_only_prefilter_is_caught():
+    # dropping the anti-causal half of the inverse breaks interpolation
+    h = o.inverse_filter(3)
+    half = {k: (v if k >= 0 else Fr(0)) for k, v in h.items()}
+    x = [7, -2, 5]
+    c = {k: sum(x[j] * half.get(k - j, 0) for j in range(3)) for k in range(-20, 23)}
+    b = {k: o.bspline(3, k) for k in (-1, 0, 1)}
+    resid = max(abs(sum(c.get(k - d, 0) * w for d, w in b.items()) - (x[k] if 0 <= k < 3 else 0))
+                for k in range(-5, 8))
+    assert resid > Fr(1, 10)
