@@ -447,6 +447,10 @@ def run_line1d(args):
         dist.barrier()
     shp = _shape(args) or (2048, 65536)
     w = synthetic.workload_1d(count=shp[0], length=shp[1], seed_offset=rank)
+    if args.n1 is not None:
+        w["n1"] = args.n1
+    if args.n2 is not None:
+        w["n2"] = args.n2
     f, a = w["signals"], w["scales"]
     count, length = f.shape
     flt = AdaptiveFilter1D(length, count, w["n1"], w["n2"], torch.float32, q_bits=w["q_bits"],
@@ -520,12 +524,14 @@ def run_line1d(args):
         "unit": "Msample/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64x%d" % L, "data": "synthetic",
-        "config": {"workload": "%d signals x %d samples f32 (2^-16 grid), n1=1, n2=3, a in [1,64], Q=8, exact form"
-                               % (count, length), "l2": "inputs larger than L2 (signals %.0f MB, scales %.0f MB)"
+        "config": {"workload": "%d signals x %d samples f32 (2^-16 grid), n1=%d, n2=%d, a in [1,64], Q=8, exact form%s"
+                               % (count, length, w["n1"], w["n2"],
+                                  " (c = f * (b^n1)^-1 on the 2^-16 grid)" if w["n1"] >= 2 else ""),
+                   "l2": "inputs larger than L2 (signals %.0f MB, scales %.0f MB)"
                                % (f.nbytes / 1e6, a.nbytes / 1e6), "parallelism": "replicas x%d" % world},
         "e2e": {"value": round(replica_throughput(samples, K, world, e2e_ms), 3), "unit": "Msample/s",
                 "h2d_bytes_per_step": int(f.nbytes + a.nbytes), "d2h_bytes_per_step": int(o_h.numel() * 4)},
-        "gpu_launches": int(K * 2),
+        "gpu_launches": int(K * (3 if w["n1"] >= 2 else 2)),
         "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
         "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak / 1e9, 2),
                      "unit": "G MAC/s (%d-limb integer x 64-bit weight)" % L, "frac": round(achieved / peak, 4),
@@ -536,7 +542,8 @@ def run_line1d(args):
         "roofline_integrate": {"bound": "hbm", "achieved": round((f.nbytes + samples * 8 * L) / (integ_ms * 1e-3)
                                                                  / 1e9, 1),
                                "peak": _peaks().get("hbm_gbs"), "unit": "GB/s",
-                               "bytes_note": "f read once, g written once"},
+                               "bytes_note": "f read once, g written once" +
+                                             ("; prefilter + row pass" if w["n1"] >= 2 else "")},
         "clocks": clk,
     }
     if rank == 0 and args.cpu_baseline:
@@ -549,7 +556,11 @@ def run_line1d(args):
             r = int(rng.integers(0, count))
             ms = sorted(rng.integers(0, length, 64).tolist())
             A = o.quantise(a[r], w["q_bits"])
-            o.filter_paper_at(list(fi[r]), A, w["n1"], w["n2"], w["q_bits"], w["frac_bits"], ms)
+            if w["n1"] >= 2:
+                kq, cq = o.prefilter_quantised([int(v) for v in fi[r]], w["n1"])
+            else:
+                kq, cq = 0, list(fi[r])
+            o.filter_paper_at(cq, A, w["n1"], w["n2"], w["q_bits"], w["frac_bits"], ms, k_first=kq)
             done += len(ms)
         el = time.perf_counter() - t_start
         line["cpu_baseline"] = {"value": done / el / 1e6, "unit": "Msample/s", "cores": 1, "kind": "oracle",
@@ -787,6 +798,8 @@ def main():
     ap.add_argument("--shape", default="", help="HxW: the same recipe at another size (profiling, sweeps)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--n1", type=int, default=None, help="d1: model degree (2..5 interpolate the samples)")
+    ap.add_argument("--n2", type=int, default=None, help="d1: analysis degree")
     ap.add_argument("--pool", type=int, default=8, help="c5: distinct images in the request pool")
     ap.add_argument("--inflight", type=int, default=4, help="c5: concurrent jobs (slots)")
     ap.add_argument("--jobs", type=int, default=200, help="c5: measured jobs per load")

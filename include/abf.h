@@ -346,12 +346,21 @@ abf_status abf_estimate_ellipses(const void* d_f, size_t f_pitch, abf_dtype in_d
  * interpolation at y_j = m + tau - a j, tau = (a-1)(n2+1)/2 (Eq. (link)):
  *   S[m] = sum_j (-1)^j binom(n2+1, j) sum_k g[k] D beta^N(y_j - k),
  *   s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F),  D = N! 2^(N (Q+1)),
- * with A = rint(a 2^Q).  The signal is zero outside [0, length).  n1 >= 2
- * (an irrational IIR prefilter) is not served (ABF_ERR_UNSUPPORTED).        */
+ * with A = rint(a 2^Q).  The signal is zero outside [0, length).
+ * For n1 in 2..5 the model coefficients c = f * (b^{n1})^-1 (b^{n1}[k] =
+ * beta^{n1}(k), the B-spline interpolation filter; the inverse is two-sided
+ * and irrational) are rounded to the 2^-F grid, c_q = rint(c 2^F), and the
+ * two steps run exactly on c_q, which starts `left` samples before the signal
+ * (its decaying tail).  Since the kernel of s in terms of c is non-negative
+ * with unit lattice sum, |s - s(c)| <= 2^-(F+1) plus the prefilter's own
+ * error (binary64 poles and weights in 64-bit fixed point: about
+ * 2^-46 |f|max 2^F + 2^-18 grid steps), which can only move c_q by one step
+ * where c 2^F lies that close to a rounding tie.
+ * n1 >= 6 returns ABF_ERR_UNSUPPORTED.                                       */
 typedef struct {
   int32_t length;         /* samples per signal, >= 1                           */
   int32_t count;          /* signals (rows), >= 1                               */
-  int32_t n1;             /* model degree: 0 or 1                               */
+  int32_t n1;             /* model degree: 0..5                                 */
   int32_t n2;             /* analysis degree: 0..3                              */
   abf_dtype in_dtype;     /* f elements                                         */
   abf_dtype out_dtype;    /* s elements: ABF_F32 or ABF_F64                     */
@@ -364,22 +373,29 @@ typedef struct {
 typedef struct abf1d_plan_s* abf1d_plan;
 
 /* Plan: validates the descriptor, picks the limb count L from the numerator
- * bound D max_scale^(n2+1) |f|max 2^F (|s| <= |f|max: the kernel is
- * non-negative with unit lattice sum), uploads the D beta^N table.
- * ABF_ERR_RANGE if L would exceed 4.                                         */
+ * bound D max_scale^(n2+1) |c|max 2^F (|s| <= |c|max: the kernel is
+ * non-negative with unit lattice sum; |c|max = |f|max for n1 <= 1, else
+ * ||(b^{n1})^-1||_1 |f|max), uploads the D beta^N table.  For n1 >= 2 the
+ * plan also owns a staging buffer for c_q (count x g_pitch_elems int32, or
+ * int64 when ||(b^{n1})^-1||_1 |f|max 2^F does not fit 31 bits).
+ * ABF_ERR_RANGE if L would exceed 4, or (n1 >= 2) if |f|max 2^F leaves fewer
+ * than 24 guard bits in the prefilter's 64-bit fixed point (about 2^35).    */
 abf_status abf1d_plan_create(const abf1d_desc* desc, abf1d_plan* out);
 abf_status abf1d_plan_destroy(abf1d_plan plan);
 
 /* integrated_bytes: size of the integrated signals g (count rows of
- * g_pitch_elems elements of L uint64 limbs); right: samples past the signal
- * end that g holds (the adaptive step reads up to tau + (N+1)/2 beyond it).  */
-abf_status abf1d_plan_query(abf1d_plan plan, size_t* integrated_bytes, int32_t* right, int32_t* limbs,
-                            int64_t* g_pitch_elems);
+ * g_pitch_elems elements of L uint64 limbs; element i holds g at signal
+ * position i - left); left: samples before the signal start that g holds (0
+ * for n1 <= 1); right: samples past the signal end that g holds (the adaptive
+ * step reads up to tau + (N+1)/2 beyond it).  Any pointer may be NULL.      */
+abf_status abf1d_plan_query(abf1d_plan plan, size_t* integrated_bytes, int32_t* left, int32_t* right,
+                            int32_t* limbs, int64_t* g_pitch_elems);
 
-/* Non-adaptive step: g = u_1^{(n2+1)} * (f 2^F) per row, exact modulo
- * 2^(64 L).  d_f: count rows of length in_dtype elements (row pitch in
- * bytes); d_g: plan-sized, 16-byte aligned.  Off-grid or out-of-bound float
- * inputs read as 0 and set ABF_DEV_BAD_INPUT.                                */
+/* Non-adaptive step: g = u_1^{(n2+1)} * (c 2^F) per row, exact modulo
+ * 2^(64 L) (c = f for n1 <= 1; the prefiltered c_q for n1 >= 2).  d_f: count
+ * rows of length in_dtype elements (row pitch in bytes); d_g: plan-sized,
+ * 16-byte aligned.  Off-grid or out-of-bound float inputs read as 0 and set
+ * ABF_DEV_BAD_INPUT.  Launches: the prefilter (n1 >= 2), then the row pass.  */
 abf_status abf1d_integrate(abf1d_plan plan, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t stream);
 
 /* Adaptive step: d_a holds one float32 scale a per sample (count rows, row

@@ -105,7 +105,7 @@ def lib():
         "abf_server_destroy": ([vp], st),
         "abf1d_plan_create": ([P(abf1d_desc), P(vp)], st),
         "abf1d_plan_destroy": ([vp], st),
-        "abf1d_plan_query": ([vp, P(sz), P(i32), P(i32), P(ctypes.c_int64)], st),
+        "abf1d_plan_query": ([vp, P(sz), P(i32), P(i32), P(i32), P(ctypes.c_int64)], st),
         "abf1d_integrate": ([vp, vp, sz, vp, vp], st),
         "abf1d_filter": ([vp, vp, vp, sz, vp, sz, vp], st),
         "abf1d_filter_numerator": ([vp, vp, vp, sz, vp, sz, vp], st),
@@ -298,10 +298,12 @@ def abf1d_plan_destroy(plan):
 
 
 def abf1d_plan_query(plan):
-    gb, right, limbs, pitch = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
-    _check(lib().abf1d_plan_query(plan, ctypes.byref(gb), ctypes.byref(right), ctypes.byref(limbs),
-                                  ctypes.byref(pitch)), "abf1d_plan_query")
-    return dict(integrated_bytes=gb.value, right=right.value, limbs=limbs.value, g_pitch=pitch.value)
+    gb, left, right = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32()
+    limbs, pitch = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().abf1d_plan_query(plan, ctypes.byref(gb), ctypes.byref(left), ctypes.byref(right),
+                                  ctypes.byref(limbs), ctypes.byref(pitch)), "abf1d_plan_query")
+    return dict(integrated_bytes=gb.value, left=left.value, right=right.value, limbs=limbs.value,
+                g_pitch=pitch.value)
 
 
 def abf1d_integrate(plan, f, f_pitch, g, stream=None):

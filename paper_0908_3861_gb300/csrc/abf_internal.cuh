@@ -5,6 +5,7 @@
 // are formed in this ring; only the final numerator, whose true size is bounded
 // (abf_plan_create checks the bound), is read back as a signed integer.
 #pragma once
+#include <type_traits>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/abf.h"
@@ -566,6 +567,11 @@ struct Stencil {
 // ---------------------------------------------------------------- host side
 
 // Everything a kernel needs to know about one plan (passed by value).
+// Row-pass input types beyond abf_dtype: integer coefficients staged on the
+// device (the 1-D prefilter's output), read without conversion or checks.
+constexpr int kStageI32 = 16;
+constexpr int kStageI64 = 17;
+
 struct PlanView {
   int W, H, n, Q, P, F;
   int left, right, above;         // lattice box margins (rows start at k2 = 0)
@@ -665,6 +671,45 @@ __device__ __forceinline__ bool pixel_steps(const PlanView& pv, const float4* sc
 __device__ __forceinline__ void raise_status(int32_t* st, int32_t bits) {
   atomicOr(st, bits);
 }
+
+// Input element -> integer f 2^F; raises ABF_DEV_BAD_INPUT (and reads 0) when
+// a floating-point value is off the 2^-F grid or beyond the value bound
+// (bound_i = floor(value_bound 2^F)).  binary32 inputs are checked in binary32
+// (scaling by 2^F is exact, rintf is exact) and integers, keeping the per-sample
+// work off the slow binary64 pipe.
+template <typename TIn>
+__device__ __forceinline__ int64_t convert_f(TIn raw, double scale, long long bound_i, int32_t* status) {
+  if constexpr (std::is_integral<TIn>::value) {
+    if constexpr (sizeof(TIn) <= 2) return (int64_t)raw * (int64_t)scale;  // u8 / u16 samples
+    else return (int64_t)raw;  // integer coefficients staged by the 1-D prefilter: already c 2^F
+  } else if constexpr (sizeof(TIn) == 4) {
+    const float v = raw * (float)scale;  // exact: scale is a power of two (inf if it overflows)
+    if (!(rintf(v) == v) || !(fabsf(v) < 4.0e18f)) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    const long long r = __float2ll_rn(v);
+    if (r > bound_i || r < -bound_i) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    return r;
+  } else {
+    const double v = (double)raw * scale;  // exact: scale is a power of two
+    const double r = rint(v);
+    if (!(r == v) || !(fabs(r) < 4.0e18)) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    const long long ri = (long long)r;
+    if (ri > bound_i || ri < -bound_i) {
+      raise_status(status, ABF_DEV_BAD_INPUT);
+      return 0;
+    }
+    return ri;
+  }
+}
+
 
 }  // namespace abf
 

@@ -1,11 +1,14 @@
 // The 1-D scale-adaptive B-spline filter of Sec. 3 (Proposition "prop"), exact
 // form, on a batch of signals (one per row).
 //
-//   Non-adaptive step: g = u_1^{(n2+1)} * c, n2+1 causal running sums of
-//     c = f 2^F (c = f because the model degree n1 is 0 or 1, where the
-//     interpolation prefilter (b^{n1})^-1 is the identity).  The row pass of
-//     scan.cu runs it, on rows extended by `right` samples past the signal end
-//     (the sums keep changing there while the adaptive step reads them).
+//   Non-adaptive step: g = u_1^{(n2+1)} * c, n2+1 causal running sums of the
+//     model coefficients c 2^F.  For model degree n1 in {0, 1} the
+//     interpolation prefilter (b^{n1})^-1 is the identity and c = f; for n1 in
+//     2..5 `prefilter_kernel` computes c = f * (b^{n1})^-1 rounded to the 2^-F
+//     grid (below).  The row pass of scan.cu runs the sums, on rows extended by
+//     `left` samples before the signal (the prefilter's tail; 0 for n1 <= 1)
+//     and `right` samples past its end (the sums keep changing there while the
+//     adaptive step reads them).
 //   Adaptive step: s[m] = Delta_a^{n2+1} F(m), F(x) = sum_k g[k] beta^N(x +
 //     tau - k), N = n1 + n2 + 1, tau = (a - 1)(n2 + 1)/2 (Eq. (link)): the FD
 //     mask d^{n2+1}_a of Eq. (FD) at the points y_j = m + tau - a j, each
@@ -33,6 +36,7 @@ cudaError_t run_row_scan(const PlanView& pv, const void* f, size_t f_pitch, uint
 
 struct Line1dView {
   int length, count, n1, n2, N, Q, P, F, K, dmin;
+  int left;          // samples of g before the signal (g index = k + left)
   int Amax;
   long long Gp;      // row pitch of g, elements
   int limbs;
@@ -61,8 +65,10 @@ __device__ __forceinline__ int binom_n2p1(int j) {
   return c;
 }
 
-// One thread per output sample.
-template <int L, int N2>
+// One thread per output sample.  KK = K, the table's neighbours per row, so
+// the neighbour loop unrolls; g holds zeros for the adaptive step's whole
+// reach before the signal, so no read needs a bounds check.
+template <int L, int N2, int KK>
 __global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const uint64_t* __restrict__ g,
                                                      const float* __restrict__ a, size_t a_pitch, void* s,
                                                      size_t s_pitch, uint64_t* num, size_t num_pitch,
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const u
     }
     return;
   }
-  const int P = v.P, K = v.K;
+  const int P = v.P;
   const long long mask = (1ll << P) - 1;
   const long long tauP = (A - (1ll << v.Q)) * (N2 + 1);  // tau in units of 2^-P
   const uint64_t* grow = g + (size_t)row * (size_t)v.Gp * L;
@@ -107,15 +113,12 @@ __global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const u
     const long long Y = ((long long)m << P) + tauP - 2 * A * j;  // y_j in units of 2^-P
     const long long p = Y >> P;
     const int r = (int)(Y & mask);
-    const uint64_t* trow = v.table + (size_t)r * K;
+    const uint64_t* trow = v.table + (size_t)r * KK;
+    const uint64_t* gk = grow + (size_t)(p + v.dmin + v.left) * L;
     Wide<L> Fj;
     wzero<L>(Fj);
-    for (int d = 0; d < K; ++d) {
-      const long long k = p + v.dmin + d;
-      if (k < 0) continue;  // the running sums vanish before the signal
-      const Wide<L> gv = wload<L>(grow + (size_t)k * L);
-      mac64<L>(Fj, gv, __ldg(trow + d));
-    }
+#pragma unroll
+    for (int d = 0; d < KK; ++d) mac64<L>(Fj, wload<L>(gk + (size_t)d * L), __ldg(trow + d));
     Wide<L> t;
     wzero<L>(t);
     wmac<L>(t, Fj, (uint64_t)binom_n2p1<N2>(j));
@@ -138,18 +141,29 @@ __global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const u
   }
 }
 
+template <int L, int N2, int KK>
+static cudaError_t launch_mesh1d_K(const Line1dView& v, const uint64_t* g, const float* a, size_t a_pitch, void* s,
+                                   size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
+                                   cudaStream_t st) {
+  dim3 grid((v.length + 255) / 256, v.count);
+  mesh1d_kernel<L, N2, KK><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status);
+  return cudaGetLastError();
+}
+
+// K = N + 1 (N odd) or N + 2 (N even), N = n1 + n2 + 1 with n1 in 0..5: the
+// pairs (n2, K) that occur.
 template <int L>
 static cudaError_t launch_mesh1d_L(const Line1dView& v, const uint64_t* g, const float* a, size_t a_pitch, void* s,
                                    size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status,
                                    cudaStream_t st) {
-  dim3 grid((v.length + 255) / 256, v.count);
-  switch (v.n2) {
-    case 0: mesh1d_kernel<L, 0><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
-    case 1: mesh1d_kernel<L, 1><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
-    case 2: mesh1d_kernel<L, 2><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
-    default: mesh1d_kernel<L, 3><<<grid, 256, 0, st>>>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status); break;
-  }
-  return cudaGetLastError();
+#define ABF_MESH1D(N2, KK) \
+  if (v.n2 == N2 && v.K == KK) return launch_mesh1d_K<L, N2, KK>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st)
+  ABF_MESH1D(0, 2); ABF_MESH1D(0, 4); ABF_MESH1D(0, 6); ABF_MESH1D(0, 8);
+  ABF_MESH1D(1, 4); ABF_MESH1D(1, 6); ABF_MESH1D(1, 8);
+  ABF_MESH1D(2, 4); ABF_MESH1D(2, 6); ABF_MESH1D(2, 8); ABF_MESH1D(2, 10);
+  ABF_MESH1D(3, 6); ABF_MESH1D(3, 8); ABF_MESH1D(3, 10);
+#undef ABF_MESH1D
+  return cudaErrorInvalidValue;
 }
 
 static cudaError_t run_mesh1d(const Line1dView& v, const uint64_t* g, const float* a, size_t a_pitch, void* s,
@@ -159,6 +173,124 @@ static cudaError_t run_mesh1d(const Line1dView& v, const uint64_t* g, const floa
     case 2: return launch_mesh1d_L<2>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
     case 3: return launch_mesh1d_L<3>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
     default: return launch_mesh1d_L<4>(v, g, a, a_pitch, s, s_pitch, num, num_pitch, status, st);
+  }
+}
+
+// ----------------------------------------- interpolation prefilter (n1 >= 2)
+// c = f * (b^{n1})^-1 (Sec. 3).  The inverse of the symmetric B-spline
+// interpolation filter is, by partial fractions over the poles z_p in (-1, 0)
+// of its symbol (one for n1 = 2, 3, two for n1 = 4, 5), a sum of two-sided
+// exponentials h[k] = sum_p A_p z_p^|k|, so
+//   c[k] = sum_p A_p (y+_p[k] + y-_p[k] - x[k]),
+//   y+_p[k] = x[k] + z_p y+_p[k-1]  (causal),  y-_p[k] = x[k] + z_p y-_p[k+1]  (anti-causal),
+// with x = f 2^F zero outside the signal.  The exact form takes c on the 2^-F
+// grid, c_q = rint(c 2^F) (ties to even), so the recursions need only a bounded
+// error below that grid: they run in 64-bit fixed point with G guard bits
+// (x 2^G; z_p as rint(z_p 2^64) through the high half of a signed 64 x 64
+// product; A_p as rint(A_p 2^60)), on the integer pipe rather than the binary64
+// one (a thirty-second of the integer multiply-add rate on GB300).  A thread
+// owns kPfSeg consecutive outputs and starts each recursion W_p samples early
+// from a zero state (|z_p|^W_p 2^63 < 1/8 unit); the CTA stages its tile of x
+// with both halos in shared memory (one pad word per 32 keeps the threads'
+// strided reads off a common bank) and stores c_q through it, coalesced.
+constexpr int kPfThreads = 128;
+constexpr int kPfSeg = 32;                          // outputs per thread
+constexpr int kPfTile = kPfThreads * kPfSeg;        // outputs per CTA
+constexpr int kPfHalo = 64;                         // >= every W_p
+constexpr int kPfStage = kPfTile + 2 * kPfHalo;     // staged samples
+constexpr int kPfSmem = kPfStage + kPfStage / 32 + 1;
+constexpr int kPfMaxPoles = 2;
+
+struct PrefilterView {
+  int length, Gw, left, G, npoles;
+  int W[kPfMaxPoles];            // warm-up samples per pole
+  long long Z[kPfMaxPoles];      // rint(z_p 2^64)
+  long long A[kPfMaxPoles];      // rint(A_p 2^60)
+  double scale;                  // 2^F
+  long long bound;               // floor(value_bound 2^F)
+};
+
+__device__ __forceinline__ int pf_pad(int j) { return j + (j >> 5); }
+
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kPfThreads) prefilter_kernel(const PrefilterView v, const TIn* __restrict__ f,
+                                                               size_t f_pitch, TOut* __restrict__ c,
+                                                               long long c_pitch, int32_t* status) {
+  __shared__ long long sx[kPfSmem];
+  const int row = blockIdx.y;
+  const long long i0 = (long long)blockIdx.x * kPfTile;  // first output (g index; k = i - left)
+  const TIn* frow = reinterpret_cast<const TIn*>(reinterpret_cast<const char*>(f) + (size_t)row * f_pitch);
+  for (int j = threadIdx.x; j < kPfStage; j += kPfThreads) {
+    const long long k = i0 - kPfHalo + j - v.left;
+    long long xv = 0;
+    if (k >= 0 && k < v.length) xv = convert_f<TIn>(frow[k], v.scale, v.bound, status);
+    sx[pf_pad(j)] = xv;
+  }
+  __syncthreads();
+  const long long one = 1ll << v.G;
+  long long acc[kPfSeg];  // c 2^F in units of 2^-(G-4)
+#pragma unroll
+  for (int e = 0; e < kPfSeg; ++e) acc[e] = 0;
+  const int jb = kPfHalo + threadIdx.x * kPfSeg;
+#pragma unroll
+  for (int p = 0; p < kPfMaxPoles; ++p) {
+    if (p >= v.npoles) break;
+    const long long Z = v.Z[p], A = v.A[p];
+    const int W = v.W[p];
+    long long y = 0;
+    for (int j = jb - W; j < jb; ++j) y = sx[pf_pad(j)] * one + __mul64hi(y, Z);
+#pragma unroll
+    for (int e = 0; e < kPfSeg; ++e) {
+      const long long xs = sx[pf_pad(jb + e)] * one;
+      y = xs + __mul64hi(y, Z);
+      acc[e] += __mul64hi(y - xs, A);
+    }
+    y = 0;
+    for (int j = jb + kPfSeg - 1 + W; j >= jb + kPfSeg; --j) y = sx[pf_pad(j)] * one + __mul64hi(y, Z);
+#pragma unroll
+    for (int e = kPfSeg - 1; e >= 0; --e) {
+      y = sx[pf_pad(jb + e)] * one + __mul64hi(y, Z);
+      acc[e] += __mul64hi(y, A);
+    }
+  }
+  __syncthreads();  // every thread is done with x
+  const int sh = v.G - 4;
+  const long long half = 1ll << (sh - 1);
+#pragma unroll
+  for (int e = 0; e < kPfSeg; ++e) {
+    long long q = acc[e] >> sh;  // floor
+    const long long r = acc[e] - q * (1ll << sh);
+    if (r > half || (r == half && (q & 1))) ++q;
+    sx[pf_pad(threadIdx.x * kPfSeg + e)] = q;
+  }
+  __syncthreads();
+  TOut* crow = c + (size_t)row * (size_t)c_pitch;
+  for (int j = threadIdx.x; j < kPfTile; j += kPfThreads) {
+    const long long i = i0 + j;
+    if (i < v.Gw) crow[i] = (TOut)sx[pf_pad(j)];
+  }
+}
+
+template <typename TIn>
+static cudaError_t launch_prefilter_in(const PrefilterView& v, int count, const void* f, size_t f_pitch,
+                                       void* c, long long c_pitch, bool wide, int32_t* status, cudaStream_t st) {
+  dim3 grid((unsigned)((v.Gw + kPfTile - 1) / kPfTile), (unsigned)count);
+  if (wide)
+    prefilter_kernel<TIn, long long><<<grid, kPfThreads, 0, st>>>(v, (const TIn*)f, f_pitch, (long long*)c, c_pitch,
+                                                                  status);
+  else
+    prefilter_kernel<TIn, int32_t><<<grid, kPfThreads, 0, st>>>(v, (const TIn*)f, f_pitch, (int32_t*)c, c_pitch,
+                                                                status);
+  return cudaGetLastError();
+}
+
+static cudaError_t run_prefilter(const PrefilterView& v, int count, int in_dtype, const void* f, size_t f_pitch,
+                                 void* c, long long c_pitch, bool wide, int32_t* status, cudaStream_t st) {
+  switch (in_dtype) {
+    case ABF_U8: return launch_prefilter_in<uint8_t>(v, count, f, f_pitch, c, c_pitch, wide, status, st);
+    case ABF_U16: return launch_prefilter_in<uint16_t>(v, count, f, f_pitch, c, c_pitch, wide, status, st);
+    case ABF_F32: return launch_prefilter_in<float>(v, count, f, f_pitch, c, c_pitch, wide, status, st);
+    default: return launch_prefilter_in<double>(v, count, f, f_pitch, c, c_pitch, wide, status, st);
   }
 }
 
@@ -207,12 +339,67 @@ static bool build_table_1d(int N, int P, int K, int dmin, std::vector<uint64_t>&
   return true;
 }
 
+// Neighbours d with beta^N(r - d) != 0 for some r in [0, 1): -(N+1)/2 < d < (N+3)/2.
+static void table_shape(int N, int* dmin, int* K) {
+  *dmin = (N % 2) ? -(N + 1) / 2 + 1 : -N / 2;
+  *K = (N % 2) ? N + 1 : N + 2;
+}
+
+// Poles z_p and partial-fraction weights A_p of (b^{n1})^-1, n1 = 2..5:
+// h[k] = sum_p A_p z_p^|k|.  With w = q + 1/q the symbol
+// b_0 + sum_{k>=1} b_k (q^k + q^-k) is a polynomial of degree M = n1/2 in w
+// (q^2 + q^-2 = w^2 - 2); each root w_p < -2 gives z_p + 1/z_p = w_p, and
+// 1/(w - w_p) = -z_p / ((1 - z_p q^-1)(1 - z_p q)) expands to
+// -z_p / (1 - z_p^2) sum_k z_p^|k| q^k.
+struct PoleSet {
+  int M;
+  double z[2], A[2];
+  double hnorm;  // sum_p |A_p| (1 + |z_p|) / (1 - |z_p|) >= ||h||_1
+};
+
+static bool interp_poles(int n1, PoleSet& ps) {
+  if (n1 < 2 || n1 > 5) return false;
+  // b^{n1}[k] = beta^{n1}(k) from the degree recurrence at P = 1 (row r = 0)
+  int dmin = 0, K = 0;
+  table_shape(n1, &dmin, &K);
+  std::vector<uint64_t> t;
+  unsigned long long D = 0;
+  if (!build_table_1d(n1, 1, K, dmin, t, &D)) return false;
+  double b[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k <= n1 / 2; ++k) b[k] = (double)t[(size_t)(-k - dmin)] / (double)D;  // beta(k) = beta(-k)
+  ps.M = n1 / 2;
+  double w[2];
+  if (ps.M == 1) {
+    w[0] = -b[0] / b[1];
+  } else {
+    const double disc = b[1] * b[1] - 4.0 * b[2] * (b[0] - 2.0 * b[2]);
+    if (!(disc > 0.0)) return false;
+    const double q = -0.5 * (b[1] + std::sqrt(disc));  // b[1] > 0: no cancellation
+    w[0] = (b[0] - 2.0 * b[2]) / q;
+    w[1] = q / b[2];
+  }
+  ps.hnorm = 0.0;
+  for (int p = 0; p < ps.M; ++p) {
+    if (!(w[p] < -2.0)) return false;
+    ps.z[p] = 2.0 / (w[p] - std::sqrt(w[p] * w[p] - 4.0));  // the root inside (-1, 0), no cancellation
+    const double res = -ps.z[p] / (1.0 - ps.z[p] * ps.z[p]);
+    if (ps.M == 1) ps.A[p] = res / b[1];
+    else ps.A[p] = (p == 0 ? 1.0 : -1.0) * res / (b[2] * (w[0] - w[1]));
+    const double az = std::fabs(ps.z[p]);
+    ps.hnorm += std::fabs(ps.A[p]) * (1.0 + az) / (1.0 - az);
+  }
+  return true;
+}
+
 struct abf1d_plan_s {
   abf1d_desc desc;
   abf::Line1dView v;
   abf::PlanView rows;   // the row pass over the extended signals
+  abf::PrefilterView pf;
   uint64_t* d_table = nullptr;
   int32_t* d_status = nullptr;
+  void* d_stage = nullptr;   // n1 >= 2: c_q per row (int32 or int64, g's pitch)
+  bool stage_wide = false;
   size_t g_bytes = 0;
   int right = 0;
 };
@@ -224,7 +411,7 @@ abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
   *out = nullptr;
   if (d->length < 1 || d->count < 1 || d->count > 65535) return ABF_ERR_INVALID;
   if (d->n1 < 0 || d->n2 < 0 || d->n2 > 3) return ABF_ERR_INVALID;
-  if (d->n1 > 1) return ABF_ERR_UNSUPPORTED;
+  if (d->n1 > 5) return ABF_ERR_UNSUPPORTED;
   if (d->in_dtype < ABF_U8 || d->in_dtype > ABF_F64) return ABF_ERR_INVALID;
   if (d->out_dtype != ABF_F32 && d->out_dtype != ABF_F64) return ABF_ERR_INVALID;
   if (d->q_bits < 1 || d->q_bits > 10 || d->in_frac_bits < 0 || d->in_frac_bits > 40) return ABF_ERR_INVALID;
@@ -239,9 +426,8 @@ abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
     else return ABF_ERR_INVALID;
   }
   const int N = d->n1 + d->n2 + 1, P = d->q_bits + 1;
-  // neighbours d with beta^N(r - d) != 0 for some r in [0, 1): -(N+1)/2 < d < (N+3)/2
-  const int dmin = (N % 2) ? -(N + 1) / 2 + 1 : -N / 2;
-  const int K = (N % 2) ? N + 1 : N + 2;
+  int dmin = 0, K = 0;
+  table_shape(N, &dmin, &K);
   std::vector<uint64_t> tab;
   unsigned long long D = 0;
   try {
@@ -249,9 +435,45 @@ abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
   } catch (const std::bad_alloc&) {
     return ABF_ERR_OOM;
   }
-  // |s| <= |f|max (non-negative kernel, unit lattice sum), so
-  // |S| <= D max_scale^(n2+1) |f|max 2^F.
-  const double lb = std::log2((double)D) + (d->n2 + 1) * std::log2((double)Amax / qd) + std::log2(vb) +
+  // Model coefficients: c = f (n1 <= 1) or c = f * (b^{n1})^-1 rounded to the
+  // 2^-F grid, |c_q| <= hnorm |f|max + 2^-(F+1).
+  const double xmax = std::ldexp(vb, d->in_frac_bits);  // bound on |f 2^F|
+  PoleSet ps{};
+  abf::PrefilterView pf{};
+  double cmax = vb;
+  int left = 0;
+  bool wide = false;
+  if (d->n1 >= 2) {
+    if (!interp_poles(d->n1, ps)) return ABF_ERR_UNSUPPORTED;
+    double zmax = 0.0;
+    for (int q = 0; q < ps.M; ++q) zmax = std::max(zmax, std::fabs(ps.z[q]));
+    // guard bits: |x 2^G|, |y+ 2^G|, |y- 2^G| and their combination stay below 2^61
+    const int G = (int)std::floor(61.0 - std::log2(xmax * (2.0 / (1.0 - zmax) + 1.0)));
+    if (G < 24) return ABF_ERR_RANGE;
+    pf.G = std::min(G, 40);
+    pf.npoles = ps.M;
+    for (int q = 0; q < ps.M; ++q) {
+      const double az = std::fabs(ps.z[q]);
+      pf.W[q] = std::min(abf::kPfHalo, (int)std::ceil(66.0 / -std::log2(az)));
+      pf.Z[q] = std::llrint(std::ldexp(ps.z[q], 64));
+      pf.A[q] = std::llrint(std::ldexp(ps.A[q], 60));
+      if (!(std::fabs(ps.A[q]) < 7.0)) return ABF_ERR_UNSUPPORTED;
+    }
+    // left tail: for k <= -(left+1), |c[k]| <= xmax sum_p |A_p| |z_p|^(left+1) / (1 - |z_p|) < 1/4
+    for (left = 0; left < 4096; ++left) {
+      double t = 0.0;
+      for (int q = 0; q < ps.M; ++q) {
+        const double az = std::fabs(ps.z[q]);
+        t += std::fabs(ps.A[q]) * std::pow(az, left + 1) / (1.0 - az);
+      }
+      if (xmax * t < 0.25) break;
+    }
+    cmax = ps.hnorm * vb + std::ldexp(1.0, -d->in_frac_bits);
+    wide = !(ps.hnorm * xmax + 1.0 < 2147483647.0);
+  }
+  // |s| <= |c|max (non-negative kernel, unit lattice sum), so
+  // |S| <= D max_scale^(n2+1) |c|max 2^F.
+  const double lb = std::log2((double)D) + (d->n2 + 1) * std::log2((double)Amax / qd) + std::log2(cmax) +
                     d->in_frac_bits + 1e-6;
   const int L = (int)std::floor((lb + 1.0) / 64.0) + 1;
   if (L > abf::kMaxLimbs) return ABF_ERR_RANGE;
@@ -264,29 +486,60 @@ abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
   abf::Line1dView& v = p->v;
   v.length = d->length; v.count = d->count; v.n1 = d->n1; v.n2 = d->n2; v.N = N; v.Q = d->q_bits; v.P = P;
   v.F = d->in_frac_bits; v.K = K; v.dmin = dmin; v.Amax = Amax; v.limbs = L; v.out_dtype = d->out_dtype;
-  v.log2_base = (float)(std::log2((double)D) + std::log2(vb) + d->in_frac_bits);
+  // g keeps zeros before the signal for the adaptive step's reach there
+  // (y_j >= -(a + 1)(n2 + 1)/2 >= -(tau_max + n2 + 1), and (N+1)/2 + 1 more
+  // for the B-spline's neighbours), so its reads need no bounds check
+  left = std::max(left, (int)std::ceil(tau_max + (d->n2 + 1) + (N + 1) / 2.0) + 2);
+  v.left = left;
+  v.log2_base = (float)(std::log2((double)D) + std::log2(cmax) + d->in_frac_bits);
   v.Dd = (double)D;
-  const long long Gw = (long long)d->length + p->right;
+  const long long Gw = (long long)left + d->length + p->right;
+  if (Gw >= (1ll << 31)) {
+    delete p;
+    return ABF_ERR_INVALID;
+  }
   v.Gp = (Gw + 3) / 4 * 4;
   abf::PlanView& r = p->rows;
   r = abf::PlanView{};
-  r.W = d->length; r.H = d->count; r.n = d->n2 + 1; r.Q = d->q_bits; r.P = P; r.F = d->in_frac_bits;
-  r.left = 0; r.right = p->right; r.above = 0; r.Gw = (int)Gw; r.Gh = d->count; r.Gp = v.Gp;
-  r.in_dtype = d->in_dtype; r.out_dtype = d->out_dtype; r.limbs = L; r.value_bound = vb;
+  r.H = d->count; r.n = d->n2 + 1; r.Q = d->q_bits; r.P = P; r.F = d->in_frac_bits;
+  r.above = 0; r.Gw = (int)Gw; r.Gh = d->count; r.Gp = v.Gp;
+  r.out_dtype = d->out_dtype; r.limbs = L; r.value_bound = vb;
+  if (d->n1 >= 2) {
+    // the row pass reads the staged c_q: the whole extended row is its input
+    r.W = (int)Gw; r.left = 0; r.right = 0;
+    r.in_dtype = wide ? abf::kStageI64 : abf::kStageI32;
+    pf.length = d->length; pf.Gw = (int)Gw; pf.left = left;
+    pf.scale = std::ldexp(1.0, d->in_frac_bits);
+    const double bd = std::floor(xmax);
+    pf.bound = bd < 4.0e18 ? (long long)bd : 4000000000000000000ll;
+    p->pf = pf;
+    p->stage_wide = wide;
+  } else {
+    r.W = d->length; r.left = left; r.right = p->right;
+    r.in_dtype = d->in_dtype;
+  }
   p->g_bytes = (size_t)v.Gp * (size_t)d->count * (size_t)L * 8;
   if (cudaMalloc(&p->d_table, tab.size() * sizeof(uint64_t)) != cudaSuccess) {
+    delete p;
+    return ABF_ERR_OOM;
+  }
+  if (d->n1 >= 2 &&
+      cudaMalloc(&p->d_stage, (size_t)v.Gp * (size_t)d->count * (wide ? 8 : 4)) != cudaSuccess) {
+    cudaFree(p->d_table);
     delete p;
     return ABF_ERR_OOM;
   }
   if (cudaMemcpy(p->d_table, tab.data(), tab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) {
     cudaFree(p->d_table);
+    if (p->d_stage) cudaFree(p->d_stage);
     delete p;
     return ABF_ERR_CUDA;
   }
   if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
     cudaFree(p->d_table);
     cudaFree(p->d_status);
+    if (p->d_stage) cudaFree(p->d_stage);
     delete p;
     return ABF_ERR_CUDA;
   }
@@ -299,14 +552,16 @@ abf_status abf1d_plan_destroy(abf1d_plan p) {
   if (!p) return ABF_ERR_INVALID;
   if (p->d_table) cudaFree(p->d_table);
   if (p->d_status) cudaFree(p->d_status);
+  if (p->d_stage) cudaFree(p->d_stage);
   delete p;
   return ABF_OK;
 }
 
-abf_status abf1d_plan_query(abf1d_plan p, size_t* integrated_bytes, int32_t* right, int32_t* limbs,
+abf_status abf1d_plan_query(abf1d_plan p, size_t* integrated_bytes, int32_t* left, int32_t* right, int32_t* limbs,
                             int64_t* g_pitch_elems) {
   if (!p) return ABF_ERR_INVALID;
   if (integrated_bytes) *integrated_bytes = p->g_bytes;
+  if (left) *left = p->v.left;
   if (right) *right = p->right;
   if (limbs) *limbs = p->v.limbs;
   if (g_pitch_elems) *g_pitch_elems = p->v.Gp;
@@ -318,6 +573,16 @@ abf_status abf1d_integrate(abf1d_plan p, const void* d_f, size_t f_pitch, void* 
   const int dt = p->desc.in_dtype;
   const size_t esz = dt == ABF_U8 ? 1 : dt == ABF_U16 ? 2 : dt == ABF_F32 ? 4 : 8;
   if (f_pitch < (size_t)p->desc.length * esz || ((uintptr_t)d_g & 15)) return ABF_ERR_INVALID;
+  if (p->d_stage) {
+    const size_t esz_c = p->stage_wide ? 8 : 4;
+    if (abf::run_prefilter(p->pf, p->desc.count, dt, d_f, f_pitch, p->d_stage, p->v.Gp, p->stage_wide, p->d_status,
+                           st) != cudaSuccess)
+      return ABF_ERR_CUDA;
+    return abf::run_row_scan(p->rows, p->d_stage, (size_t)p->v.Gp * esz_c, (uint64_t*)d_g, p->d_status, st) ==
+                   cudaSuccess
+               ? ABF_OK
+               : ABF_ERR_CUDA;
+  }
   return abf::run_row_scan(p->rows, d_f, f_pitch, (uint64_t*)d_g, p->d_status, st) == cudaSuccess ? ABF_OK
                                                                                                    : ABF_ERR_CUDA;
 }
@@ -348,10 +613,10 @@ abf_status abf1d_filter_numerator(abf1d_plan p, const void* d_g, const float* d_
 
 abf_status abf1d_weight_table_host(int32_t n1, int32_t n2, int32_t q_bits, uint64_t* out, size_t out_elems,
                                    size_t* needed_elems, int32_t* K, int32_t* dmin, uint64_t* D) {
-  if (n1 < 0 || n1 > 1 || n2 < 0 || n2 > 3 || q_bits < 1 || q_bits > 10) return ABF_ERR_INVALID;
+  if (n1 < 0 || n1 > 5 || n2 < 0 || n2 > 3 || q_bits < 1 || q_bits > 10) return ABF_ERR_INVALID;
   const int N = n1 + n2 + 1, P = q_bits + 1;
-  const int dm = (N % 2) ? -(N + 1) / 2 + 1 : -N / 2;
-  const int k = (N % 2) ? N + 1 : N + 2;
+  int dm = 0, k = 0;
+  table_shape(N, &dm, &k);
   std::vector<uint64_t> tab;
   unsigned long long Dv = 0;
   try {

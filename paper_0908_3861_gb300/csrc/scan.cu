@@ -24,6 +24,8 @@
 //                bounded wait that raises ABF_DEV_TIMEOUT instead of hanging.
 #include <mutex>
 
+#include <type_traits>
+
 #include "abf_internal.cuh"
 
 namespace abf {
@@ -58,43 +60,6 @@ __device__ __forceinline__ Wide<L> warp_inclusive(Wide<L> v, int lane) {
     if (lane >= d) waddc<L>(v, o);
   }
   return v;
-}
-
-// Input element -> integer f 2^F; raises ABF_DEV_BAD_INPUT (and reads 0) when
-// a floating-point value is off the 2^-F grid or beyond the value bound
-// (bound_i = floor(value_bound 2^F)).  binary32 inputs are checked in binary32
-// (scaling by 2^F is exact, rintf is exact) and integers, keeping the per-sample
-// work off the slow binary64 pipe.
-template <typename TIn>
-__device__ __forceinline__ int64_t convert_f(TIn raw, double scale, long long bound_i, int32_t* status) {
-  if constexpr (sizeof(TIn) <= 2) {
-    return (int64_t)raw;
-  } else if constexpr (sizeof(TIn) == 4) {
-    const float v = raw * (float)scale;  // exact: scale is a power of two (inf if it overflows)
-    if (!(rintf(v) == v) || !(fabsf(v) < 4.0e18f)) {
-      raise_status(status, ABF_DEV_BAD_INPUT);
-      return 0;
-    }
-    const long long r = __float2ll_rn(v);
-    if (r > bound_i || r < -bound_i) {
-      raise_status(status, ABF_DEV_BAD_INPUT);
-      return 0;
-    }
-    return r;
-  } else {
-    const double v = (double)raw * scale;  // exact: scale is a power of two
-    const double r = rint(v);
-    if (!(r == v) || !(fabs(r) < 4.0e18)) {
-      raise_status(status, ABF_DEV_BAD_INPUT);
-      return 0;
-    }
-    const long long ri = (long long)r;
-    if (ri > bound_i || ri < -bound_i) {
-      raise_status(status, ABF_DEV_BAD_INPUT);
-      return 0;
-    }
-    return ri;
-  }
 }
 
 constexpr int kRowVec = 4;     // elements per lane per chunk
@@ -410,6 +375,8 @@ template <int L>
 static cudaError_t rows_L(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, int32_t* status,
                           cudaStream_t st) {
   switch (pv.in_dtype) {
+    case kStageI32: return launch_rows<L, int32_t>(pv, f, f_pitch, g, status, st);
+    case kStageI64: return launch_rows<L, long long>(pv, f, f_pitch, g, status, st);
     case ABF_U8: return launch_rows<L, uint8_t>(pv, f, f_pitch, g, status, st);
     case ABF_U16: return launch_rows<L, uint16_t>(pv, f, f_pitch, g, status, st);
     case ABF_F32: return launch_rows<L, float>(pv, f, f_pitch, g, status, st);

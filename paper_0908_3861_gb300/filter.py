@@ -220,7 +220,10 @@ class Server:
 
 class AdaptiveFilter1D:
     """The 1-D scale-adaptive B-spline filter of Sec. 3 on `count` signals of
-    `length` samples (abf1d_integrate + abf1d_filter)."""
+    `length` samples (abf1d_integrate + abf1d_filter).  n1 is the degree of
+    the signal model (0..5; from 2 on the samples are interpolated, c = f *
+    (b^{n1})^-1 rounded to the 2^-frac_bits grid), n2 that of the analysis
+    B-spline (0..3)."""
 
     def __init__(self, length, count, n1, n2, in_dtype, q_bits=8, frac_bits=0, max_scale=8.0, value_bound=0.0,
                  out="f64", device=None):
@@ -280,7 +283,8 @@ class AdaptiveFilter1D:
         return num
 
     def integrated(self):
-        """g as (count, pitch, limbs) int64 (a view of the buffer)."""
+        """g as (count, pitch, limbs) int64 (a view of the buffer); element i
+        holds g at signal position i - info["left"]."""
         pitch = self.info["g_pitch"]
         return self.g[: self.count * pitch * self.limbs * 8].view(torch.int64).view(self.count, pitch, self.limbs)
 

@@ -100,7 +100,7 @@ def test_plan_rejects_bad_descriptors(lib):
         _abf.abf_plan_create(d)
 
 
-@pytest.mark.parametrize("n1,n2,q", [(0, 0, 3), (1, 1, 2), (0, 2, 4), (1, 3, 3), (1, 2, 8)])
+@pytest.mark.parametrize("n1,n2,q", [(0, 0, 3), (1, 1, 2), (0, 2, 4), (1, 3, 3), (1, 2, 8), (3, 1, 8), (5, 0, 3)])
 def test_line1d_host_table_matches_oracle(n1, n2, q):
     """The 1-D B-spline table (built by the degree recurrence) against the
     oracle's truncated-power B-spline, entry by entry."""
