@@ -21,7 +21,9 @@
 // degree n from degree n-1 (two shifted copies weighted by linear factors) in
 // integers, and every row is checked to sum to D (partition of unity).
 //   S[m] = sum_j (-1)^j binom(n2+1, j) sum_d g[p_j + d] T[r_j][d]  (mod 2^(64 L))
-//   s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F)  in binary64.
+//   s[m] = S[m] 2^(Q (n2+1)) / (D A^(n2+1) 2^F)  in binary64, as S[m] times a
+//   per-plan table of the normaliser's reciprocal per integer scale A (one
+//   binary64 multiply per sample instead of a division and a power).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -44,6 +46,7 @@ struct Line1dView {
   float log2_base;   // log2(D |f|max 2^F)
   double Dd;         // D
   const uint64_t* table;  // 2^P rows x K entries
+  const double* rtab;     // R[A] = 2^(Q(n2+1) - F) / (D A^(n2+1)), A = 0..Amax, or null
 };
 
 // acc += g * w (mod 2^(64 L)) for a 64-bit table weight, as carry chains.
@@ -77,14 +80,16 @@ __global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const u
   const int row = blockIdx.y;
   if (m >= v.length) return;
   const float av = reinterpret_cast<const float*>(reinterpret_cast<const char*>(a) + (size_t)row * a_pitch)[m];
-  const double q = ldexp(1.0, v.Q);
-  const double x = (double)av * q;  // exact (power of two)
+  // a 2^Q is exact in binary32 (a power-of-two scaling), so its rint there is
+  // the binary64 rint of the same value; this keeps the per-sample work off
+  // the binary64 pipe, a thirty-second of the integer rate on GB300
+  const float x = av * (float)(1 << v.Q);
   int ok = 1;
   long long A = 0;
-  if (!(x > 0.0) || !(x < 2147483648.0)) {
+  if (!(x > 0.0f) || !(x < 2147483648.0f)) {
     ok = 0;
   } else {
-    A = __double2ll_rn(x);
+    A = __float2ll_rn(x);
     if (A < 1 || A > v.Amax) ok = 0;
   }
   if (ok) {
@@ -131,10 +136,15 @@ __global__ void __launch_bounds__(256) mesh1d_kernel(const Line1dView v, const u
     for (int i = 0; i < L; ++i) q8[i] = acc.w[i];
   }
   if (s) {
-    double den = v.Dd;
+    double val;
+    if (v.rtab) {
+      val = wto_double<L>(acc) * __ldg(v.rtab + A);  // R[A] = 2^(Q(n2+1) - F) / (D A^(n2+1))
+    } else {
+      double den = v.Dd;
 #pragma unroll
-    for (int e = 0; e < N2 + 1; ++e) den *= (double)A;
-    const double val = ldexp(wto_double<L>(acc), v.Q * (N2 + 1) - v.F) / den;
+      for (int e = 0; e < N2 + 1; ++e) den *= (double)A;
+      val = ldexp(wto_double<L>(acc), v.Q * (N2 + 1) - v.F) / den;
+    }
     char* srow = reinterpret_cast<char*>(s) + (size_t)row * s_pitch;
     if (f64) reinterpret_cast<double*>(srow)[m] = val;
     else reinterpret_cast<float*>(srow)[m] = (float)val;
@@ -213,21 +223,21 @@ struct PrefilterView {
 __device__ __forceinline__ int pf_pad(int j) { return j + (j >> 5); }
 
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(kPfThreads) prefilter_kernel(const PrefilterView v, const TIn* __restrict__ f,
-                                                               size_t f_pitch, TOut* __restrict__ c,
-                                                               long long c_pitch, int32_t* status) {
-  __shared__ long long sx[kPfSmem];
+__global__ void __launch_bounds__(kPfThreads, 3) prefilter_kernel(const PrefilterView v, const TIn* __restrict__ f,
+                                                                  size_t f_pitch, TOut* __restrict__ c,
+                                                                  long long c_pitch, int32_t* status) {
+  __shared__ long long sx[kPfSmem];  // x 2^G
   const int row = blockIdx.y;
   const long long i0 = (long long)blockIdx.x * kPfTile;  // first output (g index; k = i - left)
   const TIn* frow = reinterpret_cast<const TIn*>(reinterpret_cast<const char*>(f) + (size_t)row * f_pitch);
+  const long long one = 1ll << v.G;
   for (int j = threadIdx.x; j < kPfStage; j += kPfThreads) {
     const long long k = i0 - kPfHalo + j - v.left;
     long long xv = 0;
     if (k >= 0 && k < v.length) xv = convert_f<TIn>(frow[k], v.scale, v.bound, status);
-    sx[pf_pad(j)] = xv;
+    sx[pf_pad(j)] = xv * one;
   }
   __syncthreads();
-  const long long one = 1ll << v.G;
   long long acc[kPfSeg];  // c 2^F in units of 2^-(G-4)
 #pragma unroll
   for (int e = 0; e < kPfSeg; ++e) acc[e] = 0;
@@ -237,20 +247,20 @@ __global__ void __launch_bounds__(kPfThreads) prefilter_kernel(const PrefilterVi
     if (p >= v.npoles) break;
     const long long Z = v.Z[p], A = v.A[p];
     const int W = v.W[p];
-    long long y = 0;
-    for (int j = jb - W; j < jb; ++j) y = sx[pf_pad(j)] * one + __mul64hi(y, Z);
-#pragma unroll
-    for (int e = 0; e < kPfSeg; ++e) {
-      const long long xs = sx[pf_pad(jb + e)] * one;
-      y = xs + __mul64hi(y, Z);
-      acc[e] += __mul64hi(y - xs, A);
+    // the causal and the anti-causal recursion advance together: two
+    // independent dependency chains per thread
+    long long yf = 0, yb = 0;
+    for (int i = 0; i < W; ++i) {
+      yf = sx[pf_pad(jb - W + i)] + __mul64hi(yf, Z);
+      yb = sx[pf_pad(jb + kPfSeg - 1 + W - i)] + __mul64hi(yb, Z);
     }
-    y = 0;
-    for (int j = jb + kPfSeg - 1 + W; j >= jb + kPfSeg; --j) y = sx[pf_pad(j)] * one + __mul64hi(y, Z);
 #pragma unroll
-    for (int e = kPfSeg - 1; e >= 0; --e) {
-      y = sx[pf_pad(jb + e)] * one + __mul64hi(y, Z);
-      acc[e] += __mul64hi(y, A);
+    for (int i = 0; i < kPfSeg; ++i) {
+      const long long xf = sx[pf_pad(jb + i)];
+      yf = xf + __mul64hi(yf, Z);
+      acc[i] += __mul64hi(yf - xf, A);
+      yb = sx[pf_pad(jb + kPfSeg - 1 - i)] + __mul64hi(yb, Z);
+      acc[kPfSeg - 1 - i] += __mul64hi(yb, A);
     }
   }
   __syncthreads();  // every thread is done with x
@@ -399,6 +409,7 @@ struct abf1d_plan_s {
   uint64_t* d_table = nullptr;
   int32_t* d_status = nullptr;
   void* d_stage = nullptr;   // n1 >= 2: c_q per row (int32 or int64, g's pitch)
+  double* d_rtab = nullptr;  // normalisation per integer scale
   bool stage_wide = false;
   size_t g_bytes = 0;
   int right = 0;
@@ -544,6 +555,28 @@ abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
     return ABF_ERR_CUDA;
   }
   v.table = p->d_table;
+  v.rtab = nullptr;
+  if (Amax <= (1 << 22)) {
+    // the normalisation per integer scale, in the kernel's former operation order
+    std::vector<double> rt((size_t)Amax + 1, 0.0);
+    const double e2 = std::ldexp(1.0, d->q_bits * (d->n2 + 1) - d->in_frac_bits);
+    for (int A = 1; A <= Amax; ++A) {
+      double den = (double)D;
+      for (int e = 0; e < d->n2 + 1; ++e) den *= (double)A;
+      rt[(size_t)A] = e2 / den;
+    }
+    double* d_rt = nullptr;
+    if (cudaMalloc(&d_rt, rt.size() * sizeof(double)) != cudaSuccess) {
+      abf1d_plan_destroy(p);
+      return ABF_ERR_OOM;
+    }
+    p->d_rtab = d_rt;
+    if (cudaMemcpy(d_rt, rt.data(), rt.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+      abf1d_plan_destroy(p);
+      return ABF_ERR_CUDA;
+    }
+    v.rtab = d_rt;
+  }
   *out = p;
   return ABF_OK;
 }
@@ -553,6 +586,7 @@ abf_status abf1d_plan_destroy(abf1d_plan p) {
   if (p->d_table) cudaFree(p->d_table);
   if (p->d_status) cudaFree(p->d_status);
   if (p->d_stage) cudaFree(p->d_stage);
+  if (p->d_rtab) cudaFree(p->d_rtab);
   delete p;
   return ABF_OK;
 }
