@@ -688,7 +688,8 @@ __device__ __forceinline__ int64_t convert_f(TIn raw, double scale, long long bo
       raise_status(status, ABF_DEV_BAD_INPUT);
       return 0;
     }
-    const long long r = __float2ll_rn(v);
+    // a 32-bit conversion where it fits: the 64-bit one issues on the binary64 pipe
+    const long long r = fabsf(v) < 2147483648.0f ? (long long)__float2int_rn(v) : __float2ll_rn(v);
     if (r > bound_i || r < -bound_i) {
       raise_status(status, ABF_DEV_BAD_INPUT);
       return 0;
