@@ -338,6 +338,22 @@ def run_ours(args):
                                              "once per line direction: |f| + 7 |g| per integrate"},
         "clocks": clk,
     }
+    hbm = peaks.get("hbm_gbs")
+    if hbm:
+        # whole step against its bounds, the kernels in sequence: the integrate at
+        # the copy peak for its algorithmic bytes, then the mesh at the larger of
+        # its ALU time (derived peak) and its HBM time (scales, g once, output)
+        t_integ = integ_bytes / (hbm * 1e9) * 1e3
+        t_alu = macs / peak_macs * 1e3
+        t_mesh_hbm = pix * (16.0 + 8.0 * L + out_exact.element_size()) / (hbm * 1e9) * 1e3
+        lower = t_integ + max(t_alu, t_mesh_hbm)
+        line["roofline_path"] = {
+            "lower_bound_ms": round(lower, 4), "achieved_ms": round(total_ms / K, 4),
+            "frac": round(lower / (total_ms / K), 4),
+            "parts_ms": {"integrate_hbm": round(t_integ, 4), "mesh_alu": round(t_alu, 4),
+                         "mesh_hbm": round(t_mesh_hbm, 4)},
+            "note": "integrate bytes / measured copy peak + max(mesh MACs / derived ALU peak, "
+                    "mesh bytes / measured copy peak)"}
     if rank == 0 and args.cpu_baseline:
         cb, pts, vals = cpu_baseline(w, seconds=args.cpu_seconds, keep=True)
         line["cpu_baseline"] = cb
