@@ -356,6 +356,14 @@ def run_ours(args):
                     "mesh bytes / measured copy peak)"}
     if rank == 0 and args.cpu_baseline:
         cb, pts, vals = cpu_baseline(w, seconds=args.cpu_seconds, keep=True)
+        try:
+            done, el, procs = cpu_baseline_all_cores(args.workload, _shape(args), args.cpu_seconds)
+            cb = {"value": done / el / 1e6, "unit": UNIT, "cores": procs, "kind": "oracle",
+                  "sample": "%d random pixels of the same workload, exact per-pixel evaluation, one process per "
+                            "host core for %.1f s; single core: %s" % (done, el, cb["sample"]),
+                  "single_core_value": cb["value"]}
+        except Exception as e:  # keep the single-core figure if a pool cannot start here
+            cb["all_cores_error"] = str(e)[:200]
         line["cpu_baseline"] = cb
         for k, v in forms.items():
             v["err_range_vs_oracle"] = err_range(v["out"], pts, vals, img)
@@ -771,6 +779,40 @@ def cpu_baseline(w, seconds=15.0, sample=None, keep=False):
     if keep:
         return out, pts, vals
     return out
+
+
+def _oracle_sample_worker(job):
+    """One host core: the oracle as it stands on random pixels of the workload
+    (regenerated from its seed), for `seconds` after its own setup."""
+    name, shape, seed, seconds = job
+    from oracle import paper, scales as osc
+    w = _workload(name, 0, shape)
+    img, sc = w["image"], w["scales"]
+    H, W = img.shape
+    fi = (img.astype(np.float64) * float(1 << w["frac_bits"])).astype(np.int64)
+    C = osc.scales_to_C(w["scale_kind"], sc, w["n"], w["q_bits"], w["cmax"])
+    rng = np.random.default_rng(seed)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        p = (int(rng.integers(0, W)), int(rng.integers(0, H)))
+        paper.filter_pixels(fi, C, w["n"], w["q_bits"], w["frac_bits"], [p])
+        done += 1
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(name, shape, seconds, procs=None):
+    """The same oracle sample on every host core at once (one process per core,
+    started with spawn: the parent holds a CUDA context).  Returns (pixels,
+    seconds of the slowest worker's timed loop, processes)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    procs = procs or os.cpu_count() or 1
+    jobs = [(name, shape, 1000 + i, seconds) for i in range(procs)]
+    # an executor, not a Pool: a worker that cannot start raises instead of
+    # being restarted forever
+    with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_sample_worker, jobs, timeout=seconds + 300.0))
+    return sum(d for d, _ in res), max(t for _, t in res), procs
 
 
 def err_range(out, pts, vals, img):
