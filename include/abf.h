@@ -95,16 +95,23 @@ typedef struct {
 
 typedef struct abf_plan_s* abf_plan;
 
-/* Create a plan (host work + one upload of the ZP^{*n} weight table, which is
- * shared by all plans with the same n and grid).  The plan fixes the lattice
+/* Create a plan for the problem of Sec. 6 (s[m] = <f, beta_{a(m)}(. - m)> for
+ * a given per-pixel scale map) with the four-direction box spline of Sec. 7,
+ * phi = delta (Sec. 7 (1)) and order n (each directional box n-fold): host
+ * work + one upload of the ZP^{*n} weight table, which is shared by all plans
+ * with the same n and grid.  The plan fixes the lattice
  * box of the integrated image: [-left, W + right) x [0, H + above) in image
  * coordinates (rows below the image are all zero and are not stored).
  * Errors: ABF_ERR_INVALID (descriptor), ABF_ERR_RANGE (exact form: the
  * numerator bound needs more than 4 limbs), ABF_ERR_CUDA / ABF_ERR_OOM.      */
 abf_status abf_plan_create(const abf_desc* desc, abf_plan* out);
+/* Free the plan's own memory (the plan and its device status word); the
+ * weight tables, shared by plans, stay with the library until the process
+ * exits, and caller buffers are never touched.  ABF_ERR_INVALID for NULL.    */
 abf_status abf_plan_destroy(abf_plan plan);
 
-/* Sizes the caller allocates: the integrated image (exact form; 0 otherwise)
+/* Sizes the caller allocates (the lattice box of the non-adaptive step of
+ * Sec. 7 (1)): the integrated image (exact form; 0 otherwise)
  * and the scratch workspace; the margins (left, right, below, above) of the
  * integrated lattice box; the number of 64-bit limbs L (exact form) and the
  * row pitch of the integrated image in elements (each element L * 8 bytes).
@@ -166,7 +173,8 @@ abf_status abf_filter(abf_plan plan, const void* d_src, size_t src_pitch, const 
                       size_t scale_pitch, void* d_s, size_t s_pitch, void* d_ws,
                       cudaStream_t stream);
 
-/* Exact form only: the integer numerators S[m] = D sum_j w_j g_I(y_j)
+/* Exact form only: the numerator of Eq. (final_eqn) before the normaliser,
+ * as integers S[m] = D sum_j w_j g_I(y_j)
  * (L uint64 limbs per pixel, two's complement modulo 2^(64 L)), row pitch in
  * bytes.  s[m] = S[m] 2^(4 Q n) / (D (C1 C2 C3 C4)^n 2^F).                    */
 abf_status abf_filter_numerator(abf_plan plan, const void* d_g, const void* d_scales,
@@ -217,7 +225,8 @@ abf_status abf_batch_autotune(const abf_job* jobs, int32_t njobs, void* d_ws, si
                               int32_t* warps_out, float* ms3);
 
 /* ------------------------------------------------------------------ serving
- * A request loop for filter jobs (image + per-pixel scale field, host memory)
+ * No counterpart in the paper: a serving interface around its two steps
+ * (Sec. 6, (1) non-adaptive and (2) adaptive).  A request loop for filter jobs (image + per-pixel scale field, host memory)
  * on one GPU.  A worker thread admits queued jobs in arrival order as long as
  * a slot (a CUDA stream) is free and the job's device footprint (image,
  * scales, output, integrated image, workspace) fits the HBM budget; later
@@ -275,11 +284,16 @@ abf_status abf_server_stats(abf_server srv, size_t* used, size_t* peak, int32_t*
 abf_status abf_server_destroy(abf_server srv);
 
 /* The per-pixel integer steps C_k = rint(c_k 2^Q) (int32 x4 per pixel) that
- * abf_filter uses, for inspection and reuse.                                 */
+ * abf_filter uses, for inspection and reuse: the scale reading of Sec. 7
+ * (c2 = a2 / sqrt2, c4 = a4 / sqrt2, the a'_j of Table "Mesh Vertices") or the
+ * ellipse moment rule (a reading; its isotropic case is Theorem (convergence)
+ * of Sec. 4).  d_C: H rows of W int4, row pitch C_pitch bytes.  Invalid pixels
+ * get zeros and set the device status.                                       */
 abf_status abf_prepare_scales(abf_plan plan, const void* d_scales, size_t scale_pitch,
                               void* d_C, size_t C_pitch, cudaStream_t stream);
 
-/* Measure a scale field before planning: the largest step max_k c_k and the
+/* Measure a scale field before planning (no counterpart in the paper: the
+ * bounds that size a plan's limbs): the largest step max_k c_k and the
  * largest product c1 c2 c3 c4 over the image, after rounding to the 2^-Q grid
  * (desc supplies width, height, order_n, scale_kind, q_bits and max_scale, the
  * clamp of the ellipse rule).  Synchronises `stream`.  Returns
@@ -288,12 +302,13 @@ abf_status abf_prepare_scales(abf_plan plan, const void* d_scales, size_t scale_
 abf_status abf_measure_scales(const abf_desc* desc, const void* d_scales, size_t scale_pitch,
                               double* max_step, double* max_product, cudaStream_t stream);
 
-/* The common denominator D of the integer ZP^{*n} weights of this plan, as
- * four 32-bit words (little-endian, D < 2^128).                              */
+/* The common denominator D of the integer ZP^{*n} weights of this plan (the
+ * interpolation weights of Eq. (final_eqn) are D times the kernel's values on
+ * the 2^-P grid), as four 32-bit words (little-endian, D < 2^128).          */
 abf_status abf_plan_denominator(abf_plan plan, uint32_t* d_words4);
 
-/* Read and clear the plan's device status word (synchronises the device).
- * code = 0 or an OR of ABF_DEV_* bits.                                        */
+/* Read and clear the plan's device status word (synchronises the device; no
+ * counterpart in the paper).  code = 0 or an OR of ABF_DEV_* bits.           */
 #define ABF_DEV_BAD_SCALE   1   /* a scale was non-finite, non-positive or out of bounds */
 #define ABF_DEV_RANGE       2   /* a pixel's numerator bound exceeded 64 L - 1 bits       */
 #define ABF_DEV_TIMEOUT     4   /* a bounded wait (scan look-back) ran out                 */
@@ -302,8 +317,9 @@ abf_status abf_last_device_status(abf_plan plan, int32_t* code);
 
 const char* abf_status_str(abf_status s);
 
-/* Host-only: generate the ZP^{*n} weight table for order n and grid 2^-Q (the
- * table abf_plan_create uploads) into a caller buffer, without touching a
+/* Host-only: generate the ZP^{*n} weight table (the interpolation kernel of
+ * Eq. (final_eqn): the ZP element of Sec. 7, n-fold self-convolved) for order
+ * n and grid 2^-Q (the table abf_plan_create uploads) into a caller buffer, without touching a
  * device.  Layout: (2^P)^2 rows, row index ry 2^P + rx (P = Q for even n,
  * Q + 1 for odd n; fractional offset r = (rx, ry) 2^-P, minus 1/2 for odd n).
  * Row entries: D ZP^{*n}(r - d) for the lattice neighbours d that can carry a
@@ -383,7 +399,8 @@ typedef struct abf1d_plan_s* abf1d_plan;
 abf_status abf1d_plan_create(const abf1d_desc* desc, abf1d_plan* out);
 abf_status abf1d_plan_destroy(abf1d_plan plan);
 
-/* integrated_bytes: size of the integrated signals g (count rows of
+/* Sizes of the Proposition's step 1 output.
+ * integrated_bytes: size of the integrated signals g (count rows of
  * g_pitch_elems elements of L uint64 limbs; element i holds g at signal
  * position i - left); left: samples before the signal start that g holds (0
  * for n1 <= 1); right: samples past the signal end that g holds (the adaptive
@@ -391,30 +408,36 @@ abf_status abf1d_plan_destroy(abf1d_plan plan);
 abf_status abf1d_plan_query(abf1d_plan plan, size_t* integrated_bytes, int32_t* left, int32_t* right,
                             int32_t* limbs, int64_t* g_pitch_elems);
 
-/* Non-adaptive step: g = u_1^{(n2+1)} * (c 2^F) per row, exact modulo
+/* Non-adaptive step (Proposition "prop", step 1, Sec. 3):
+ * g = u_1^{(n2+1)} * (c 2^F) per row, exact modulo
  * 2^(64 L) (c = f for n1 <= 1; the prefiltered c_q for n1 >= 2).  d_f: count
  * rows of length in_dtype elements (row pitch in bytes); d_g: plan-sized,
  * 16-byte aligned.  Off-grid or out-of-bound float inputs read as 0 and set
  * ABF_DEV_BAD_INPUT.  Launches: the prefilter (n1 >= 2), then the row pass.  */
 abf_status abf1d_integrate(abf1d_plan plan, const void* d_f, size_t f_pitch, void* d_g, cudaStream_t stream);
 
-/* Adaptive step: d_a holds one float32 scale a per sample (count rows, row
+/* Adaptive step (Proposition "prop", step 2, Sec. 3: the FIR localisation
+ * mask Delta_a^{n2+1} beta^{n1+n2+1}(k + tau)): d_a holds one float32 scale a
+ * per sample (count rows, row
  * pitch in bytes); d_s receives s (out_dtype).  Samples whose scale is
  * invalid (non-finite, A < 1 or A > rint(max_scale 2^Q)) or whose numerator
  * bound exceeds the limbs get NaN and set the device status.                 */
 abf_status abf1d_filter(abf1d_plan plan, const void* d_g, const float* d_a, size_t a_pitch, void* d_s,
                         size_t s_pitch, cudaStream_t stream);
 
-/* The integer numerators S[m] (L little-endian uint64 limbs per sample, two's
+/* Step 2 before the normaliser a^-(n2+1): the integer numerators S[m] (L
+ * little-endian uint64 limbs per sample, two's
  * complement modulo 2^(64 L)), for bit-exact checks.                         */
 abf_status abf1d_filter_numerator(abf1d_plan plan, const void* d_g, const float* d_a, size_t a_pitch,
                                   void* d_num, size_t num_pitch, cudaStream_t stream);
 
-/* Device status bits (ABF_DEV_*) of the plan's launches since the last read;
+/* Device status bits (ABF_DEV_*; no counterpart in the paper) of the plan's
+ * launches since the last read;
  * synchronises the device, then clears the word.                             */
 abf_status abf1d_last_device_status(abf1d_plan plan, int32_t* code);
 
-/* Host-only: the B-spline weight table abf1d_plan_create uploads, without
+/* Host-only: the B-spline weight table abf1d_plan_create uploads (the
+ * interpolation by beta^N of the Proposition's step 2, Sec. 3), without
  * touching a device.  2^(Q+1) rows (r = R 2^-(Q+1) in [0, 1)) of *K entries
  * D beta^N(r - d), d = *dmin .. *dmin + *K - 1, N = n1 + n2 + 1,
  * D = N! 2^(N (Q+1)).  With out = NULL only the sizes and D are returned.   */
