@@ -15,7 +15,9 @@
 //
 // Kernels:
 //   row_scan   : one CTA per row, its warps on contiguous segments; input
-//                conversion (a0) fused, all n folds of v1 together (lane-local
+//                conversion (a0) fused (the 1-D filter's prefiltered models pass
+//                integer coefficients staged by its prefilter instead), all n
+//                folds of v1 together (lane-local
 //                scans + warp shuffles, a running state per fold); segment
 //                states composed through shared memory (affine carries).
 //   line_scan  : v2 / v3 / v4, one thread per line (sheared so that a warp reads
@@ -23,7 +25,6 @@
 //                are chained by decoupled look-back on per-line flags, with a
 //                bounded wait that raises ABF_DEV_TIMEOUT instead of hanging.
 #include <mutex>
-
 #include <type_traits>
 
 #include "abf_internal.cuh"
