@@ -444,6 +444,14 @@ abf_status abf1d_last_device_status(abf1d_plan plan, int32_t* code);
 abf_status abf1d_weight_table_host(int32_t n1, int32_t n2, int32_t q_bits, uint64_t* out, size_t out_elems,
                                    size_t* needed_elems, int32_t* K, int32_t* dmin, uint64_t* D);
 
+/* Host-only: the constants of the interpolation prefilter c = f * (b^{n1})^-1
+ * (Sec. 3) that abf1d_plan_create derives for n1 in 2..5: the inverse of the
+ * B-spline interpolation filter as h[k] = sum_p A_p z_p^|k| over *npoles
+ * (1 or 2) poles z_p in (-1, 0), binary64; z and A: caller arrays of 2.
+ * *hnorm (optional): sum_p |A_p| (1 + |z_p|) / (1 - |z_p|), a bound on the
+ * l1 norm of h.  ABF_ERR_INVALID outside 2..5 or for NULL arrays.           */
+abf_status abf1d_prefilter_host(int32_t n1, int32_t* npoles, double* z, double* A, double* hnorm);
+
 /* Test hook for the failure path of the scans (no counterpart in the paper):
  * runs one line pass (direction v3) of the non-adaptive step with the CTAs of
  * its first band skipped, so the next band's look-back waits on flags that

@@ -110,6 +110,7 @@ def lib():
         "abf1d_filter": ([vp, vp, vp, sz, vp, sz, vp], st),
         "abf1d_filter_numerator": ([vp, vp, vp, sz, vp, sz, vp], st),
         "abf1d_last_device_status": ([vp, P(i32)], st),
+        "abf1d_prefilter_host": ([i32, P(i32), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)], st),
         "abf1d_weight_table_host": ([i32, i32, i32, P(ctypes.c_uint64), sz, P(sz), P(i32), P(i32),
                                      P(ctypes.c_uint64)], st),
         "abf_ellipse_ws_bytes": ([i32, i32], sz),
@@ -341,6 +342,14 @@ def abf_batch_autotune(jobs, ws, stream=None):
     _check(lib().abf_batch_autotune(arr, len(jobs), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
                                     ctypes.byref(w), ms), "abf_batch_autotune")
     return w.value, list(ms)
+
+
+def abf1d_prefilter_host(n1):
+    """(z, A, hnorm): poles and weights of the inverse interpolation filter."""
+    npoles = ctypes.c_int32()
+    z, A, hn = (ctypes.c_double * 2)(), (ctypes.c_double * 2)(), ctypes.c_double()
+    _check(lib().abf1d_prefilter_host(n1, ctypes.byref(npoles), z, A, ctypes.byref(hn)), "abf1d_prefilter_host")
+    return list(z[: npoles.value]), list(A[: npoles.value]), hn.value
 
 
 def abf1d_weight_table_host(n1, n2, q_bits):

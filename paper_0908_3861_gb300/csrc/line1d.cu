@@ -669,6 +669,19 @@ abf_status abf1d_weight_table_host(int32_t n1, int32_t n2, int32_t q_bits, uint6
   return ABF_OK;
 }
 
+abf_status abf1d_prefilter_host(int32_t n1, int32_t* npoles, double* z, double* A, double* hnorm) {
+  if (n1 < 2 || n1 > 5 || !npoles || !z || !A) return ABF_ERR_INVALID;
+  PoleSet ps{};
+  if (!interp_poles(n1, ps)) return ABF_ERR_UNSUPPORTED;
+  *npoles = ps.M;
+  for (int p = 0; p < ps.M; ++p) {
+    z[p] = ps.z[p];
+    A[p] = ps.A[p];
+  }
+  if (hnorm) *hnorm = ps.hnorm;
+  return ABF_OK;
+}
+
 abf_status abf1d_last_device_status(abf1d_plan p, int32_t* code) {
   if (!p || !code) return ABF_ERR_INVALID;
   if (cudaDeviceSynchronize() != cudaSuccess) return ABF_ERR_CUDA;

@@ -114,3 +114,23 @@ def test_line1d_host_table_matches_oracle(n1, n2, q):
         ref = [o.dbspline_int(N, P, R - ((dmin + c) << P)) for c in range(len(row))]
         assert row == ref, R
         assert sum(row) == D
+
+
+@pytest.mark.parametrize("n1", [2, 3, 4, 5])
+def test_line1d_prefilter_constants_match_the_oracle_inverse(n1):
+    """The poles and weights the 1-D plan derives for the interpolation
+    prefilter (partial fractions of the B-spline filter's symbol, binary64)
+    against the oracle's inverse from its definition (exact banded solve)."""
+    from oracle import line1d as o
+    from paper_0908_3861_gb300 import _abf
+    z, A, hnorm = _abf.abf1d_prefilter_host(n1)
+    assert len(z) == n1 // 2 and all(-1.0 < p < 0.0 for p in z)
+    h = o.inverse_filter(n1)
+    h0 = float(h[0])
+    for k in range(0, 25):
+        got = sum(a * p ** k for a, p in zip(A, z))
+        assert abs(got - float(h[k])) <= 4e-16 * abs(h0) * (k + 1), k
+    l1 = sum(abs(float(h[k])) for k in range(-60, 61))
+    assert l1 <= hnorm * (1 + 1e-12)
+    with pytest.raises(_abf.AbfError):
+        _abf.abf1d_prefilter_host(6)
