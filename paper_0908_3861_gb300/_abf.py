@@ -69,17 +69,11 @@ class abf_job_stats(ctypes.Structure):
 _lib = None
 
 
-def lib():
-    """The loaded libabf (raises if it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError("libabf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
-    L = ctypes.CDLL(LIB_PATH)
+def signatures():
+    """name -> (argtypes, restype) of every C entry point (include/abf.h)."""
     vp, sz, i32, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int
     P = ctypes.POINTER
-    sigs = {
+    return {
         "abf_plan_create": ([P(abf_desc), P(vp)], st),
         "abf_plan_destroy": ([vp], st),
         "abf_plan_query": ([vp, P(sz), P(sz), P(i32), P(i32), P(ctypes.c_int64)], st),
@@ -120,6 +114,17 @@ def lib():
         "abf_status_str": ([st], ctypes.c_char_p),
         "abf_version": ([], i32),
     }
+
+
+def lib():
+    """The loaded libabf (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libabf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    sigs = signatures()
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
         fn.argtypes = args

@@ -134,3 +134,37 @@ def test_line1d_prefilter_constants_match_the_oracle_inverse(n1):
     assert l1 <= hnorm * (1 + 1e-12)
     with pytest.raises(_abf.AbfError):
         _abf.abf1d_prefilter_host(6)
+
+
+def _c_kind(param):
+    p = " ".join(param.replace("const", " ").split())
+    if "*" in p or p.split()[0] in ("abf_plan", "abf1d_plan", "abf_server", "cudaStream_t"):
+        return "ptr"
+    t = p.split()[0]
+    return {"double": "f64", "float": "f32", "size_t": "u64", "uint64_t": "u64", "int64_t": "i64",
+            "int32_t": "i32", "uint32_t": "i32", "abf_dtype": "i32", "abf_status": "i32", "int": "i32"}[t]
+
+
+def _ctypes_kind(t):
+    import ctypes
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and not isinstance(t._type_, str):
+        return "ptr"
+    return {ctypes.c_double: "f64", ctypes.c_float: "f32", ctypes.c_size_t: "u64", ctypes.c_uint64: "u64",
+            ctypes.c_int64: "i64", ctypes.c_int32: "i32", ctypes.c_uint32: "i32", ctypes.c_int: "i32"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point's parameter list in include/abf.h against the ctypes
+    argtypes the binding installs: same count, same kinds (pointer, integer
+    width, floating type), so the two cannot drift apart silently."""
+    from paper_0908_3861_gb300 import _abf
+    src = open(os.path.join(ROOT, "include", "abf.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    decls = dict(re.findall(r"\b(abf(?:1d)?_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src))
+    sigs = _abf.signatures()
+    assert set(sigs) == set(decls)
+    for name, params in decls.items():
+        plist = [q.strip() for q in params.split(",") if q.strip() and q.strip() != "void"]
+        args, _ = sigs[name]
+        assert len(args) == len(plist), name
+        assert [_c_kind(q) for q in plist] == [_ctypes_kind(a) for a in args], name
