@@ -25,7 +25,9 @@ Unser, "Fast adaptive elliptical filtering using box splines"):
   (Proposition "prop"): B-splines and their dilates (Sec. 2), the projection
   s[m] = <f, beta_a^{n2}(. - m)> from its definition by exact piecewise
   integration, and the Proposition's two steps (running sums, then the FD
-  mask with B-spline interpolation) in exact integers.
+  mask with B-spline interpolation) in exact integers; for model degrees
+  n1 >= 2 the interpolation prefilter c = f * (b^{n1})^-1, its inverse taken
+  from the definition (an exact banded solve of b * h = delta).
 * ``structure``  -- scale-map estimation (the paper defers it, Sec. 8): a
   reading, the structure tensor of the image turned into an edge-following
   ellipse per pixel (binary64).
