@@ -166,7 +166,7 @@ def replica_throughput(pixels_per_rank, steps, world, total_ms):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_0908_3861_gb300 import _abf, AdaptiveFilter
+    from paper_0908_3861_gb300 import AdaptiveFilter, ellipse_product_bound
     import __graft_entry__
 
     world, rank, local = _dist()
@@ -184,11 +184,10 @@ def run_ours(args):
     n = w["n"]
     f_t = _host_tensor(img).to(dev)
     s_t = torch.from_numpy(sc.astype(np.float32)).to(dev)
-    d = _abf.abf_desc()
-    d.width, d.height, d.order_n = W, H, n
-    d.scale_kind = _abf.SCALE_KINDS[w["scale_kind"]]
-    d.q_bits, d.max_scale = w["q_bits"], w["cmax"]
-    _, max_prod = _abf.abf_measure_scales(d, s_t, W * 16)
+    # the plan's scale-product bound comes from the workload's parameter range
+    # (sigma <= 24, elongation <= 6), not from this image's field
+    max_prod = (ellipse_product_bound(w["sigma_max"], w["e_max"], n, w["q_bits"], w["cmax"], device=dev)
+                if w["scale_kind"] == "ellipse" else 0.0)
     tin = {np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64,
            np.dtype(np.uint8): torch.uint8, np.dtype(np.uint16): torch.uint16}[img.dtype]
     filt = AdaptiveFilter(W, H, n, tin, scale_kind=w["scale_kind"], q_bits=w["q_bits"], frac_bits=w["frac_bits"],
@@ -371,6 +370,8 @@ def run_ours(args):
     for v in forms.values():
         v.pop("out", None)
     line["forms"] = forms
+    if rank == 0 and args.serving and world == 1:
+        line["serving"] = serving_leg(dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     filt.close()
@@ -667,86 +668,178 @@ def run_scale_map(args):
     filt.close()
 
 
-def run_serve(args):
-    """Poisson-arrival stream of filter jobs (sides U{256..4096}, n U{1,2},
-    float32 images on the 2^-16 grid with ellipse fields as the 2048^2 case)
-    through the library's request loop, admitted by device-memory footprint
-    (budget: half the free HBM).  Measures the saturation rate, then p50/p99
-    latency (done - arrival) at 0.5, 0.8 and 0.95 of it; and the same stream
-    at 0.8 of it through a one-job-at-a-time server."""
+def run_constant_cost(args):
+    """Sec. 7 states that the cost per output pixel does not depend on the
+    scale vector.  Mesh time per Mpixel for spatially constant steps
+    c1 = c2 = c3 = c4 = c in {1, 4, 16, 64} on the 2048^2 image of the order-2
+    recipe, orders 1 and 2, one plan per order (max_scale 64, so the limb
+    count is the same for every c), CUDA events on the launching stream."""
     import torch
     import synthetic
-    from paper_0908_3861_gb300 import _abf, Server, make_desc
+    from paper_0908_3861_gb300 import AdaptiveFilter
     import __graft_entry__
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     __graft_entry__.build()
+    shp = _shape(args) or (2048, 2048)
+    w = synthetic.workload("c2", shape=shp)
+    img = w["image"]
+    H, W = img.shape
+    f_t = torch.from_numpy(img).to(dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+    launches = 0
+    with ClockSampler(local) as clk:
+        for n in (1, 2):
+            filt = AdaptiveFilter(W, H, n, torch.float32, scale_kind="c4", q_bits=8, frac_bits=16, max_scale=64.0,
+                                  out="f32", value_bound=255.0, device=dev)
+            filt.integrate(f_t)
+            per = {}
+            for c in (1.0, 4.0, 16.0, 64.0):
+                sc = torch.full((H, W, 4), c, dtype=torch.float32, device=dev)
+                for _ in range(args.warmup):
+                    filt.filter(sc, out)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(args.steps):
+                    filt.filter(sc, out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                launches += args.steps
+                ms = a.elapsed_time(b) / args.steps
+                per[str(int(c))] = {"mesh_ms": round(ms, 4), "ms_per_mpixel": round(ms / (H * W / 1e6), 5)}
+            assert filt.device_status() == 0
+            vals = [v["ms_per_mpixel"] for v in per.values()]
+            rows["n%d" % n] = {"limbs": filt.limbs, "by_step": per,
+                               "max_over_min": round(max(vals) / min(vals), 3)}
+            filt.close()
+    base = rows["n2"]["by_step"]["1"]["mesh_ms"]
+    line = {"metric": "mesh ms per Mpixel vs constant step c (Sec. 7: cost independent of the scales)",
+            "value": rows["n2"]["max_over_min"], "unit": "max/min ms per Mpixel over c in {1,4,16,64}, order 2",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": base,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64 limbs",
+            "data": "synthetic",
+            "config": {"workload": "%dx%d f32 image of the order-2 recipe, constant steps c1=c2=c3=c4=c, exact form, "
+                                   "Q=8, max_scale 64" % (H, W), "l2": "inputs larger than L2"},
+            "gpu_launches": launches, "orders": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def _serve_pool(npool, inflight, dev, rank=0):
+    """Distinct jobs of the serving recipe: sides U{256..4096}, float32 images
+    on the 2^-16 grid (smooth field + edges), ellipse fields as the 2048^2
+    order-2 workload; one descriptor per order n in {1, 2}, whose scale-product
+    bound comes from the recipe's parameter range (sigma <= 24, elongation <= 6)."""
+    import torch
+    import synthetic
+    from paper_0908_3861_gb300 import make_desc, ellipse_product_bound
     rng = np.random.default_rng(synthetic.SEED_BASE + 4 + 97 * rank)
+    prods = {n: ellipse_product_bound(24.0, 6.0, n, 8, 150.0, device=dev) for n in (1, 2)}
     pool = []
-    for i in range(args.pool):
+    for i in range(npool):
         h, w = int(rng.integers(256, 4097)), int(rng.integers(256, 4097))
         r = np.random.default_rng(synthetic.SEED_BASE + 4 + 1000 * (i + 1))
         img = synthetic.image_f32_grid(r, (h, w), 24.0, 12, 16)
         sc = synthetic.ellipse_field(r, (h, w))
-        d = _abf.abf_desc()
-        d.width, d.height, d.scale_kind, d.q_bits, d.max_scale = w, h, _abf.ABF_SCALES_ELLIPSE, 8, 150.0
-        prods = {}
-        for n in (1, 2):
-            d.order_n = n
-            prods[n] = _abf.abf_measure_scales(d, torch.from_numpy(sc).to(dev), w * 16)[1]
         pool.append(dict(img=torch.from_numpy(img).pin_memory(), sc=torch.from_numpy(sc).pin_memory(),
-                         outs=[torch.empty((h, w), dtype=torch.float32).pin_memory() for _ in range(args.inflight + 2)],
+                         outs=[torch.empty((h, w), dtype=torch.float32).pin_memory() for _ in range(inflight + 2)],
                          desc={n: make_desc(w, h, n, torch.float32, scale_kind="ellipse", q_bits=8, frac_bits=16,
                                             max_scale=150.0, out="f32", value_bound=255.0,
                                             max_scale_product=prods[n]) for n in (1, 2)},
                          px=h * w, next=0))
-    free, _ = torch.cuda.mem_get_info(dev)
-    budget = int(free * 0.5)
+    return pool
 
-    def draw(rg):
-        e = pool[int(rg.integers(0, len(pool)))]
-        return e, int(rg.integers(1, 3))
 
-    def submit(srv, e, n):
+def _serve_stream(pool, budget, inflight, lam, njobs, warm, seed, dev):
+    """One request stream through the library's server: njobs jobs drawn from
+    the pool (order n U{1,2}) with exponential gaps of mean 1/lam seconds (lam
+    = 0: all at once); latency = done - submit of the jobs after the first
+    `warm`.  Every job's status must be ok."""
+    from paper_0908_3861_gb300 import Server
+    srv = Server(budget, max_inflight=inflight, device=dev)
+    rg = np.random.default_rng(seed)
+
+    def submit(e, n):
         o = e["outs"][e["next"] % len(e["outs"])]
         e["next"] += 1
         return srv.submit(e["desc"][n], e["img"], e["sc"], o), e["px"]
 
-    def run_stream(inflight, lam, njobs, warm, seed):
-        srv = Server(budget, max_inflight=inflight, device=dev)
-        rg = np.random.default_rng(seed)
-        for e in pool:                       # plans and tables, outside the measurement
-            for n in (1, 2):
-                srv.wait(submit(srv, e, n)[0])
-        gaps = rg.exponential(1.0 / lam, njobs) if lam else np.zeros(njobs)
-        t0 = time.perf_counter()
-        due = t0
-        tickets = []
-        for k in range(njobs):
-            due += gaps[k]
-            dt = due - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            e, n = draw(rg)
-            tickets.append(submit(srv, e, n))
-        stats = [(srv.wait(t), px) for t, px in tickets]
-        srv.close()
-        meas = stats[warm:]
-        lat = np.array([(s["t_done_us"] - s["t_submit_us"]) * 1e-3 for s, _ in meas])
-        span = (max(s["t_done_us"] for s, _ in meas) - min(s["t_submit_us"] for s, _ in meas)) * 1e-6
-        return dict(p50_ms=round(float(np.percentile(lat, 50)), 2), p99_ms=round(float(np.percentile(lat, 99)), 2),
-                    mpix_s=round(sum(px for _, px in meas) / span / 1e6, 2), jobs=len(meas),
-                    jobs_per_s=round(len(meas) / span, 2))
+    for e in pool:                       # plans and tables, outside the measurement
+        for n in (1, 2):
+            srv.wait(submit(e, n)[0])
+    gaps = rg.exponential(1.0 / lam, njobs) if lam else np.zeros(njobs)
+    t0 = time.perf_counter()
+    due = t0
+    tickets = []
+    for k in range(njobs):
+        due += gaps[k]
+        dt = due - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        e = pool[int(rg.integers(0, len(pool)))]
+        tickets.append(submit(e, int(rg.integers(1, 3))))
+    stats = [(srv.wait(t), px) for t, px in tickets]
+    peak = srv.stats()["peak"]
+    srv.close()
+    assert all(s["status"] == 0 and s["device_status"] == 0 for s, _ in stats)
+    meas = stats[warm:]
+    lat = np.array([(s["t_done_us"] - s["t_submit_us"]) * 1e-3 for s, _ in meas])
+    span = (max(s["t_done_us"] for s, _ in meas) - min(s["t_submit_us"] for s, _ in meas)) * 1e-6
+    # device overlap: pairs of consecutive jobs whose device-clock intervals intersect
+    iv = sorted((s["t_gpu_start_us"], s["t_gpu_end_us"]) for s, _ in meas)
+    overl = sum(1 for a, b in zip(iv, iv[1:]) if b[0] < a[1])
+    return dict(p50_ms=round(float(np.percentile(lat, 50)), 2), p99_ms=round(float(np.percentile(lat, 99)), 2),
+                mpix_s=round(sum(px for _, px in meas) / span / 1e6, 2), jobs=len(meas), warmup_jobs=warm,
+                jobs_per_s=round(len(meas) / span, 2), overlapping_neighbours=overl, peak_bytes=int(peak),
+                budget_bytes=int(budget))
 
+
+def serving_leg(dev, npool=4, inflight=4, sat_jobs=32, jobs=300, warm=30):
+    """A short serving measurement for the default line: saturation rate from
+    a burst, then p50/p99 latency of a Poisson stream at 0.8 of it."""
+    import torch
+    pool = _serve_pool(npool, inflight, dev)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.5)
+    sat = _serve_stream(pool, budget, inflight, 0.0, sat_jobs, 0, 11, dev)
+    load = _serve_stream(pool, budget, inflight, 0.8 * sat["jobs_per_s"], jobs + warm, warm, 80, dev)
+    return {"workload": "Poisson stream at 0.8 x the saturation rate, %d distinct jobs, sides U{256..4096}, "
+                        "n U{1,2}, f32 + ellipse fields; exact form; %d slots; HBM budget half the free memory"
+                        % (npool, inflight),
+            "saturation_mpix_s": sat["mpix_s"], "saturation_jobs_per_s": sat["jobs_per_s"],
+            "p50_ms": load["p50_ms"], "p99_ms": load["p99_ms"], "mpix_s": load["mpix_s"], "jobs": load["jobs"],
+            "warmup_jobs": warm, "overlapping_neighbours": load["overlapping_neighbours"]}
+
+
+def run_serve(args):
+    """Poisson-arrival stream of filter jobs (sides U{256..4096}, n U{1,2},
+    float32 images on the 2^-16 grid with ellipse fields as the 2048^2 case)
+    through the library's request loop, admitted by device-memory footprint
+    (budget: half the free HBM).  Measures the saturation rate, then p50/p99
+    latency (done - arrival) at 0.5, 0.8 and 0.95 of it (--jobs measured jobs
+    after a warm-up of a tenth as many); and the same stream at 0.8 of it
+    through a one-job-at-a-time server."""
+    import torch
+    import __graft_entry__
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    pool = _serve_pool(args.pool, args.inflight, dev, rank)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.5)
+    warm = max(args.jobs // 10, 1)
     with ClockSampler(local) as clk:
-        sat = run_stream(args.inflight, 0.0, args.sat_jobs, 0, 11)
+        sat = _serve_stream(pool, budget, args.inflight, 0.0, args.sat_jobs, 0, 11, dev)
         mu = sat["jobs_per_s"]
         loads = {}
         for frac in (0.5, 0.8, 0.95):
-            loads[str(frac)] = run_stream(args.inflight, frac * mu, args.jobs + args.jobs // 10, args.jobs // 10,
-                                          int(frac * 100))
-        fifo = run_stream(1, 0.8 * mu, args.jobs + args.jobs // 10, args.jobs // 10, 80)
+            loads[str(frac)] = _serve_stream(pool, budget, args.inflight, frac * mu, args.jobs + warm, warm,
+                                             int(frac * 100), dev)
+        fifo = _serve_stream(pool, budget, 1, 0.8 * mu, args.jobs + warm, warm, 80, dev)
     line = {"metric": METRIC, "value": sat["mpix_s"], "unit": UNIT, "n_gpus": 1, "steps": args.sat_jobs,
             "warmup": 2 * len(pool), "ms_per_step": round(1e3 / mu, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64 limbs", "data": "synthetic",
@@ -883,8 +976,10 @@ def main():
     ap.add_argument("--n2", type=int, default=None, help="d1: analysis degree")
     ap.add_argument("--pool", type=int, default=8, help="c5: distinct images in the request pool")
     ap.add_argument("--inflight", type=int, default=4, help="c5: concurrent jobs (slots)")
-    ap.add_argument("--jobs", type=int, default=200, help="c5: measured jobs per load")
+    ap.add_argument("--jobs", type=int, default=2000, help="c5: measured jobs per load (after a tenth as many)")
     ap.add_argument("--sat-jobs", dest="sat_jobs", type=int, default=48, help="c5: jobs of the saturation burst")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="default workload: skip the short serving leg")
     ap.add_argument("--compare", default="plain_f64,tile_f32",
                     help="comma-separated forms timed beside the exact form ('' for none)")
     args = ap.parse_args()
@@ -899,6 +994,8 @@ def main():
         run_line1d(args)
     elif args.workload == "s2":
         run_scale_map(args)
+    elif args.workload == "cc":
+        run_constant_cost(args)
     else:
         run_ours(args)
 

@@ -149,7 +149,9 @@ abf_status abf_integrate(abf_plan plan, const void* d_f, size_t f_pitch, void* d
  * d_f and d_g exactly as for abf_integrate.
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: after
+ *     cudaDeviceReset on that device the cached address is stale, so do not
+ *     call this entry point again in a process that reset the device.
  *   - The current device must be the plan's device (else ABF_ERR_INVALID).
  *   - Plans whose workspace (abf_plan_query) exceeds 32 MiB are rejected with
  *     ABF_ERR_UNSUPPORTED (e.g. order 2, two limbs, steps up to 150: images up
@@ -261,14 +263,21 @@ typedef struct {
   double t_submit_us, t_admit_us, t_done_us;  /* host steady clock, microseconds  */
   int32_t resident_hit;     /* 1 if the integrated image was reused                 */
   int32_t status;           /* abf_status of the job (valid once done)              */
-  int32_t device_status;    /* OR of ABF_DEV_* bits seen by this job's plan          */
+  int32_t device_status;    /* OR of ABF_DEV_* bits raised by this job's own launches */
   int32_t reserved;
+  /* Device clock (CUDA events on the job's stream), microseconds since the
+   * server was created: when the job's first copy could start and when its
+   * last copy ended.  Two jobs whose intervals intersect were on the device
+   * at the same time.  0 if the job never ran.                              */
+  double t_gpu_start_us, t_gpu_end_us;
 } abf_job_stats;
 
 /* Start a server on the current device.  Errors: ABF_ERR_INVALID, ABF_ERR_CUDA. */
 abf_status abf_server_create(const abf_server_cfg* cfg, abf_server* out);
 /* Queue a job; the host buffers must stay valid until the job is done.
- * ABF_ERR_BUSY if the job alone exceeds the budget.                         */
+ * ABF_ERR_BUSY if the job alone exceeds the budget.  A request with h_f =
+ * NULL must name an image that is resident now (else ABF_ERR_INVALID); that
+ * image is then held (never evicted) until the job is done.                 */
 abf_status abf_submit(abf_server srv, const abf_request* req, uint64_t* ticket);
 /* done = 1 once the job finished (stats filled); the record is kept until waited. */
 abf_status abf_poll(abf_server srv, uint64_t ticket, int32_t* done, abf_job_stats* stats);

@@ -11,11 +11,12 @@ from . import _abf
 from ._abf import AbfError
 
 __all__ = ["_abf", "AbfError", "AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc",
-           "estimate_ellipses"]
+           "estimate_ellipses", "ellipse_product_bound"]
 
 
 def __getattr__(name):
-    if name in ("AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc", "estimate_ellipses"):
+    if name in ("AdaptiveFilter", "AdaptiveFilter1D", "Batch", "Server", "make_desc", "estimate_ellipses",
+                "ellipse_product_bound"):
         from . import filter as _f
         return getattr(_f, name)
     raise AttributeError(name)

@@ -63,7 +63,8 @@ class abf_request(ctypes.Structure):
 class abf_job_stats(ctypes.Structure):
     _fields_ = [("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
                 ("resident_hit", ctypes.c_int32), ("status", ctypes.c_int32), ("device_status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("t_gpu_start_us", ctypes.c_double),
+                ("t_gpu_end_us", ctypes.c_double)]
 
 
 _lib = None

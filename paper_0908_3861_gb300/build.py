@@ -31,7 +31,19 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def check_generated():
+    """The carry-chained MAC routines in abf_internal.cuh are written by
+    csrc/gen_mac_chains.py: re-check their schedule and that the header holds
+    exactly what the generator writes."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("gen_mac_chains", os.path.join(CSRC, "gen_mac_chains.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.check_header(os.path.join(CSRC, "abf_internal.cuh"))
+
+
 def build(verbose=False, extra_flags=()):
+    check_generated()
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()

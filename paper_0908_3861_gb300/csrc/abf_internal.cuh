@@ -174,7 +174,8 @@ __device__ __forceinline__ void wmac2_u64(Wide<2>& acc, const Wide<2>& g, uint64
 }
 
 // Carry-chained multiply-accumulates for wider limbs and weights (written by
-// gen_mac_chains.py beside this file, which also checks the schedule).
+// gen_mac_chains.py beside this file; the build re-checks their schedule and
+// that this file holds exactly what the generator writes).
 // acc += g * w (mod 2^192): 3-limb g, 64-bit w; 20 multiply-adds in carry chains.
 __device__ __forceinline__ void wmac_w6_b2(Wide<3>& acc, const Wide<3>& g, uint32_t w0, uint32_t w1) {
   uint32_t r[6], a[6];
@@ -725,3 +726,13 @@ struct abf_plan_s {
   size_t g_bytes = 0, ws_bytes = 0;
   int mesh_warps = 8;          // rows per CTA of the exact mesh (abf_plan_autotune)
 };
+
+namespace abf {
+// abf_integrate / abf_filter (exact form) with the device status word given by
+// the caller instead of the plan's own: the serving loop gives every slot its
+// own word, so that jobs sharing a plan do not see each other's flags.
+abf_status integrate_with_status(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, void* d_ws,
+                                 int32_t* d_status, cudaStream_t st);
+abf_status filter_with_status(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_s,
+                              size_t s_pitch, int32_t* d_status, cudaStream_t st);
+}  // namespace abf

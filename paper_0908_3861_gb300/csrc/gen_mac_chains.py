@@ -6,7 +6,9 @@ a_0 w_j at word j and the high halves of a_i w_j at words j+1+i, a second
 chain adds the low halves of a_i w_j (i >= 1) at words j+i; each chain
 carries up to the top word, and the carry out of the top is the modulus.
 Running it prints the routines and checks the schedule against Python
-integers (the carry semantics of mad.cc / madc) on random operands.
+integers (the carry semantics of mad.cc / madc) on random operands; the
+build (build.py) runs check_header() first, which repeats that check and
+requires abf_internal.cuh to hold exactly the routines generated here.
 """
 def chain(W, B):
     lines = []
@@ -57,12 +59,17 @@ def emit(W, B, name):
     out.append('}')
     return '\n'.join(out)
 
-for (W, B) in [(6, 2), (8, 2), (4, 4), (6, 4), (8, 4)]:
-    print(emit(W, B, 'wmac_w%d_b%d' % (W, B)))
-    print()
-# self-check of the schedule on random numbers in Python
-import random
+ROUTINES = [(6, 2), (8, 2), (4, 4), (6, 4), (8, 4)]
+
+
+def generate():
+    """The routines as they appear in abf_internal.cuh, in order."""
+    return [emit(W, B, 'wmac_w%d_b%d' % (W, B)) for (W, B) in ROUTINES]
+
+
 def sim(W, B, acc, a, w):
+    """The chain run on Python integers with the carry semantics of mad.cc /
+    madc (the carry flag holds the bit out of the 32-bit sum)."""
     r = [(acc >> (32 * k)) & 0xffffffff for k in range(W)]
     A = [(a >> (32 * k)) & 0xffffffff for k in range(W)]
     Wv = [(w >> (32 * k)) & 0xffffffff for k in range(B)]
@@ -78,9 +85,36 @@ def sim(W, B, acc, a, w):
         r[di] = s & 0xffffffff
         cc = (s >> 32) if '.cc' in op else 0
     return sum(v << (32 * k) for k, v in enumerate(r))
-for (W, B) in [(4, 2), (6, 2), (8, 2), (4, 4), (6, 4), (8, 4), (4, 1), (6, 1), (8, 1)]:
-    for _ in range(2000):
-        acc = random.getrandbits(32 * W); a = random.getrandbits(32 * W); w = random.getrandbits(32 * B)
-        assert sim(W, B, acc, a, w) == (acc + a * w) % (1 << (32 * W)), (W, B)
-import sys
-print('// schedule verified', file=sys.stderr)
+
+
+def verify_schedule(trials=400, seed=0):
+    """Every chain schedule equals acc + a w modulo 2^(32 W) on random operands."""
+    import random
+    rnd = random.Random(seed)
+    for (W, B) in [(4, 2), (6, 2), (8, 2), (4, 4), (6, 4), (8, 4), (4, 1), (6, 1), (8, 1)]:
+        for _ in range(trials):
+            acc = rnd.getrandbits(32 * W); a = rnd.getrandbits(32 * W); w = rnd.getrandbits(32 * B)
+            if sim(W, B, acc, a, w) != (acc + a * w) % (1 << (32 * W)):
+                raise AssertionError('carry chain schedule wrong for W=%d B=%d' % (W, B))
+
+
+def check_header(path=None):
+    """The build's check: the schedules are right and abf_internal.cuh holds
+    exactly the routines this generator writes."""
+    import os
+    path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), 'abf_internal.cuh')
+    verify_schedule()
+    with open(path) as fh:
+        text = fh.read()
+    for body in generate():
+        if body not in text:
+            raise AssertionError('abf_internal.cuh differs from the generated routine:\n' + body.split('\n')[1])
+
+
+if __name__ == '__main__':
+    import sys
+    for body in generate():
+        print(body)
+        print()
+    verify_schedule(trials=2000)
+    print('// schedule verified', file=sys.stderr)

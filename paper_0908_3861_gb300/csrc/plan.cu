@@ -420,6 +420,30 @@ double u128_to_double(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073
 
 // ------------------------------------------------------------------ the plan
 
+static abf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ABF_OK : ABF_ERR_CUDA; }
+
+abf_status abf::integrate_with_status(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, void* d_ws,
+                                      int32_t* d_status, cudaStream_t st) {
+  if (!p || !d_f || !d_g || !d_ws || !d_status) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
+  if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
+  return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, d_status, st));
+}
+
+abf_status abf::filter_with_status(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_s,
+                                   size_t s_pitch, int32_t* d_status, cudaStream_t st) {
+  if (!p || !d_g || !d_scales || !d_s || !d_status) return ABF_ERR_INVALID;
+  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
+  if (scale_pitch < (size_t)p->pv.W * 16 || s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
+  if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, d_s, s_pitch, nullptr, 0,
+                                         d_status, p->mesh_warps, st));
+}
+
 
 
 extern "C" {
@@ -563,16 +587,9 @@ abf_status abf_plan_denominator(abf_plan p, uint32_t* w4) {
   return ABF_OK;
 }
 
-static abf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ABF_OK : ABF_ERR_CUDA; }
-
 abf_status abf_integrate(abf_plan p, const void* d_f, size_t f_pitch, void* d_g, void* d_ws, cudaStream_t st) {
-  if (!p || !d_f || !d_g || !d_ws) return ABF_ERR_INVALID;
-  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
-  const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
-  if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
-  if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
-  uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
-  return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, p->d_status, st));
+  if (!p) return ABF_ERR_INVALID;
+  return abf::integrate_with_status(p, d_f, f_pitch, d_g, d_ws, p->d_status, st);
 }
 
 abf_status abf_debug_starved_lookback(abf_plan p, void* d_g, void* d_ws, cudaStream_t st) {
@@ -609,8 +626,7 @@ abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const voi
     return cuda_status(abf::run_tiles(p->pv, p->desc.form == ABF_FORM_PLAIN_F64, d_src, src_pitch, d_scales,
                                       scale_pitch, d_s, s_pitch, d_ws, p->real_table, p->d_status, st));
   }
-  return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_src, d_scales, scale_pitch, d_s, s_pitch,
-                                         nullptr, 0, p->d_status, p->mesh_warps, st));
+  return abf::filter_with_status(p, d_src, d_scales, scale_pitch, d_s, s_pitch, p->d_status, st);
 }
 
 abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_num,

@@ -523,16 +523,22 @@ cudaError_t run_lookback_starved(const PlanView& pv, uint64_t* g, void* ws, uint
   }
 }
 
-cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
-                          uint32_t* epoch, int32_t* status, cudaStream_t st) {
-  const cudaError_t e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
-  if (e != cudaSuccess) return e;
+// The scans alone, on a workspace whose ticket and flags already read as zero.
+static cudaError_t integrate_cleared(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
+                                     uint32_t* epoch, int32_t* status, cudaStream_t st) {
   switch (pv.limbs) {
     case 1: return integrate_L<1>(pv, f, f_pitch, g, ws, epoch, status, st);
     case 2: return integrate_L<2>(pv, f, f_pitch, g, ws, epoch, status, st);
     case 3: return integrate_L<3>(pv, f, f_pitch, g, ws, epoch, status, st);
     default: return integrate_L<4>(pv, f, f_pitch, g, ws, epoch, status, st);
   }
+}
+
+cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
+                          uint32_t* epoch, int32_t* status, cudaStream_t st) {
+  const cudaError_t e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
+  if (e != cudaSuccess) return e;
+  return integrate_cleared(pv, f, f_pitch, g, ws, epoch, status, st);
 }
 
 // ------------------------------------------------------ fixed-scratch variant
@@ -568,14 +574,12 @@ static cudaError_t noalloc_scratch(void** out) {
   return cudaSuccess;
 }
 
-// The same scans as run_integrate, on the fixed scratch.  The ticket and the
-// flags are cleared first: the array keeps whatever the previous call left.
+// The same scans as run_integrate, on the fixed scratch (which clears the
+// ticket and the flags first: the array keeps whatever the previous call left).
 cudaError_t run_integrate_noalloc(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, uint32_t* epoch,
                                   int32_t* status, cudaStream_t st) {
   void* ws = nullptr;
-  cudaError_t e = noalloc_scratch(&ws);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
+  const cudaError_t e = noalloc_scratch(&ws);
   if (e != cudaSuccess) return e;
   return run_integrate(pv, f, f_pitch, g, ws, epoch, status, st);
 }

@@ -55,8 +55,10 @@ struct Job {
   void *d_f = nullptr, *d_sc = nullptr, *d_s = nullptr, *d_g = nullptr, *d_ws = nullptr;
   size_t bytes = 0;        // footprint charged to the budget
   int slot = -1;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;     // end of the job's stream work (timed)
+  cudaEvent_t ev0 = nullptr;    // start of the job's stream work (timed)
   Resident* res = nullptr; // integrated image reused from / kept in the resident set
+  Resident* pinned = nullptr;  // resident image held since submit (a request without h_f)
   bool keep = false;       // keep d_g resident after the job
   abf_job_stats st{};
   int state = 0;           // 0 queued, 1 running, 2 done
@@ -78,6 +80,8 @@ struct abf_server_s {
   std::vector<cudaStream_t> streams;
   std::vector<int> slot_busy;
   int32_t* h_dev_status = nullptr;  // pinned, one word per slot
+  int32_t* d_slot_status = nullptr; // device status word per slot, cleared before every job
+  cudaEvent_t base_ev = nullptr;    // device-clock origin of the job timestamps
   size_t used = 0, peak = 0;
   uint64_t next_ticket = 1;
   bool stop = false, paused = false;
@@ -132,6 +136,7 @@ struct abf_server_s {
     abf_status s;
     j->plan = plan_for(j->req.desc, &s);
     if (s != ABF_OK) {
+      unpin(j);
       finish(j, s);
       return true;
     }
@@ -139,7 +144,8 @@ struct abf_server_s {
     const int W = p->pv.W, H = p->pv.H;
     const size_t fb = (size_t)W * H * elem_bytes(p->pv.in_dtype), sb = (size_t)W * H * 16,
                  ob = (size_t)W * H * elem_bytes(p->pv.out_dtype);
-    j->res = find_resident(j->req.image_id, j->key);
+    // a request without an image uses the resident image held since submit
+    j->res = j->pinned ? j->pinned : find_resident(j->req.image_id, j->key);
     const bool hit = j->res != nullptr;
     const size_t need = (hit ? 0 : fb + p->g_bytes + p->ws_bytes) + sb + ob;
     if (!make_room(need, st)) return false;
@@ -153,6 +159,10 @@ struct abf_server_s {
     running.push_back(j);
     cudaError_t e = cudaSuccess;
     auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    int32_t* dst = d_slot_status + slot;
+    ok(cudaEventCreate(&j->ev0));
+    if (e == cudaSuccess) ok(cudaEventRecord(j->ev0, st));
+    ok(cudaMemsetAsync(dst, 0, sizeof(int32_t), st));
     ok(cudaMallocAsync(&j->d_sc, sb, st));
     ok(cudaMallocAsync(&j->d_s, ob, st));
     if (e == cudaSuccess)
@@ -160,7 +170,8 @@ struct abf_server_s {
                            cudaMemcpyHostToDevice, st));
     if (hit) {
       j->d_g = j->res->d_g;
-      j->res->users++;
+      if (!j->pinned) j->res->users++;  // a pinned image was counted at submit
+      j->pinned = nullptr;              // from here on released through j->res
       j->res->last_use = now_us();
       j->st.resident_hit = 1;
     } else {
@@ -170,18 +181,19 @@ struct abf_server_s {
       if (e == cudaSuccess)
         ok(cudaMemcpy2DAsync(j->d_f, (size_t)W * elem_bytes(p->pv.in_dtype), j->req.h_f, j->req.f_pitch,
                              (size_t)W * elem_bytes(p->pv.in_dtype), H, cudaMemcpyHostToDevice, st));
-      if (e == cudaSuccess && abf_integrate(p, j->d_f, (size_t)W * elem_bytes(p->pv.in_dtype), j->d_g, j->d_ws, st) != ABF_OK)
+      if (e == cudaSuccess && abf::integrate_with_status(p, j->d_f, (size_t)W * elem_bytes(p->pv.in_dtype), j->d_g,
+                                                         j->d_ws, dst, st) != ABF_OK)
         e = cudaErrorLaunchFailure;
     }
     if (e == cudaSuccess &&
-        abf_filter(p, j->d_g, 0, j->d_sc, (size_t)W * 16, j->d_s, (size_t)W * elem_bytes(p->pv.out_dtype), j->d_ws, st) !=
-            ABF_OK)
+        abf::filter_with_status(p, j->d_g, j->d_sc, (size_t)W * 16, j->d_s, (size_t)W * elem_bytes(p->pv.out_dtype),
+                                dst, st) != ABF_OK)
       e = cudaErrorLaunchFailure;
     if (e == cudaSuccess)
       ok(cudaMemcpy2DAsync(j->req.h_s, j->req.s_pitch, j->d_s, (size_t)W * elem_bytes(p->pv.out_dtype),
                            (size_t)W * elem_bytes(p->pv.out_dtype), H, cudaMemcpyDeviceToHost, st));
-    if (e == cudaSuccess) ok(cudaMemcpyAsync(&h_dev_status[slot], p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (e == cudaSuccess) ok(cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming));
+    if (e == cudaSuccess) ok(cudaMemcpyAsync(&h_dev_status[slot], dst, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (e == cudaSuccess) ok(cudaEventCreate(&j->ev));
     if (e == cudaSuccess) ok(cudaEventRecord(j->ev, st));
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -190,13 +202,32 @@ struct abf_server_s {
     return true;
   }
 
+  // Release the resident image a request without h_f has held since submit.
+  void unpin(Job* j) {
+    if (j->pinned) {
+      j->pinned->users--;
+      j->pinned = nullptr;
+    }
+  }
+
   // Release a running job's resources (after its event completed, or on error).
   void complete(Job* j, abf_status s) {
     cudaStream_t st = streams[j->slot];
     if (j->ev) {
       j->st.device_status = h_dev_status[j->slot];
+      float a = 0.f, b = 0.f;
+      if (s == ABF_OK && cudaEventElapsedTime(&a, base_ev, j->ev0) == cudaSuccess &&
+          cudaEventElapsedTime(&b, base_ev, j->ev) == cudaSuccess) {
+        j->st.t_gpu_start_us = 1e3 * (double)a;
+        j->st.t_gpu_end_us = 1e3 * (double)b;
+      }
+      cudaGetLastError();
       cudaEventDestroy(j->ev);
       j->ev = nullptr;
+    }
+    if (j->ev0) {
+      cudaEventDestroy(j->ev0);
+      j->ev0 = nullptr;
     }
     size_t freed = 0;
     const abf_plan p = j->plan;
@@ -279,6 +310,18 @@ abf_status abf_server_create(const abf_server_cfg* cfg, abf_server* out) {
     delete s;
     return ABF_ERR_CUDA;
   }
+  if (cudaMalloc((void**)&s->d_slot_status, sizeof(int32_t) * cfg->max_inflight) != cudaSuccess) {
+    cudaFreeHost(s->h_dev_status);
+    delete s;
+    return ABF_ERR_CUDA;
+  }
+  if (cudaEventCreate(&s->base_ev) != cudaSuccess || cudaEventRecord(s->base_ev, s->streams[0]) != cudaSuccess ||
+      cudaEventSynchronize(s->base_ev) != cudaSuccess) {
+    cudaFreeHost(s->h_dev_status);
+    cudaFree(s->d_slot_status);
+    delete s;
+    return ABF_ERR_CUDA;
+  }
   s->worker = std::thread([s] { s->loop(); });
   *out = s;
   return ABF_OK;
@@ -309,9 +352,16 @@ abf_status abf_submit(abf_server s, const abf_request* req, uint64_t* ticket) {
       delete j;
       return ABF_ERR_BUSY;
     }
-    if (!req->h_f && !s->find_resident(req->image_id, j->key)) {
-      delete j;
-      return ABF_ERR_INVALID;
+    if (!req->h_f) {
+      // hold the resident image from now on, so that no eviction can take it
+      // away before the job is admitted
+      Resident* r = s->find_resident(req->image_id, j->key);
+      if (!r) {
+        delete j;
+        return ABF_ERR_INVALID;
+      }
+      r->users++;
+      j->pinned = r;
     }
     j->ticket = s->next_ticket++;
     s->jobs[j->ticket] = j;
@@ -391,6 +441,8 @@ abf_status abf_server_destroy(abf_server s) {
     cudaStreamDestroy(st);
   }
   if (s->h_dev_status) cudaFreeHost(s->h_dev_status);
+  if (s->d_slot_status) cudaFree(s->d_slot_status);
+  if (s->base_ev) cudaEventDestroy(s->base_ev);
   delete s;
   return ABF_OK;
 }

@@ -200,7 +200,8 @@ class Server:
         st = C.abf_wait(self.h, ticket, -1 if timeout_s is None else int(timeout_s * 1e6))
         self.keep.pop(ticket, None)
         return dict(t_submit_us=st.t_submit_us, t_admit_us=st.t_admit_us, t_done_us=st.t_done_us,
-                    resident_hit=st.resident_hit, status=st.status, device_status=st.device_status)
+                    resident_hit=st.resident_hit, status=st.status, device_status=st.device_status,
+                    t_gpu_start_us=st.t_gpu_start_us, t_gpu_end_us=st.t_gpu_end_us)
 
     def poll(self, ticket):
         done, st = C.abf_poll(self.h, ticket)
@@ -304,3 +305,31 @@ def estimate_ellipses(f, rho=2.0, sigma0=4.0, e_max=4.0, stream=None):
     C.abf_estimate_ellipses(f, f.stride(0) * f.element_size(), _DT[f.dtype], W, H, float(rho), float(sigma0),
                             float(e_max), ws, out, W * 16, stream)
     return out
+
+
+def ellipse_product_bound(sigma_max, e_max, n, q_bits=8, max_scale=150.0, device=None, margin=1.01):
+    """An upper bound on c1 c2 c3 c4 for every ellipse with sigma <= sigma_max
+    and elongation in [1, e_max] (any orientation), for abf_desc's
+    max_scale_product: the library's own moment rule measured
+    (abf_measure_scales) over a grid of the parameter range at sigma_max (every
+    step grows with sigma), times a margin for the space between grid points.
+    It depends on the parameter range only, not on an image's scale field;
+    the filter still checks every pixel's numerator bound and flags a pixel
+    that exceeds it (ABF_DEV_RANGE), so a bound that is too small is never
+    silently wrong."""
+    import math
+    dev = torch.device(device or "cuda")
+    ne, nt = 64, 1024
+    e = torch.linspace(1.0, float(e_max), ne, dtype=torch.float64)
+    th = torch.arange(nt, dtype=torch.float64) * (math.pi / nt)
+    f = torch.empty((ne, nt, 4), dtype=torch.float32)
+    f[..., 0] = float(sigma_max)
+    f[..., 1] = e[:, None].to(torch.float32)
+    f[..., 2] = torch.cos(th)[None, :].to(torch.float32)
+    f[..., 3] = torch.sin(th)[None, :].to(torch.float32)
+    d = C.abf_desc()
+    d.width, d.height, d.order_n = nt, ne, int(n)
+    d.scale_kind = C.ABF_SCALES_ELLIPSE
+    d.q_bits, d.max_scale = int(q_bits), float(max_scale)
+    _, prod = C.abf_measure_scales(d, f.to(dev), nt * 16)
+    return prod * margin

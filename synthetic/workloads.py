@@ -103,7 +103,7 @@ def workload(name, shape=None, seed_offset=0):
         img = image_c2(rng, shape)
         sc = ellipse_field(rng, shape)
         return dict(image=img, frac_bits=16, scale_kind="ellipse", scales=sc, n=2, q_bits=8,
-                    cmax=150.0, value_bound=255.0)
+                    cmax=150.0, value_bound=255.0, sigma_max=24.0, e_max=6.0)
     if name == "c3":  # 8192x8192 uint16, n=3, a_k in [1, 48]
         rng = np.random.default_rng(SEED_BASE + 2 + seed_offset)
         shape = shape or (8192, 8192)

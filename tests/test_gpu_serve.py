@@ -137,3 +137,94 @@ def test_job_larger_than_budget_is_refused():
         srv.submit(_desc(img, n), _pinned(img), _pinned(sc), o)
     assert e.value.status == 7   # ABF_ERR_BUSY
     srv.close()
+
+
+def test_device_status_is_per_job_not_per_descriptor():
+    """A job with an invalid scale raises its own status bit; the next job
+    with the same descriptor (so the same plan) starts from a clear word."""
+    import torch
+    from paper_0908_3861_gb300 import Server
+    img, sc, n = _job(600, 48, 64, 2)
+    bad = sc.copy()
+    bad[5, 7, 0] = np.nan   # sigma not finite: ABF_DEV_BAD_SCALE for that pixel
+    srv = Server(64 << 20, max_inflight=1, device="cuda:0")
+    o1 = torch.zeros(img.shape, dtype=torch.float32).pin_memory()
+    o2 = torch.zeros(img.shape, dtype=torch.float32).pin_memory()
+    t1 = srv.submit(_desc(img, n), _pinned(img), _pinned(bad), o1)
+    t2 = srv.submit(_desc(img, n), _pinned(img), _pinned(sc), o2)
+    s1 = srv.wait(t1, timeout_s=60)
+    s2 = srv.wait(t2, timeout_s=60)
+    assert s1["status"] == 0 and s1["device_status"] == 1
+    assert torch.isnan(o1[5, 7]) and int(torch.isnan(o1).sum()) == 1
+    assert s2["status"] == 0 and s2["device_status"] == 0
+    assert torch.equal(o2, _alone(img, sc, n))
+    srv.close()
+
+
+def _footprint(img, n, hit):
+    """Device bytes the server charges for a job (f32 image, f32 output)."""
+    import torch
+    from paper_0908_3861_gb300 import AdaptiveFilter
+    H, W = img.shape
+    f = AdaptiveFilter(W, H, n, torch.float32, scale_kind="ellipse", q_bits=6, frac_bits=16, max_scale=20.0,
+                       out="f32", value_bound=255.0, device="cuda:0")
+    g, ws = f.info["integrated_bytes"], f.info["workspace_bytes"]
+    f.close()
+    return H * W * (16 + 4) + (0 if hit else H * W * 4 + g + ws), g
+
+
+def test_resident_image_named_at_submit_survives_a_later_eviction():
+    """A request without an image (h_f = NULL) holds its resident image from
+    submit on.  Here a job queued before it needs the room that image takes:
+    that job must wait for the resident job instead of evicting its image."""
+    import torch
+    from paper_0908_3861_gb300 import Server
+    img_a, sc_a, n = _job(700, 64, 64, 2)
+    _, sc_b, _ = _job(701, 64, 64, 2)
+    img_c, sc_c, _ = _job(702, 64, 64, 2)
+    need_c, g_a = _footprint(img_c, n, hit=False)
+    need_b, _ = _footprint(img_a, n, hit=True)
+    budget = need_c           # C alone fits; C beside the resident image does not
+    assert g_a + need_b <= budget < g_a + need_c
+    srv = Server(budget, max_inflight=2, device="cuda:0")
+    oa = torch.zeros(img_a.shape, dtype=torch.float32).pin_memory()
+    assert srv.wait(srv.submit(_desc(img_a, n), _pinned(img_a), _pinned(sc_a), oa, image_id=9),
+                    timeout_s=60)["status"] == 0
+    assert srv.stats()["resident"] == 1
+    srv.pause(True)
+    oc = torch.zeros(img_c.shape, dtype=torch.float32).pin_memory()
+    ob = torch.zeros(img_a.shape, dtype=torch.float32).pin_memory()
+    tc = srv.submit(_desc(img_c, n), _pinned(img_c), _pinned(sc_c), oc)
+    tb = srv.submit(_desc(img_a, n), None, _pinned(sc_b), ob, image_id=9)
+    srv.pause(False)
+    sb = srv.wait(tb, timeout_s=60)
+    sc_ = srv.wait(tc, timeout_s=60)
+    assert sb["status"] == 0 and sb["resident_hit"] == 1
+    assert sc_["status"] == 0
+    assert torch.equal(ob, _alone(img_a, sc_b, n))
+    assert torch.equal(oc, _alone(img_c, sc_c, n))
+    assert srv.stats()["peak"] <= budget
+    srv.close()
+
+
+def test_concurrent_jobs_overlap_on_the_device():
+    """With two slots, two long jobs submitted together are on the device at
+    the same time: their device-clock intervals (CUDA events on their own
+    streams) intersect, and each result equals the job run alone."""
+    import torch
+    from paper_0908_3861_gb300 import Server
+    jobs = [_job(800 + i, 512, 512, 2) for i in range(2)]
+    srv = Server(1 << 30, max_inflight=2, device="cuda:0")
+    outs, tickets = [], []
+    for img, sc, n in jobs:
+        o = torch.zeros(img.shape, dtype=torch.float32).pin_memory()
+        tickets.append(srv.submit(_desc(img, n), _pinned(img), _pinned(sc), o))
+        outs.append(o)
+    st = [srv.wait(t, timeout_s=120) for t in tickets]
+    for s in st:
+        assert s["status"] == 0 and s["t_gpu_end_us"] > s["t_gpu_start_us"] > 0
+    a, b = st
+    assert a["t_gpu_start_us"] < b["t_gpu_end_us"] and b["t_gpu_start_us"] < a["t_gpu_end_us"]
+    for (img, sc, n), o in zip(jobs, outs):
+        assert torch.equal(o, _alone(img, sc, n))
+    srv.close()

@@ -434,6 +434,25 @@ def test_paper_equals_direct_definition_n2():
             assert Fr(S[y, x]) / mesh.denominator(C[y, x], 0) == exact[y, x]
 
 
+@pytest.mark.slow
+def test_paper_equals_direct_definition_n3():
+    """Order 3: algorithm == definition exactly at every pixel of a tiny image,
+    borders included, two scale vectors spread over it (the n-fold reading:
+    256 vertices, weights prod (-1)^j binom(3, j), ZP^{*3} interpolation)."""
+    rng = np.random.default_rng(31)
+    H, W = 5, 6
+    Q = 1
+    f = rng.integers(0, 256, (H, W))
+    choices = np.array([[2, 3, 2, 2], [3, 2, 2, 3]])
+    C = choices[rng.integers(0, 2, (H, W))]
+    S, s = paper.filter_image(f, C, 3, Q)
+    exact, sd = direct.filter_direct(f, C, 3, Q)
+    mesh = paper.Mesh(3, Q)
+    for y in range(H):
+        for x in range(W):
+            assert Fr(S[y, x]) / mesh.denominator(C[y, x], 0) == exact[y, x]
+
+
 def test_windowed_pixels_equal_global():
     """Per-pixel windows (used at large sizes) give the same exact numerators."""
     rng = np.random.default_rng(23)
@@ -488,6 +507,54 @@ def test_ellipse_rule_matches_covariance():
         ref = R @ np.diag([s * s * e, s * s / e]) @ R.T
         if min(c) > 1.0:
             assert np.allclose(cov, ref, rtol=1e-10, atol=1e-9)
+
+
+# Ellipses the four directions cannot represent (|C12| > min(C11, C22)): the
+# rule takes t = min(C11, C22) / 2 and sets negative u to 0.  Worked by hand
+# for sigma = 2, elongation 4 (eigenvalues 16 and 1) and the unit axis
+# (0.6, 0.8) or its reflections: cc = 0.36, ss = 0.64, cs = +-0.48, so
+# {C11, C22} = {6.4, 10.6}, |C12| = 7.2 > 6.4, t = 3.2, h = C12 / 2 = +-3.6 and
+# u = (C11 - 2t, t + h, C22 - 2t, t - h); every u <= 0 gives the clamp c = 1,
+# the others c = sqrt(12 u / n).
+_INFEASIBLE = [
+    # (cos, sin, u1, u2, u3, u4) before the clamp
+    (0.6, 0.8, 0.0, 6.8, 4.2, -0.4),
+    (0.8, 0.6, 4.2, 6.8, 0.0, -0.4),
+    (-0.6, 0.8, 0.0, -0.4, 4.2, 6.8),
+]
+
+
+@pytest.mark.parametrize("case", _INFEASIBLE)
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_ellipse_rule_infeasible_branch_by_hand(case, n):
+    ct, st, *u = case
+    c = scales.c_from_ellipse_scalar(2.0, 4.0, ct, st, n, 1e9)
+    want = [1.0 if uk <= 0 else math.sqrt(12.0 * uk / n) for uk in u]
+    assert np.allclose(c, want, rtol=1e-12, atol=0)
+    # the hand values solve the moment equations exactly before the clamp
+    C11 = 16 * ct * ct + st * st
+    C22 = 16 * st * st + ct * ct
+    C12 = 15 * ct * st
+    assert abs(u[0] + u[1] + u[3] - C11) < 1e-12 and abs(u[1] + u[2] + u[3] - C22) < 1e-12
+    assert abs(u[1] - u[3] - C12) < 1e-12
+    # on the kernel's covariance the clamps show up only as the added
+    # (n c^2 / 12) v v^T of the directions that were clamped
+    cov = np.zeros((2, 2))
+    for ck, v in zip(c, V):
+        cov += n * ck * ck / 12.0 * np.outer(v, v)
+    ref = np.array([[C11, C12], [C12, C22]])
+    for uk, ck, v in zip(u, c, V):
+        if uk <= 0:
+            ref += (n * ck * ck / 12.0 - uk) * np.outer(v, v)
+    assert np.allclose(cov, ref, rtol=0, atol=1e-9)
+
+
+def test_ellipse_rule_infeasible_branch_uses_the_smaller_diagonal():
+    """A slip to max(C11, C22), or to the midpoint of an empty family, moves
+    the steps: the hand case above gives these four steps only with the min."""
+    c = scales.c_from_ellipse_scalar(2.0, 4.0, 0.6, 0.8, 1, 1e9)
+    assert c[0] == 1.0 and c[3] == 1.0
+    assert abs(c[1] * c[1] - 81.6) < 1e-9 and abs(c[2] * c[2] - 50.4) < 1e-9
 
 
 def test_a4_steps_use_paper_diagonal_convention():
