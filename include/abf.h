@@ -63,10 +63,18 @@ typedef enum {
    * integer ZP^{*n} weights, integer numerator S; one binary64 division at the
    * end.  Bit-exact numerator.  Input must be integer after scaling by 2^F.  */
   ABF_FORM_EXACT = 0,
-  /* Plain: binary64 running sums restarted on a window around each output tile
-   * (the window holds every read of the tile's mesh), binary64 weights.      */
+  /* Plain: running sums restarted on a window around each output tile (the
+   * window holds every read of the tile's mesh), then the mesh, all in pairs
+   * of binary64 numbers (hi + lo, error-free TwoSum / TwoProd: unit roundoff
+   * about 2^-104).  Every pixel checks an a-priori bound on its error; where
+   * it exceeds 1e-12 times the plan's value bound the pixel is NaN and sets
+   * ABF_DEV_PRECISION.  Single binary64 cannot meet 1e-12: the mesh cancels
+   * the running sums by up to 1e13 (order 2, steps 1..150).               */
   ABF_FORM_PLAIN_F64 = 1,
-  /* Fast: as PLAIN_F64 but binary32 arithmetic, window-local re-centring.    */
+  /* As PLAIN_F64 in pairs of binary32 numbers (unit roundoff about 2^-46),
+   * tolerance 1e-5 times the value bound.  Order 1 only: at order 2 and 3
+   * the bound exceeds 1e-5 already for the smallest window that holds one
+   * pixel's reads at unit steps, so the plan returns ABF_ERR_UNSUPPORTED.  */
   ABF_FORM_TILE_F32 = 2
 } abf_form;
 
@@ -89,7 +97,8 @@ typedef struct {
   int32_t flags;              /* reserved, 0                                          */
   double max_scale;           /* upper bound on every step c_k (lattice units)        */
   double min_scale;           /* lower bound on c1 and c3 (>= 2^-Q); 0 means 1.0      */
-  double value_bound;         /* upper bound on |f|; 0 means the dtype's range        */
+  double value_bound;         /* upper bound on |f|; 0 means the dtype's range (u8,   *
+                               * u16 only: required for float inputs)                 */
   double max_scale_product;   /* upper bound on c1 c2 c3 c4; 0 means max_scale^4      */
 } abf_desc;
 
@@ -165,7 +174,10 @@ abf_status abf_integrate_noalloc(abf_plan plan, const void* d_f, size_t f_pitch,
 /* Adaptive step (Eq. (final_eqn)) for every pixel.
  *   exact form:      d_src = the integrated image from abf_integrate().
  *   PLAIN_F64 / TILE_F32: d_src = the image f itself (pitch f_pitch bytes);
- *                    the running sums are restarted per output tile.
+ *                    the running sums are restarted per output tile; d_ws is
+ *                    the plan's workspace (abf_plan_query); pixels whose
+ *                    error bound exceeds the form's tolerance get NaN and set
+ *                    ABF_DEV_PRECISION.
  *   d_scales : H rows of W float4 (desc.scale_kind), row pitch in bytes.
  *   d_s      : H rows of W desc.out_dtype, row pitch in bytes.
  * Pixels whose scales are invalid (non-finite, C_k = rint(c_k 2^Q) < 1 or
@@ -322,6 +334,8 @@ abf_status abf_plan_denominator(abf_plan plan, uint32_t* d_words4);
 #define ABF_DEV_RANGE       2   /* a pixel's numerator bound exceeded 64 L - 1 bits       */
 #define ABF_DEV_TIMEOUT     4   /* a bounded wait (scan look-back) ran out                 */
 #define ABF_DEV_BAD_INPUT   8   /* f 2^F not an integer within value_bound (exact form)   */
+#define ABF_DEV_PRECISION  16   /* floating-point forms: a pixel's error bound exceeded the
+                                   form's tolerance (the pixel is NaN)                     */
 abf_status abf_last_device_status(abf_plan plan, int32_t* code);
 
 const char* abf_status_str(abf_status s);

@@ -11,13 +11,14 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libabf.so")
 
-ABF_OK = 0
+ABF_OK, ABF_ERR_INVALID, ABF_ERR_OOM, ABF_ERR_CUDA, ABF_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+ABF_ERR_RANGE, ABF_ERR_TIMEOUT, ABF_ERR_BUSY = 5, 6, 7
 STATUS_NAMES = {0: "ABF_OK", 1: "ABF_ERR_INVALID", 2: "ABF_ERR_OOM", 3: "ABF_ERR_CUDA",
                 4: "ABF_ERR_UNSUPPORTED", 5: "ABF_ERR_RANGE", 6: "ABF_ERR_TIMEOUT", 7: "ABF_ERR_BUSY"}
 ABF_U8, ABF_U16, ABF_F32, ABF_F64 = 0, 1, 2, 3
 ABF_FORM_EXACT, ABF_FORM_PLAIN_F64, ABF_FORM_TILE_F32 = 0, 1, 2
 ABF_SCALES_C4, ABF_SCALES_A4, ABF_SCALES_ELLIPSE = 0, 1, 2
-ABF_DEV_BAD_SCALE, ABF_DEV_RANGE, ABF_DEV_TIMEOUT, ABF_DEV_BAD_INPUT = 1, 2, 4, 8
+ABF_DEV_BAD_SCALE, ABF_DEV_RANGE, ABF_DEV_TIMEOUT, ABF_DEV_BAD_INPUT, ABF_DEV_PRECISION = 1, 2, 4, 8, 16
 
 SCALE_KINDS = {"c4": ABF_SCALES_C4, "a4": ABF_SCALES_A4, "ellipse": ABF_SCALES_ELLIPSE}
 FORMS = {"exact": ABF_FORM_EXACT, "plain_f64": ABF_FORM_PLAIN_F64, "tile_f32": ABF_FORM_TILE_F32}

@@ -719,7 +719,9 @@ __device__ __forceinline__ int64_t convert_f(TIn raw, double scale, long long bo
 struct abf_plan_s {
   abf_desc desc;
   abf::PlanView pv;
-  void* real_table = nullptr;  // tile forms
+  void* real_table = nullptr;  // tile forms: pair weight table (D0 ZP^{*n})
+  double D0 = 0.0;             // tile forms: D = D0 2^((4n-2)P)
+  double tol_abs = 0.0;        // tile forms: error tolerance times the value bound
   unsigned __int128 D;
   int device;
   int32_t* d_status = nullptr;

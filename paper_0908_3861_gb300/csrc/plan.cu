@@ -56,8 +56,8 @@ cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* cou
 size_t tile_ws_bytes(const PlanView& pv, int real_bytes, int* slots_out, size_t* slot_elems_out, size_t* off_bmax,
                      size_t* off_tiles, size_t* off_cnt, size_t* off_scratch);
 cudaError_t run_tiles(const PlanView& pv, bool f64, const void* f, size_t f_pitch, const void* scales,
-                      size_t scale_pitch, void* s, size_t s_pitch, void* ws, const void* wtab, int32_t* status,
-                      cudaStream_t st);
+                      size_t scale_pitch, void* s, size_t s_pitch, void* ws, const void* wtab, double D0,
+                      double tol_abs, int32_t* status, cudaStream_t st);
 cudaError_t run_integrate_noalloc(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, uint32_t* epoch,
                                   int32_t* status, cudaStream_t st);
 }  // namespace abf
@@ -373,18 +373,32 @@ uint32_t reserve_epochs(uint32_t count) {
   }
 }
 
-// Floating-point copies of a weight table (D ZP^{*n} / D, rounded once), for
-// the tile forms; same row layout as the integer table.
-std::map<std::tuple<int, int, int, int>, void*> g_real_tables;  // (device, n, P, bytes); held until exit
+// Pair copies of a weight table for the floating-point forms: entry w (the
+// integer D ZP^{*n}) scaled by 2^-k, where D = D0 2^k with k = (4n - 2) P, as
+// hi + lo with hi = w rounded to p bits and lo = the rest rounded to p bits
+// (p = 53 or 24), both scaled by 2^-k (exact: a power of two).  The scaled
+// rows sum to D0.
+std::map<std::tuple<int, int, int, int>, std::pair<void*, double>> g_pair_tables;  // (device, n, P, bytes)
 
-double u128_to_double(u128 v);
+// v rounded to p significant bits, ties to even (an integer again).
+u128 round_bits(u128 v, int p) {
+  int b = 0;
+  for (u128 t = v; t; t >>= 1) ++b;
+  if (b <= p) return v;
+  const int sh = b - p;
+  const u128 q = v >> sh, rem = v & (((u128)1 << sh) - 1), half = (u128)1 << (sh - 1);
+  u128 r = q;
+  if (rem > half || (rem == half && (q & 1))) r += 1;
+  return r << sh;
+}
 
-abf_status get_real_table(int device, int n, int P, int real_bytes, void** out) {
+abf_status get_pair_table(int device, int n, int P, int real_bytes, void** out, double* D0_out) {
   std::lock_guard<std::mutex> lk(g_table_mu);
   auto key = std::make_tuple(device, n, P, real_bytes);
-  auto it = g_real_tables.find(key);
-  if (it != g_real_tables.end()) {
-    *out = it->second;
+  auto it = g_pair_tables.find(key);
+  if (it != g_pair_tables.end()) {
+    *out = it->second.first;
+    *D0_out = it->second.second;
     return ABF_OK;
   }
   HostTable ht;
@@ -393,15 +407,27 @@ abf_status get_real_table(int device, int n, int P, int real_bytes, void** out) 
   } catch (const std::bad_alloc&) {
     return ABF_ERR_OOM;
   }
+  const int k = (4 * n - 2) * P;
+  const u128 D0 = ht.D >> k;
+  if ((D0 << k) != ht.D) return ABF_ERR_UNSUPPORTED;
+  const int p = real_bytes == 8 ? 53 : 24;
   const size_t count = ht.bytes.size() / ht.wbytes;
-  std::vector<uint8_t> buf(count * real_bytes);
-  const double D = u128_to_double(ht.D);
+  std::vector<uint8_t> buf(count * 2 * real_bytes);
   for (size_t i = 0; i < count; ++i) {
     u128 w = 0;
     for (int b = 0; b < ht.wbytes; ++b) w |= (u128)ht.bytes[i * ht.wbytes + b] << (8 * b);
-    const double v = u128_to_double(w) / D;
-    if (real_bytes == 8) std::memcpy(&buf[i * 8], &v, 8);
-    else { const float fv = (float)v; std::memcpy(&buf[i * 4], &fv, 4); }
+    const u128 hi = round_bits(w, p);
+    const bool neg = hi > w;
+    const u128 lo = round_bits(neg ? hi - w : w - hi, p);
+    if (real_bytes == 8) {
+      const double h = std::ldexp((double)hi, -k), l = std::ldexp(neg ? -(double)lo : (double)lo, -k);
+      std::memcpy(&buf[i * 16], &h, 8);
+      std::memcpy(&buf[i * 16 + 8], &l, 8);
+    } else {
+      const float h = std::ldexp((float)hi, -k), l = std::ldexp(neg ? -(float)lo : (float)lo, -k);
+      std::memcpy(&buf[i * 8], &h, 4);
+      std::memcpy(&buf[i * 8 + 4], &l, 4);
+    }
   }
   void* d = nullptr;
   if (cudaMalloc(&d, buf.size()) != cudaSuccess) return ABF_ERR_OOM;
@@ -409,8 +435,10 @@ abf_status get_real_table(int device, int n, int P, int real_bytes, void** out) 
     cudaFree(d);
     return ABF_ERR_CUDA;
   }
-  g_real_tables[key] = d;
+  const double d0 = (double)(uint64_t)D0;
+  g_pair_tables[key] = std::make_pair(d, d0);
   *out = d;
+  *D0_out = d0;
   return ABF_OK;
 }
 
@@ -490,9 +518,10 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (!(vb > 0)) {
     if (d->in_dtype == ABF_U8) vb = 255.0;
     else if (d->in_dtype == ABF_U16) vb = 65535.0;
-    else if (exact) return ABF_ERR_INVALID;
-    else vb = 1.0;
+    else return ABF_ERR_INVALID;  // float input: the bound sizes the limbs / the error tolerance
   }
+  // binary32 pairs reach 1e-5 (times the value bound) at order 1 only: see abf.h
+  if (d->form == ABF_FORM_TILE_F32 && n != 1) return ABF_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
 
@@ -541,12 +570,13 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
     p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, n, nullptr, nullptr);
   } else {
     const int rb = d->form == ABF_FORM_PLAIN_F64 ? 8 : 4;
-    abf_status rs = get_real_table(dev, n, P, rb, &p->real_table);
+    abf_status rs = get_pair_table(dev, n, P, rb, &p->real_table, &p->D0);
     if (rs != ABF_OK) { delete p; return rs; }
+    p->tol_abs = (d->form == ABF_FORM_PLAIN_F64 ? 1e-12 : 1e-5) * vb;
     int slots;
     size_t se, o1, o2, o3, o4;
     p->g_bytes = 0;
-    p->ws_bytes = abf::tile_ws_bytes(pv, rb, &slots, &se, &o1, &o2, &o3, &o4);
+    p->ws_bytes = abf::tile_ws_bytes(pv, 2 * rb, &slots, &se, &o1, &o2, &o3, &o4);
   }
   if (cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) { delete p; return ABF_ERR_OOM; }
   if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
@@ -624,7 +654,8 @@ abf_status abf_filter(abf_plan p, const void* d_src, size_t src_pitch, const voi
     const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
     if (!d_ws || src_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
     return cuda_status(abf::run_tiles(p->pv, p->desc.form == ABF_FORM_PLAIN_F64, d_src, src_pitch, d_scales,
-                                      scale_pitch, d_s, s_pitch, d_ws, p->real_table, p->d_status, st));
+                                      scale_pitch, d_s, s_pitch, d_ws, p->real_table, p->D0, p->tol_abs,
+                                      p->d_status, st));
   }
   return abf::filter_with_status(p, d_src, d_scales, scale_pitch, d_s, s_pitch, p->d_status, st);
 }

@@ -168,3 +168,21 @@ def test_binding_signatures_match_the_header():
         args, _ = sigs[name]
         assert len(args) == len(plist), name
         assert [_c_kind(q) for q in plist] == [_ctypes_kind(a) for a in args], name
+
+
+def test_plan_refuses_forms_that_cannot_meet_their_tolerance(lib):
+    """Host-side checks of abf_plan_create that come before any device call:
+    binary32 pairs are refused beyond order 1 (their error bound exceeds 1e-5
+    of the value range there), and float inputs need a value bound (it sizes
+    the exact form's limbs and the floating-point forms' tolerance)."""
+    import ctypes
+    import torch
+    from paper_0908_3861_gb300 import _abf, make_desc
+    plan = ctypes.c_void_p()
+    for n in (2, 3):
+        d = make_desc(64, 64, n, torch.float32, form="tile_f32", q_bits=4, frac_bits=16, max_scale=8.0,
+                      value_bound=255.0)
+        assert lib.abf_plan_create(ctypes.byref(d), ctypes.byref(plan)) == _abf.ABF_ERR_UNSUPPORTED
+    for form in ("exact", "plain_f64", "tile_f32"):
+        d = make_desc(64, 64, 1, torch.float32, form=form, q_bits=4, frac_bits=16, max_scale=8.0, value_bound=0.0)
+        assert lib.abf_plan_create(ctypes.byref(d), ctypes.byref(plan)) == _abf.ABF_ERR_INVALID
