@@ -374,6 +374,8 @@ def run_ours(args):
             cb["all_cores_error"] = str(e)[:200]
         line["cpu_baseline"] = cb
         for k, v in forms.items():
+            if "out" not in v:
+                continue
             v["err_range_vs_oracle"] = err_range(v["out"], pts, vals, img)
             v["err_sample"] = "%d sampled pixels" % len(pts)
     for v in forms.values():

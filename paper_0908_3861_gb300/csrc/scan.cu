@@ -204,7 +204,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
 // published its inclusive state P, which enters as T_{dR}(P).
 
 constexpr int kBand = 32;         // rows per band
-constexpr int kLinesPerCta = 128; // lines per CTA (one per thread)
+// Lines per CTA (one per thread): the band is staged in shared memory,
+// kBand x lines x L limbs (64 KB at most).
+template <int L>
+__host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 128 : 64; }
+template <int L>
+__host__ __device__ constexpr int band_smem_bytes() { return kBand * lines_per_cta<L>() * L * 8; }
 constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;
 constexpr long long kSpinLimit = 1ll << 22;
 
@@ -272,10 +277,37 @@ __device__ __forceinline__ void st_store(uint64_t* p, const LineState<L, NF>& a)
   for (int k = 0; k < NF; ++k) wstore<L>(p + k * L, a.s[k]);
 }
 
+// Copy L limbs (8 * L bytes) from global to shared memory asynchronously, or
+// zeros when !ok (a zero-byte source read; the address stays a valid one).
+template <int L>
+__device__ __forceinline__ void cp_async_elem(uint64_t* dst, const uint64_t* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (L % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < L / 2; ++i)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d + 16 * i),
+                   "l"(__cvta_generic_to_global(src + 2 * i)), "r"(ok ? 16 : 0) : "memory");
+  } else {
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d + 8 * i),
+                   "l"(__cvta_generic_to_global(src + i)), "r"(ok ? 8 : 0) : "memory");
+  }
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// One CTA = one band of kBand rows x lines_per_cta<L>() consecutive lines.  The
+// band's elements are copied once into shared memory (each thread its own
+// line, cp.async, so the copies of all rows are in flight together); the band
+// aggregate, the decoupled look-back and the rescan then work from shared
+// memory, and g is written once: one read and one write of g per pass.
 template <int L, int DIR, int NF>
-__global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
-                                                                 LineWs ws, uint32_t epoch,
-                                                                 int32_t* status) {
+__global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
+                                                                       LineWs ws, uint32_t epoch,
+                                                                       int32_t* status) {
+  constexpr int LPC = lines_per_cta<L>();
+  extern __shared__ __align__(16) uint64_t s_band[];  // [kBand][LPC][L]
   __shared__ uint32_t s_ticket;
   if (threadIdx.x == 0) s_ticket = atomicAdd(ws.ticket, 1u);
   __syncthreads();
@@ -283,23 +315,27 @@ __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView 
   const int band = (int)(t / (uint32_t)ws.ngroups);
   const int grp = (int)(t % (uint32_t)ws.ngroups);
   if (band >= ws.nbands) return;
-  const int l = grp * kLinesPerCta + threadIdx.x;
+  const int l = grp * LPC + threadIdx.x;
   const bool line_ok = l < ws.nlines;
   const int y0 = band * kBand;
+  uint64_t* mine = s_band + (size_t)threadIdx.x * L;
+
+  // stage the band (zeros outside the box)
+#pragma unroll 8
+  for (int i = 0; i < kBand; ++i) {
+    const int y = y0 + i;
+    const int xi = line_col<DIR>(l, y, pv.Gh);
+    const bool ok = line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw;
+    const uint64_t* src = ok ? g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L : g;
+    cp_async_elem<L>(mine + (size_t)i * LPC * L, src, ok);
+  }
+  cp_async_wait_all();
 
   // band aggregate from a zero state
   LineState<L, NF> agg;
   st_zero<L, NF>(agg);
 #pragma unroll 8
-  for (int i = 0; i < kBand; ++i) {
-    const int y = y0 + i;
-    const int xi = line_col<DIR>(l, y, pv.Gh);
-    Wide<L> val;
-    wzero<L>(val);
-    if (line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw)
-      val = wload<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L);
-    st_step<L, NF>(agg, val);
-  }
+  for (int i = 0; i < kBand; ++i) st_step<L, NF>(agg, wload<L>(mine + (size_t)i * LPC * L));
 
   // decoupled look-back over the bands below (same line)
   LineState<L, NF> carry;
@@ -339,19 +375,15 @@ __global__ void __launch_bounds__(kLinesPerCta) line_scan_kernel(const PlanView 
     st_release(ws.flags + slot, (epoch << 2) | kFlagPrefix);
   }
 
-  // rescan the band from the carried state (the band's data is hot in cache)
+  // rescan the staged band from the carried state and write g
   LineState<L, NF> st = carry;
 #pragma unroll 8
   for (int i = 0; i < kBand; ++i) {
     const int y = y0 + i;
     const int xi = line_col<DIR>(l, y, pv.Gh);
     const bool ok = line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw;
-    Wide<L> val;
-    wzero<L>(val);
-    uint64_t* p = g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L;
-    if (ok) val = wload<L>(p);
-    st_step<L, NF>(st, val);
-    if (ok) wstore<L>(p, st.s[NF - 1]);
+    st_step<L, NF>(st, wload<L>(mine + (size_t)i * LPC * L));
+    if (ok) wstore<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L, st.s[NF - 1]);
   }
 }
 
@@ -410,7 +442,18 @@ static cudaError_t launch_lines(const PlanView& pv, uint64_t* g, const LineWs& w
   }
   if (e != cudaSuccess) return e;
   const int ctas = ws.nbands * ws.ngroups;
-  line_scan_kernel<L, DIR, NF><<<ctas, kLinesPerCta, 0, st>>>(pv, g, ws, epoch, status);
+  constexpr int smem = band_smem_bytes<L>();
+  // the shared-memory limit of this instantiation, set once per device before its first launch
+  static bool attr[64] = {};
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    e = cudaFuncSetAttribute(line_scan_kernel<L, DIR, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  line_scan_kernel<L, DIR, NF><<<ctas, lines_per_cta<L>(), smem, st>>>(pv, g, ws, epoch, status);
   return cudaGetLastError();
 }
 
@@ -439,7 +482,8 @@ size_t line_ws_zero_bytes(int Gw, int Gh) {
   return 256 + ((cells * 4 + 255) / 256) * 256;
 }
 
-static LineWs carve(void* ws, int Gw, int Gh, int L, int n, int DIR) {
+template <int L>
+static LineWs carve(void* ws, int Gw, int Gh, int n, int DIR) {
   LineWs w;
   int nbands, nlines_all;
   line_ws_bytes(Gw, Gh, L, n, &nbands, &nlines_all);
@@ -454,7 +498,7 @@ static LineWs carve(void* ws, int Gw, int Gh, int L, int n, int DIR) {
   w.pref = (uint64_t*)p;
   w.nbands = nbands;
   w.nlines = nlines_all;  // slot stride, the same for every direction
-  w.ngroups = ((DIR == 3 ? Gw : Gw + Gh - 1) + kLinesPerCta - 1) / kLinesPerCta;
+  w.ngroups = ((DIR == 3 ? Gw : Gw + Gh - 1) + lines_per_cta<L>() - 1) / lines_per_cta<L>();
   return w;
 }
 
@@ -464,7 +508,7 @@ static cudaError_t lines_NF(const PlanView& pv, uint64_t* g, void* ws, uint32_t*
   cudaError_t e = cudaSuccess;
   for (int dir = 2; dir <= 4 && e == cudaSuccess; ++dir) {
     const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
-    const LineWs w = carve(ws, pv.Gw, pv.Gh, L, NF, dir);
+    const LineWs w = carve<L>(ws, pv.Gw, pv.Gh, NF, dir);
     if (dir == 2) e = launch_lines<L, 2, NF>(pv, g, w, ep, status, st);
     else if (dir == 3) e = launch_lines<L, 3, NF>(pv, g, w, ep, status, st);
     else e = launch_lines<L, 4, NF>(pv, g, w, ep, status, st);
@@ -497,7 +541,7 @@ template <int L, int NF>
 static cudaError_t starved_NF(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
                               cudaStream_t st) {
   const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
-  const LineWs w = carve(ws, pv.Gw, pv.Gh, L, NF, 3);
+  const LineWs w = carve<L>(ws, pv.Gw, pv.Gh, NF, 3);
   return launch_lines<L, 3, NF>(pv, g, w, ep, status, st, (uint32_t)w.ngroups);
 }
 

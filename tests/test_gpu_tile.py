@@ -67,9 +67,9 @@ def test_plain_f64_within_1e12_every_pixel(n, shape, q, hi):
 
 def test_plain_f64_within_1e12_on_the_ellipse_recipe():
     """The order-2 ellipse workload's recipe (f32 on the 2^-16 grid, sigma up
-    to 24, elongation up to 6, steps up to 150) at 384 x 320: sampled pixels
-    (the oracle evaluates each on its own window), including every pixel of
-    the first and last rows and columns' corners and a band of the middle."""
+    to 24, elongation up to 6, steps up to 150) at 384 x 320: 120 random
+    pixels, the four corners and every 16th pixel of the middle row (the
+    oracle evaluates each on its own window)."""
     w = synthetic.workload("c2", shape=(384, 320))
     img = w["image"]
     H, W = img.shape
@@ -106,15 +106,15 @@ def test_tile_f32_within_1e5_where_its_bound_holds():
 
 
 def test_precision_flag_marks_pixels_the_bound_cannot_cover():
-    """Unit steps everywhere except one pixel with a long first step: its 8 x 8
-    tile gets a wide window, so the unit-step pixels there have a binary32-pair
-    bound far above 1e-5 and are NaN with ABF_DEV_PRECISION; binary64 pairs
-    cover them (bound ~1e-25) and stay within 1e-12 everywhere."""
+    """Unit steps everywhere except one pixel with steps of 60: its 8 x 8 tile
+    gets a window of about 190 x 190, so the unit-step pixels there have a
+    binary32-pair bound far above 1e-5 and are NaN with ABF_DEV_PRECISION;
+    binary64 pairs cover them (bound ~1e-17) and stay within 1e-12 everywhere."""
     rng = np.random.default_rng(51)
     shape = (24, 40)
     img = rng.integers(0, 256, shape).astype(np.float64)
     sc = np.ones(shape + (4,), dtype=np.float32)
-    sc[3, 3, 0] = 60.0
+    sc[3, 3, :] = 60.0
     w = dict(image=img, frac_bits=0, scale_kind="c4", scales=sc, n=1, q_bits=4, cmax=64.0, value_bound=255.0)
     C = gu.oracle_C(w)
     _, s_ref = paper.filter_image(img.astype(np.int64), C, 1, 4, 0)
