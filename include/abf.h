@@ -195,6 +195,34 @@ abf_status abf_filter_numerator(abf_plan plan, const void* d_g, const void* d_sc
                                 size_t scale_pitch, void* d_num, size_t num_pitch, void* d_ws,
                                 cudaStream_t stream);
 
+/* One image of a batched non-adaptive step: its (exact-form) plan, image,
+ * integrated image and workspace, exactly as the arguments of abf_integrate. */
+typedef struct {
+  abf_plan plan;
+  const void* d_f;
+  size_t f_pitch;
+  void* d_g;
+  void* d_ws;
+} abf_integrate_job;
+
+/* Non-adaptive step (Sec. 7 (1), Eq. (RS)) of many images of uneven size,
+ * order, limbs and input type: the images of one (limbs, order, input type)
+ * group share one row-pass launch (a CTA per row of any of them) and one
+ * launch per line direction (v2, v3, v4) whose CTAs take bands of any image
+ * from one ticket counter, image by image and band by band within an image.
+ * Every image's integrated image is bit-identical to abf_integrate on it
+ * alone.  One extra launch clears all images' look-back flags first.
+ *   jobs  : njobs entries (host memory, read during the call); each image's
+ *           d_ws is its own plan workspace, as for abf_integrate, and must not
+ *           be shared with a call that overlaps on the GPU.
+ *   d_ws  : at least 256 bytes of device memory (the ticket counters).
+ * Batches of more than abf_integrate_batch_max_jobs() images are split into
+ * several calls' worth of launches.  Device errors go to each image's plan
+ * status word.                                                              */
+abf_status abf_integrate_batch(const abf_integrate_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes,
+                               cudaStream_t stream);
+int32_t abf_integrate_batch_max_jobs(void);
+
 /* One image of a batch: its (exact-form) plan, its integrated image from
  * abf_integrate, its scale field and its output (as for abf_filter).        */
 typedef struct {
@@ -207,11 +235,12 @@ typedef struct {
 } abf_job;
 
 /* Adaptive step (Eq. (final_eqn)) for many images of uneven size, order and
- * limb count in one persistent launch per (order n, limbs) present: the images' units
- * (8 rows x 32 columns) are numbered (largest images first) and every CTA
- * takes the next unit from a device counter, so the work stays balanced
- * across SMs.  Each image's result is bit-identical to abf_filter on that
- * image alone.
+ * limb count in one persistent launch per (order n, limbs) present: the
+ * images' row runs (32 pixels of one row) are numbered (largest images first,
+ * within an image band by band and strip by strip) and every warp takes the
+ * next run from a device counter on its own, so the work stays balanced
+ * across SMs with no barrier between runs.  Each image's result is
+ * bit-identical to abf_filter on that image alone.
  *   jobs  : njobs entries (host memory, read during the call), every plan of
  *           the exact form; up to abf_batch_max_jobs() per call (larger
  *           batches are split into several launches).

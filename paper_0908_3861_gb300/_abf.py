@@ -30,6 +30,11 @@ class AbfError(RuntimeError):
         super().__init__("%s: %s" % (where, STATUS_NAMES.get(status, status)))
 
 
+class abf_integrate_job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_f", ctypes.c_void_p), ("f_pitch", ctypes.c_size_t),
+                ("d_g", ctypes.c_void_p), ("d_ws", ctypes.c_void_p)]
+
+
 class abf_job(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("d_g", ctypes.c_void_p), ("d_scales", ctypes.c_void_p),
                 ("scale_pitch", ctypes.c_size_t), ("d_s", ctypes.c_void_p), ("s_pitch", ctypes.c_size_t)]
@@ -89,6 +94,8 @@ def signatures():
         "abf_measure_scales": ([P(abf_desc), vp, sz, P(ctypes.c_double), P(ctypes.c_double), vp], st),
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
+        "abf_integrate_batch": ([P(abf_integrate_job), i32, vp, sz, vp], st),
+        "abf_integrate_batch_max_jobs": ([], i32),
         "abf_batch_max_jobs": ([], i32),
         "abf_plan_autotune": ([vp, vp, vp, sz, vp, sz, vp, P(i32), P(ctypes.c_float)], st),
         "abf_batch_autotune": ([P(abf_job), i32, vp, sz, vp, P(i32), P(ctypes.c_float)], st),
@@ -230,6 +237,17 @@ def abf_weight_table_host(n, q_bits):
     buf = ctypes.create_string_buffer(need.value)
     _check(lib().abf_weight_table_host(n, q_bits, buf, need.value, None, None, None), "abf_weight_table_host")
     return buf.raw, wb.value, sum(int(d[i]) << (32 * i) for i in range(4))
+
+
+def abf_integrate_batch(jobs, ws, stream=None):
+    """jobs: list of abf_integrate_job structures."""
+    arr = (abf_integrate_job * len(jobs))(*jobs)
+    _check(lib().abf_integrate_batch(arr, len(jobs), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "abf_integrate_batch")
+
+
+def abf_integrate_batch_max_jobs():
+    return lib().abf_integrate_batch_max_jobs()
 
 
 def abf_filter_batch(jobs, ws, stream=None):

@@ -612,34 +612,38 @@ __device__ __forceinline__ void batch_dispatch_L(const BatchJob& jb, int y, int 
                        sdx, sdy, order, soff, perm);
 }
 
-// A unit is the 32-column runs of blockDim.x / 32 consecutive rows of one image
-// (one per warp of the CTA, as in the single-image launch); CTAs take units from a
-// global counter.  One kernel per order n, so that each gets its own register
-// budget; the images of one launch share n and differ in size and limbs.
+// Work items are single warps' runs: 32 columns of one row of one image.
+// Every warp takes its next item from a global counter on its own, so a warp
+// that finishes early starts its next run at once (no CTA-wide barrier between
+// items).  Items are numbered per image band by band (a band = `rows` rows),
+// within a band strip by strip, within a strip row by row: the warps of a CTA,
+// taking consecutive items, work on nearby rows of one 32-column strip, whose g
+// patches meet in L1 as in the single-image launch.  One kernel per order n,
+// so that each gets its own register budget; the images of one launch share n
+// and limbs and differ in size.
 template <int N, int L, bool FAST>
-__device__ __forceinline__ void mesh_batch_body(const BatchJobs& jobs, unsigned long long* counter) {
+__device__ __forceinline__ void mesh_batch_body(const BatchJobs& jobs, unsigned long long* counter, int rows) {
   constexpr int R = stencil_count<N>();
   constexpr int TAPS = (N + 1) * (N + 1) * (N + 1) * (N + 1);
-  __shared__ int s_dx[R], s_dy[R], s_off[R];
+  __shared__ int s_dx[R], s_dy[R];
+  __shared__ int s_offw[(FAST && N == 3) ? kMeshWarpsMax : 1][R];
   __shared__ unsigned char s_order[TAPS], s_perm[8 * R];
   extern __shared__ int4 s_tap[];
-  __shared__ unsigned long long s_item;
   if (threadIdx.x == 0) {
     fill_stencil<N>(s_dx, s_dy);
     if constexpr (FAST && N == 2) fill_n2_order(s_order);
     if constexpr (FAST && N == 3) fill_n3_order(s_order);
   }
-  if constexpr (FAST && N == 3) {
-    __syncthreads();
-    fill_n3_perm(s_perm, s_dx, s_dy);
-  }
-  const int warp = threadIdx.x >> 5, rows = blockDim.x >> 5;
+  __syncthreads();
+  if constexpr (FAST && N == 3) fill_n3_perm(s_perm, s_dx, s_dy);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int4* taps = s_tap + warp * TAPS;
+  int* s_off = s_offw[(FAST && N == 3) ? warp : 0];
+  int last_job = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
-    __syncthreads();
-    const unsigned long long item = s_item;
-    __syncthreads();
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
     if ((long long)item >= jobs.total_units) break;
     int lo = 0, hi = jobs.njobs - 1;  // last job with units_begin <= item
     while (lo < hi) {
@@ -648,27 +652,33 @@ __device__ __forceinline__ void mesh_batch_body(const BatchJobs& jobs, unsigned 
       else hi = mid - 1;
     }
     const BatchJob& jb = jobs.job[lo];
-    if (threadIdx.x < R) s_off[threadIdx.x] = s_dy[threadIdx.x] * (int)jb.pv.Gp + s_dx[threadIdx.x];
-    __syncthreads();
+    if (FAST && N == 3 && lo != last_job) {
+      __syncwarp();
+      for (int c = lane; c < R; c += 32) s_off[c] = s_dy[c] * (int)jb.pv.Gp + s_dx[c];
+      __syncwarp();
+      last_job = lo;
+    }
     const long long u = (long long)item - jb.units_begin;
-    const int band = (int)(u / jb.segs);
-    const int y = band * rows + warp;
-    const int x0 = (int)(u - (long long)band * jb.segs) * 32;
+    const long long per_band = (long long)jb.segs * rows;
+    const int band = (int)(u / per_band);
+    const int rem = (int)(u - (long long)band * per_band);
+    const int strip = rem / rows;
+    const int y = band * rows + (rem - strip * rows);
     if (y >= jb.pv.H) continue;
-    batch_dispatch_L<N, L, FAST>(jb, y, x0, taps, s_dx, s_dy, s_order, s_off, s_perm);
+    batch_dispatch_L<N, L, FAST>(jb, y, strip * 32, taps, s_dx, s_dy, s_order, s_off, s_perm);
   }
 }
 
 template <int N, int L, bool FAST>
 __global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_batch_kernel(const __grid_constant__ BatchJobs jobs,
-                                                                        unsigned long long* counter) {
-  mesh_batch_body<N, L, FAST>(jobs, counter);
+                                                                        unsigned long long* counter, int rows) {
+  mesh_batch_body<N, L, FAST>(jobs, counter, rows);
 }
 
 template <int L, bool FAST>
 __global__ void __launch_bounds__(32 * mesh_max_warps(3), mesh_min_ctas(3)) mesh_batch_kernel3(
-    const __grid_constant__ BatchJobs jobs, unsigned long long* counter) {
-  mesh_batch_body<3, L, FAST>(jobs, counter);
+    const __grid_constant__ BatchJobs jobs, unsigned long long* counter, int rows) {
+  mesh_batch_body<3, L, FAST>(jobs, counter, rows);
 }
 
 __global__ void prepare_scales_kernel(const PlanView pv, const float4* __restrict__ scales, size_t scale_pitch,
@@ -823,7 +833,7 @@ static cudaError_t launch_batch_NL(const BatchJobs& jobs, unsigned long long* co
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);
     if (per_sm < 1) per_sm = 1;
-    kernel<<<sms * per_sm, 32 * warps, smem, st>>>(jobs, counter);
+    kernel<<<sms * per_sm, 32 * warps, smem, st>>>(jobs, counter, warps);
     return cudaGetLastError();
   };
   if constexpr (N == 3) return go(mesh_batch_kernel3<L, FAST>);
@@ -878,7 +888,7 @@ cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* cou
           jb.status = b.status;
           jb.segs = (b.pv.W + 31) / 32;
           jb.units_begin = units;
-          units += (long long)jb.segs * ((b.pv.H + wn - 1) / wn);
+          units += (long long)jb.segs * ((b.pv.H + wn - 1) / wn) * wn;  // one item per row run
         }
         jobs.total_units = units;
         unsigned long long* ctr = counter + launch++;

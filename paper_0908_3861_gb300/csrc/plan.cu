@@ -60,6 +60,16 @@ cudaError_t run_tiles(const PlanView& pv, bool f64, const void* f, size_t f_pitc
                       double tol_abs, int32_t* status, cudaStream_t st);
 cudaError_t run_integrate_noalloc(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, uint32_t* epoch,
                                   int32_t* status, cudaStream_t st);
+struct IntIn {
+  PlanView pv;
+  const void* f;
+  size_t f_pitch;
+  uint64_t* g;
+  void* ws;
+  int32_t* status;
+};
+int integrate_batch_max_jobs();
+cudaError_t run_integrate_batch(const IntIn* in, int njobs, uint32_t* ws, uint32_t epoch0, cudaStream_t st);
 }  // namespace abf
 
 using u128 = unsigned __int128;
@@ -754,6 +764,32 @@ static abf_status tune_warps(F fn, cudaStream_t st, int* best, float* ms) {
 }
 
 extern "C" {
+
+abf_status abf_integrate_batch(const abf_integrate_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes,
+                               cudaStream_t st) {
+  if (!jobs || njobs < 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
+  if (njobs == 0) return ABF_OK;
+  std::vector<abf::IntIn> in((size_t)njobs);
+  for (int i = 0; i < njobs; ++i) {
+    const abf_integrate_job& j = jobs[i];
+    abf_plan p = j.plan;
+    if (!p || !j.d_f || !j.d_g || !j.d_ws) return ABF_ERR_INVALID;
+    if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+    const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
+    if (j.f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
+    if (((uintptr_t)j.d_g & 15) || ((uintptr_t)j.d_ws & 15)) return ABF_ERR_INVALID;
+    in[i] = abf::IntIn{p->pv, j.d_f, j.f_pitch, (uint64_t*)j.d_g, j.d_ws, p->d_status};
+  }
+  const int chunk = abf::integrate_batch_max_jobs();
+  for (int b = 0; b < njobs; b += chunk) {
+    const int k = std::min(chunk, njobs - b);
+    const uint32_t ep = reserve_epochs(3u * (uint32_t)k);
+    if (abf::run_integrate_batch(in.data() + b, k, (uint32_t*)d_ws, ep, st) != cudaSuccess) return ABF_ERR_CUDA;
+  }
+  return ABF_OK;
+}
+
+int32_t abf_integrate_batch_max_jobs(void) { return abf::integrate_batch_max_jobs(); }
 
 abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t st) {
   if (!jobs || njobs < 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;

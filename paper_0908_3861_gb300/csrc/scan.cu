@@ -139,13 +139,11 @@ __device__ __forceinline__ void row_chunk(const PlanView& pv, const TIn (&raw)[k
 // rescans its segment from its incoming state and stores g.  f is read
 // twice; g is written once.
 template <int L, typename TIn, int NF>
-__global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView pv, const TIn* __restrict__ f,
-                                                                  size_t f_pitch, uint64_t* __restrict__ g,
-                                                                  int32_t* status) {
+__device__ __forceinline__ void row_scan_body(const PlanView& pv, const TIn* __restrict__ f, size_t f_pitch,
+                                              uint64_t* __restrict__ g, int32_t* status, int y) {
   __shared__ Wide<L> s_agg[kRowWarps][NF];
   __shared__ Wide<L> s_tile[kRowWarps][32 * kRowVec];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int y = blockIdx.x;
   const double scale = ldexp(1.0, pv.F);
   const double bd = floor(pv.value_bound * scale);
   const long long bound = bd < 4.0e18 ? (long long)bd : 4000000000000000000ll;
@@ -194,6 +192,13 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
   }
 }
 
+template <int L, typename TIn, int NF>
+__global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView pv, const TIn* __restrict__ f,
+                                                                  size_t f_pitch, uint64_t* __restrict__ g,
+                                                                  int32_t* status) {
+  row_scan_body<L, TIn, NF>(pv, f, f_pitch, g, status, blockIdx.x);
+}
+
 // ---------------------------------------------------------- lines (v2, v3, v4)
 // One pass per direction carries all n cascaded running sums: per line a state
 // (s_1..s_n), updated per element x as s_1 += x, s_2 += s_1, ..., out = s_n.
@@ -205,9 +210,10 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
 
 constexpr int kBand = 32;         // rows per band
 // Lines per CTA (one per thread): the band is staged in shared memory,
-// kBand x lines x L limbs (64 KB at most).
+// kBand x lines x L limbs (32 KB at most, so that several CTAs per SM keep
+// their copies in flight while others wait in the look-back).
 template <int L>
-__host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 128 : 64; }
+__host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 64 : 32; }
 template <int L>
 __host__ __device__ constexpr int band_smem_bytes() { return kBand * lines_per_cta<L>() * L * 8; }
 constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;
@@ -303,18 +309,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // aggregate, the decoupled look-back and the rescan then work from shared
 // memory, and g is written once: one read and one write of g per pass.
 template <int L, int DIR, int NF>
-__global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
-                                                                       LineWs ws, uint32_t epoch,
-                                                                       int32_t* status) {
+__device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __restrict__ g, const LineWs& ws,
+                                               uint32_t epoch, int32_t* status, int band, int grp) {
   constexpr int LPC = lines_per_cta<L>();
   extern __shared__ __align__(16) uint64_t s_band[];  // [kBand][LPC][L]
-  __shared__ uint32_t s_ticket;
-  if (threadIdx.x == 0) s_ticket = atomicAdd(ws.ticket, 1u);
-  __syncthreads();
-  const uint32_t t = s_ticket;
-  const int band = (int)(t / (uint32_t)ws.ngroups);
-  const int grp = (int)(t % (uint32_t)ws.ngroups);
-  if (band >= ws.nbands) return;
   const int l = grp * LPC + threadIdx.x;
   const bool line_ok = l < ws.nlines;
   const int y0 = band * kBand;
@@ -385,6 +383,22 @@ __global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const Pla
     st_step<L, NF>(st, wload<L>(mine + (size_t)i * LPC * L));
     if (ok) wstore<L>(g + ((size_t)y * (size_t)pv.Gp + (size_t)xi) * L, st.s[NF - 1]);
   }
+}
+
+// Bands are taken in ticket order, so every band a look-back waits on belongs
+// to a CTA that started earlier.
+template <int L, int DIR, int NF>
+__global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
+                                                                       LineWs ws, uint32_t epoch,
+                                                                       int32_t* status) {
+  __shared__ uint32_t s_ticket;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(ws.ticket, 1u);
+  __syncthreads();
+  const uint32_t t = s_ticket;
+  const int band = (int)(t / (uint32_t)ws.ngroups);
+  const int grp = (int)(t % (uint32_t)ws.ngroups);
+  if (band >= ws.nbands) return;
+  line_scan_body<L, DIR, NF>(pv, g, ws, epoch, status, band, grp);
 }
 
 // ----------------------------------------------------------------- launchers
@@ -583,6 +597,212 @@ cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uin
   const cudaError_t e = cudaMemsetAsync(ws, 0, line_ws_zero_bytes(pv.Gw, pv.Gh), st);
   if (e != cudaSuccess) return e;
   return integrate_cleared(pv, f, f_pitch, g, ws, epoch, status, st);
+}
+
+// ----------------------------------------------------------------- batches
+// The non-adaptive step of many images in one launch per pass: the images
+// of one (limbs, order, input type) group share a row-pass launch (one CTA per
+// row of any image) and one launch per line direction (every CTA takes a
+// ticket; tickets run image by image and, within an image, band by band, so a
+// look-back only waits on bands of its own image that hold earlier tickets).
+// Each image keeps its own look-back workspace; all of them are cleared by one
+// launch at the start.
+constexpr int kMaxIntBatch = 96;
+
+struct IntIn {
+  PlanView pv;
+  const void* f;
+  size_t f_pitch;
+  uint64_t* g;
+  void* ws;
+  int32_t* status;
+};
+
+struct IntJob {
+  PlanView pv;
+  const void* f;
+  size_t f_pitch;
+  uint64_t* g;
+  LineWs ws;
+  int32_t* status;
+  long long first;  // first row (row pass) or ticket (line pass) of this image
+};
+
+struct IntJobs {
+  int njobs;
+  long long total;
+  IntJob job[kMaxIntBatch];
+};
+static_assert(sizeof(IntJobs) <= 32000, "kernel parameter space");
+
+struct ClearJobs {
+  int n;
+  uint4* ptr[kMaxIntBatch + 1];
+  unsigned int words[kMaxIntBatch + 1];  // 16-byte words to clear
+};
+
+__global__ void clear_batch_kernel(const __grid_constant__ ClearJobs cj) {
+  const int j = blockIdx.y;
+  if (j >= cj.n) return;
+  uint4* p = cj.ptr[j];
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < cj.words[j]; i += gridDim.x * blockDim.x)
+    p[i] = make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ int find_int_job(const IntJobs& jobs, long long item) {
+  int lo = 0, hi = jobs.njobs - 1;  // last job with first <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs.job[mid].first <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int L, typename TIn, int NF>
+__global__ void __launch_bounds__(32 * kRowWarps) row_scan_batch_kernel(const __grid_constant__ IntJobs jobs) {
+  const long long b = blockIdx.x;
+  const IntJob& jb = jobs.job[find_int_job(jobs, b)];
+  row_scan_body<L, TIn, NF>(jb.pv, (const TIn*)jb.f, jb.f_pitch, jb.g, jb.status, (int)(b - jb.first));
+}
+
+template <int L, int DIR, int NF>
+__global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_batch_kernel(const __grid_constant__ IntJobs jobs,
+                                                                             uint32_t* ticket, uint32_t epoch) {
+  __shared__ uint32_t s_ticket;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const long long t = s_ticket;
+  if (t >= jobs.total) return;
+  const IntJob& jb = jobs.job[find_int_job(jobs, t)];
+  const long long u = t - jb.first;
+  const int band = (int)(u / jb.ws.ngroups), grp = (int)(u % jb.ws.ngroups);
+  line_scan_body<L, DIR, NF>(jb.pv, jb.g, jb.ws, epoch, jb.status, band, grp);
+}
+
+template <int L, int DIR, int NF>
+static cudaError_t launch_lines_batch(const IntIn* in, const int* idx, int m, uint32_t* ticket, uint32_t epoch,
+                                      cudaStream_t st) {
+  IntJobs jobs;
+  jobs.njobs = m;
+  long long t = 0;
+  for (int k = 0; k < m; ++k) {
+    const IntIn& b = in[idx[k]];
+    IntJob& jb = jobs.job[k];
+    jb.pv = b.pv;
+    jb.f = b.f;
+    jb.f_pitch = b.f_pitch;
+    jb.g = b.g;
+    jb.ws = carve<L>(b.ws, b.pv.Gw, b.pv.Gh, NF, DIR);
+    jb.status = b.status;
+    jb.first = t;
+    t += (long long)jb.ws.nbands * jb.ws.ngroups;
+  }
+  jobs.total = t;
+  if (t >= (1ll << 31)) return cudaErrorInvalidValue;
+  constexpr int smem = band_smem_bytes<L>();
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    e = cudaFuncSetAttribute(line_scan_batch_kernel<L, DIR, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  line_scan_batch_kernel<L, DIR, NF><<<(unsigned)t, lines_per_cta<L>(), smem, st>>>(jobs, ticket, epoch);
+  return cudaGetLastError();
+}
+
+template <int L, typename TIn, int NF>
+static cudaError_t integrate_group(const IntIn* in, const int* idx, int m, uint32_t* tickets, uint32_t epoch0,
+                                   cudaStream_t st) {
+  IntJobs jobs;
+  jobs.njobs = m;
+  long long rows = 0;
+  for (int k = 0; k < m; ++k) {
+    const IntIn& b = in[idx[k]];
+    IntJob& jb = jobs.job[k];
+    jb.pv = b.pv;
+    jb.f = b.f;
+    jb.f_pitch = b.f_pitch;
+    jb.g = b.g;
+    jb.status = b.status;
+    jb.first = rows;
+    rows += b.pv.Gh;
+  }
+  jobs.total = rows;
+  if (rows >= (1ll << 31)) return cudaErrorInvalidValue;
+  row_scan_batch_kernel<L, TIn, NF><<<(unsigned)rows, 32 * kRowWarps, 0, st>>>(jobs);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_lines_batch<L, 2, NF>(in, idx, m, tickets + 0, epoch0 + 1, st);
+  if (e == cudaSuccess) e = launch_lines_batch<L, 3, NF>(in, idx, m, tickets + 1, epoch0 + 2, st);
+  if (e == cudaSuccess) e = launch_lines_batch<L, 4, NF>(in, idx, m, tickets + 2, epoch0 + 3, st);
+  return e;
+}
+
+template <int L, typename TIn>
+static cudaError_t integrate_group_n(int n, const IntIn* in, const int* idx, int m, uint32_t* tickets,
+                                     uint32_t epoch0, cudaStream_t st) {
+  if (n == 1) return integrate_group<L, TIn, 1>(in, idx, m, tickets, epoch0, st);
+  if (n == 2) return integrate_group<L, TIn, 2>(in, idx, m, tickets, epoch0, st);
+  return integrate_group<L, TIn, 3>(in, idx, m, tickets, epoch0, st);
+}
+
+template <int L>
+static cudaError_t integrate_group_L(int n, int dtype, const IntIn* in, const int* idx, int m, uint32_t* tickets,
+                                     uint32_t epoch0, cudaStream_t st) {
+  switch (dtype) {
+    case ABF_U8: return integrate_group_n<L, uint8_t>(n, in, idx, m, tickets, epoch0, st);
+    case ABF_U16: return integrate_group_n<L, uint16_t>(n, in, idx, m, tickets, epoch0, st);
+    case ABF_F32: return integrate_group_n<L, float>(n, in, idx, m, tickets, epoch0, st);
+    default: return integrate_group_n<L, double>(n, in, idx, m, tickets, epoch0, st);
+  }
+}
+
+int integrate_batch_max_jobs() { return kMaxIntBatch; }
+
+// njobs <= kMaxIntBatch; ws: 256 bytes of device memory (ticket counters, one per
+// pass, cleared here); epoch0: the first of 3 x (number of groups) epochs
+// reserved for this call.
+cudaError_t run_integrate_batch(const IntIn* in, int njobs, uint32_t* ws, uint32_t epoch0, cudaStream_t st) {
+  if (njobs < 1 || njobs > kMaxIntBatch) return cudaErrorInvalidValue;
+  ClearJobs cj;
+  cj.n = njobs + 1;
+  unsigned int most = 16;
+  for (int i = 0; i < njobs; ++i) {
+    cj.ptr[i] = (uint4*)in[i].ws;
+    cj.words[i] = (unsigned int)(line_ws_zero_bytes(in[i].pv.Gw, in[i].pv.Gh) / 16);
+    most = most > cj.words[i] ? most : cj.words[i];
+  }
+  cj.ptr[njobs] = (uint4*)ws;
+  cj.words[njobs] = 16;
+  const unsigned gx = (most + 255) / 256 < 64 ? (most + 255) / 256 : 64;
+  clear_batch_kernel<<<dim3(gx, njobs + 1), 256, 0, st>>>(cj);
+  cudaError_t e = cudaGetLastError();
+  int done[kMaxIntBatch] = {};
+  int group = 0;
+  for (int i = 0; i < njobs && e == cudaSuccess; ++i) {
+    if (done[i]) continue;
+    int idx[kMaxIntBatch], m = 0;
+    for (int k = i; k < njobs; ++k)
+      if (!done[k] && in[k].pv.limbs == in[i].pv.limbs && in[k].pv.n == in[i].pv.n &&
+          in[k].pv.in_dtype == in[i].pv.in_dtype) {
+        idx[m++] = k;
+        done[k] = 1;
+      }
+    if (group >= 20) return cudaErrorInvalidValue;  // 3 counters per group in 64
+    uint32_t* tickets = ws + 3 * group;
+    const uint32_t ep = epoch0 + 3 * (uint32_t)group;
+    ++group;
+    switch (in[i].pv.limbs) {
+      case 1: e = integrate_group_L<1>(in[i].pv.n, in[i].pv.in_dtype, in, idx, m, tickets, ep, st); break;
+      case 2: e = integrate_group_L<2>(in[i].pv.n, in[i].pv.in_dtype, in, idx, m, tickets, ep, st); break;
+      case 3: e = integrate_group_L<3>(in[i].pv.n, in[i].pv.in_dtype, in, idx, m, tickets, ep, st); break;
+      default: e = integrate_group_L<4>(in[i].pv.n, in[i].pv.in_dtype, in, idx, m, tickets, ep, st); break;
+    }
+  }
+  return e;
 }
 
 // ------------------------------------------------------ fixed-scratch variant

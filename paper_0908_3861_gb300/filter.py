@@ -120,19 +120,28 @@ class AdaptiveFilter:
 
 
 class Batch:
-    """Many exact-form filters run as one batch: each image's non-adaptive
-    step (abf_integrate), then one persistent launch of the adaptive step
-    over all images (abf_filter_batch)."""
+    """Many exact-form filters run as one batch: the non-adaptive step of all
+    images in one launch per pass and (limbs, order, input type) group
+    (abf_integrate_batch), then one persistent launch of the adaptive step per
+    (order, limbs) group over all images (abf_filter_batch)."""
 
     def __init__(self, filters, device=None):
         self.filters = list(filters)
         self.device = torch.device(device or "cuda")
         self.ws = torch.zeros(256, dtype=torch.uint8, device=self.device)
+        self.ws_int = torch.zeros(256, dtype=torch.uint8, device=self.device)
+
+    def integrate(self, images, stream=None):
+        jobs = []
+        for flt, f in zip(self.filters, images):
+            jobs.append(C.abf_integrate_job(flt.plan.value, f.data_ptr(), flt._check_f(f), flt.g.data_ptr(),
+                                            flt.ws.data_ptr()))
+        C.abf_integrate_batch(jobs, self.ws_int, stream)
 
     def __call__(self, images, scales, outs, stream=None):
+        self.integrate(images, stream)
         jobs = []
-        for flt, f, sc, o in zip(self.filters, images, scales, outs):
-            flt.integrate(f, stream)
+        for flt, sc, o in zip(self.filters, scales, outs):
             flt._check_scales(sc)
             jobs.append(C.abf_job(flt.plan.value, flt.g.data_ptr(), sc.data_ptr(), flt.W * 16, o.data_ptr(),
                                   flt.W * o.element_size()))
@@ -142,9 +151,9 @@ class Batch:
     def autotune(self, images, scales, outs, stream=None):
         """Integrate, then time the batch launch at 4, 8 and 16 rows per CTA and
         cache the fastest for batches of this composition; returns (rows, [ms x 3])."""
+        self.integrate(images, stream)
         jobs = []
-        for flt, f, sc, o in zip(self.filters, images, scales, outs):
-            flt.integrate(f, stream)
+        for flt, sc, o in zip(self.filters, scales, outs):
             flt._check_scales(sc)
             jobs.append(C.abf_job(flt.plan.value, flt.g.data_ptr(), sc.data_ptr(), flt.W * 16, o.data_ptr(),
                                   flt.W * o.element_size()))
