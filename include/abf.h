@@ -283,10 +283,15 @@ abf_status abf_batch_autotune(const abf_job* jobs, int32_t njobs, void* d_ws, si
  * Results are the same as abf_integrate + abf_filter on the job alone.      */
 typedef struct abf_server_s* abf_server;
 
+/* Server flag: the jobs admitted together (in one round of the worker) run
+ * their adaptive step in one batched launch (as abf_filter_batch) after each
+ * has finished its own copies and non-adaptive step on its own stream.      */
+#define ABF_SERVER_GROUP_MESH 1
+
 typedef struct {
   size_t hbm_budget;        /* bytes of device memory the server may hold (> 0)    */
   int32_t max_inflight;     /* jobs running at once (slots, 1..64)                  */
-  int32_t flags;            /* reserved, 0                                          */
+  int32_t flags;            /* 0 or ABF_SERVER_GROUP_MESH                           */
 } abf_server_cfg;
 
 typedef struct {

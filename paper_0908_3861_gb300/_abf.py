@@ -261,8 +261,11 @@ def abf_batch_max_jobs():
     return lib().abf_batch_max_jobs()
 
 
-def abf_server_create(hbm_budget, max_inflight):
-    cfg = abf_server_cfg(int(hbm_budget), int(max_inflight), 0)
+ABF_SERVER_GROUP_MESH = 1
+
+
+def abf_server_create(hbm_budget, max_inflight, flags=0):
+    cfg = abf_server_cfg(int(hbm_budget), int(max_inflight), int(flags))
     h = ctypes.c_void_p()
     _check(lib().abf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "abf_server_create")
     return h

@@ -730,6 +730,21 @@ struct abf_plan_s {
 };
 
 namespace abf {
+// One image of a batched adaptive step (run_mesh_batch).
+struct BatchIn {
+  PlanView pv;
+  const uint64_t* g;
+  const void* scales;
+  size_t scale_pitch;
+  void* s;
+  size_t s_pitch;
+  int32_t* status;
+};
+int batch_max_jobs();
+// Persistent launches of the adaptive step over many images, one per (order,
+// limbs, fast path) group; counter: 32 64-bit device counters.
+cudaError_t run_mesh_batch(const BatchIn* in, int njobs, unsigned long long* counter, int warps, cudaStream_t st);
+
 // abf_integrate / abf_filter (exact form) with the device status word given by
 // the caller instead of the plan's own: the serving loop gives every slot its
 // own word, so that jobs sharing a plan do not see each other's flags.

@@ -806,16 +806,6 @@ cudaError_t run_mesh_exact(const PlanView& pv, const uint64_t* g, const void* sc
 
 // Host side of the batched launch: order the images by cost (order n, then
 // pixels), number their runs, and launch persistent CTAs over them.
-struct BatchIn {
-  PlanView pv;
-  const uint64_t* g;
-  const void* scales;
-  size_t scale_pitch;
-  void* s;
-  size_t s_pitch;
-  int32_t* status;
-};
-
 int batch_max_jobs() { return kMaxBatch; }
 
 template <int N, int L, bool FAST>

@@ -40,15 +40,6 @@ cudaError_t run_prepare_scales(const PlanView& pv, const void* scales, size_t sc
 cudaError_t run_measure_scales(const PlanView& pv, const void* scales, size_t scale_pitch,
                                unsigned long long* out2, int32_t* status, cudaStream_t st);
 size_t noalloc_scratch_bytes();
-struct BatchIn {
-  PlanView pv;
-  const uint64_t* g;
-  const void* scales;
-  size_t scale_pitch;
-  void* s;
-  size_t s_pitch;
-  int32_t* status;
-};
 int batch_max_jobs();
 cudaError_t run_lookback_starved(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
                                  cudaStream_t st);

@@ -57,6 +57,7 @@ struct Job {
   int slot = -1;
   cudaEvent_t ev = nullptr;     // end of the job's stream work (timed)
   cudaEvent_t ev0 = nullptr;    // start of the job's stream work (timed)
+  cudaEvent_t ev_ready = nullptr;  // grouped jobs: integrated image and scales on the device
   Resident* res = nullptr; // integrated image reused from / kept in the resident set
   Resident* pinned = nullptr;  // resident image held since submit (a request without h_f)
   bool keep = false;       // keep d_g resident after the job
@@ -81,6 +82,7 @@ struct abf_server_s {
   std::vector<int> slot_busy;
   int32_t* h_dev_status = nullptr;  // pinned, one word per slot
   int32_t* d_slot_status = nullptr; // device status word per slot, cleared before every job
+  unsigned long long* d_slot_counter = nullptr;  // 32 work counters per slot (grouped mesh launches)
   cudaEvent_t base_ev = nullptr;    // device-clock origin of the job timestamps
   size_t used = 0, peak = 0;
   uint64_t next_ticket = 1;
@@ -130,8 +132,13 @@ struct abf_server_s {
     cv_done.notify_all();
   }
 
-  // Start a job on a free slot; false if it cannot start now (no room).
-  bool try_start(Job* j, int slot) {
+  // Start a job on a free slot; false if it cannot start now (no room).  With
+  // `defer`, the job stops after its non-adaptive step (ev_ready recorded) and
+  // its adaptive step runs in a grouped launch (launch_group); otherwise it
+  // runs to the end on its own stream.  *started tells whether it is now
+  // running (a job that failed at once is finished instead).
+  bool try_start(Job* j, int slot, bool defer, bool* started) {
+    *started = false;
     cudaStream_t st = streams[slot];
     abf_status s;
     j->plan = plan_for(j->req.desc, &s);
@@ -140,6 +147,7 @@ struct abf_server_s {
       finish(j, s);
       return true;
     }
+    if (defer && !grouping_ok(j->plan)) defer = false;
     const abf_plan p = j->plan;
     const int W = p->pv.W, H = p->pv.H;
     const size_t fb = (size_t)W * H * elem_bytes(p->pv.in_dtype), sb = (size_t)W * H * 16,
@@ -185,21 +193,88 @@ struct abf_server_s {
                                                          j->d_ws, dst, st) != ABF_OK)
         e = cudaErrorLaunchFailure;
     }
+    if (defer) {
+      if (e == cudaSuccess) ok(cudaEventCreateWithFlags(&j->ev_ready, cudaEventDisableTiming));
+      if (e == cudaSuccess) ok(cudaEventRecord(j->ev_ready, st));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        complete(j, ABF_ERR_CUDA);
+        return true;
+      }
+      *started = true;
+      return true;
+    }
     if (e == cudaSuccess &&
         abf::filter_with_status(p, j->d_g, j->d_sc, (size_t)W * 16, j->d_s, (size_t)W * elem_bytes(p->pv.out_dtype),
                                 dst, st) != ABF_OK)
       e = cudaErrorLaunchFailure;
+    finish_tail(j, e);
+    return true;
+  }
+
+  // The end of a job's stream work: output and status word back to the host,
+  // the end event; or the job's completion with an error.
+  void finish_tail(Job* j, cudaError_t e) {
+    cudaStream_t st = streams[j->slot];
+    const abf_plan p = j->plan;
+    const int W = p->pv.W, H = p->pv.H;
+    auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     if (e == cudaSuccess)
       ok(cudaMemcpy2DAsync(j->req.h_s, j->req.s_pitch, j->d_s, (size_t)W * elem_bytes(p->pv.out_dtype),
                            (size_t)W * elem_bytes(p->pv.out_dtype), H, cudaMemcpyDeviceToHost, st));
-    if (e == cudaSuccess) ok(cudaMemcpyAsync(&h_dev_status[slot], dst, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (e == cudaSuccess)
+      ok(cudaMemcpyAsync(&h_dev_status[j->slot], d_slot_status + j->slot, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                         st));
     if (e == cudaSuccess) ok(cudaEventCreate(&j->ev));
     if (e == cudaSuccess) ok(cudaEventRecord(j->ev, st));
     if (e != cudaSuccess) {
       cudaGetLastError();
       complete(j, ABF_ERR_CUDA);
     }
-    return true;
+  }
+
+  // Jobs whose adaptive step may share a grouped launch: any exact-form plan
+  // (the batched mesh runs every order and limb count).
+  static bool grouping_ok(abf_plan p) { return p && p->desc.form == ABF_FORM_EXACT; }
+
+  // The adaptive step of jobs admitted together, in one batched launch per
+  // (order, limbs) group on the first job's stream, after every job's own
+  // non-adaptive step; each job's stream then copies its result out.
+  void launch_group(std::vector<Job*>& grp) {
+    if (grp.empty()) return;
+    if (grp.size() == 1) {
+      Job* j = grp[0];
+      cudaError_t e = cudaStreamWaitEvent(streams[j->slot], j->ev_ready, 0);
+      const abf_plan p = j->plan;
+      const int W = p->pv.W;
+      if (e == cudaSuccess &&
+          abf::filter_with_status(p, j->d_g, j->d_sc, (size_t)W * 16, j->d_s,
+                                  (size_t)W * elem_bytes(p->pv.out_dtype), d_slot_status + j->slot,
+                                  streams[j->slot]) != ABF_OK)
+        e = cudaErrorLaunchFailure;
+      finish_tail(j, e);
+      return;
+    }
+    cudaStream_t gs = streams[grp[0]->slot];
+    cudaError_t e = cudaSuccess;
+    std::vector<abf::BatchIn> in;
+    for (Job* j : grp) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, j->ev_ready, 0);
+      const abf_plan p = j->plan;
+      const int W = p->pv.W;
+      in.push_back(abf::BatchIn{p->pv, (const uint64_t*)j->d_g, j->d_sc, (size_t)W * 16, j->d_s,
+                                (size_t)W * elem_bytes(p->pv.out_dtype), d_slot_status + j->slot});
+    }
+    if (e == cudaSuccess) e = abf::run_mesh_batch(in.data(), (int)in.size(), d_slot_counter + 32 * grp[0]->slot, 8, gs);
+    cudaEvent_t meshed = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&meshed, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(meshed, gs);
+    for (Job* j : grp) {
+      cudaError_t ej = e;
+      if (ej == cudaSuccess) ej = cudaStreamWaitEvent(streams[j->slot], meshed, 0);
+      finish_tail(j, ej);
+    }
+    if (meshed) cudaEventDestroy(meshed);
   }
 
   // Release the resident image a request without h_f has held since submit.
@@ -228,6 +303,10 @@ struct abf_server_s {
     if (j->ev0) {
       cudaEventDestroy(j->ev0);
       j->ev0 = nullptr;
+    }
+    if (j->ev_ready) {
+      cudaEventDestroy(j->ev_ready);
+      j->ev_ready = nullptr;
     }
     size_t freed = 0;
     const abf_plan p = j->plan;
@@ -271,21 +350,28 @@ struct abf_server_s {
         complete(j, q == cudaSuccess ? ABF_OK : ABF_ERR_CUDA);
         progress = true;
       }
-      // admissions, in arrival order; a job that does not fit lets later ones try
+      // admissions, in arrival order; a job that does not fit lets later ones
+      // try.  With grouping on, the jobs admitted in one round share one
+      // batched launch of the adaptive step.
       if (!paused) {
+        const bool grouping = (cfg.flags & ABF_SERVER_GROUP_MESH) != 0;
+        std::vector<Job*> grp;
         for (auto it = queue.begin(); it != queue.end();) {
           int slot = -1;
           for (int k = 0; k < (int)slot_busy.size(); ++k)
             if (!slot_busy[k]) { slot = k; break; }
           if (slot < 0) break;
           Job* j = *it;
-          if (try_start(j, slot)) {
+          bool started = false;
+          if (try_start(j, slot, grouping, &started)) {
             it = queue.erase(it);
             progress = true;
+            if (started) grp.push_back(j);
           } else {
             ++it;
           }
         }
+        launch_group(grp);
       }
       if (stop && queue.empty() && running.empty()) break;
       if (!progress) cv_work.wait_for(lk, std::chrono::microseconds(running.empty() ? 2000 : 50));
@@ -297,6 +383,7 @@ extern "C" {
 
 abf_status abf_server_create(const abf_server_cfg* cfg, abf_server* out) {
   if (!cfg || !out || cfg->hbm_budget == 0 || cfg->max_inflight < 1 || cfg->max_inflight > 64) return ABF_ERR_INVALID;
+  if (cfg->flags & ~ABF_SERVER_GROUP_MESH) return ABF_ERR_INVALID;
   *out = nullptr;
   abf_server s = new (std::nothrow) abf_server_s();
   if (!s) return ABF_ERR_OOM;
@@ -315,10 +402,17 @@ abf_status abf_server_create(const abf_server_cfg* cfg, abf_server* out) {
     delete s;
     return ABF_ERR_CUDA;
   }
+  if (cudaMalloc((void**)&s->d_slot_counter, sizeof(unsigned long long) * 32 * cfg->max_inflight) != cudaSuccess) {
+    cudaFreeHost(s->h_dev_status);
+    cudaFree(s->d_slot_status);
+    delete s;
+    return ABF_ERR_CUDA;
+  }
   if (cudaEventCreate(&s->base_ev) != cudaSuccess || cudaEventRecord(s->base_ev, s->streams[0]) != cudaSuccess ||
       cudaEventSynchronize(s->base_ev) != cudaSuccess) {
     cudaFreeHost(s->h_dev_status);
     cudaFree(s->d_slot_status);
+    cudaFree(s->d_slot_counter);
     delete s;
     return ABF_ERR_CUDA;
   }
@@ -442,6 +536,7 @@ abf_status abf_server_destroy(abf_server s) {
   }
   if (s->h_dev_status) cudaFreeHost(s->h_dev_status);
   if (s->d_slot_status) cudaFree(s->d_slot_status);
+  if (s->d_slot_counter) cudaFree(s->d_slot_counter);
   if (s->base_ev) cudaEventDestroy(s->base_ev);
   delete s;
   return ABF_OK;

@@ -183,10 +183,13 @@ class Server:
     admitted by device-memory footprint, run concurrently on their own streams,
     integrated images optionally kept resident by image id."""
 
-    def __init__(self, hbm_budget, max_inflight=4, device=None):
+    def __init__(self, hbm_budget, max_inflight=4, device=None, group_mesh=False):
+        """group_mesh: jobs admitted together share one batched launch of the
+        adaptive step (ABF_SERVER_GROUP_MESH)."""
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
-            self.h = C.abf_server_create(hbm_budget, max_inflight)
+            self.h = C.abf_server_create(hbm_budget, max_inflight,
+                                         C.ABF_SERVER_GROUP_MESH if group_mesh else 0)
         self.keep = {}
 
     def submit(self, desc, f, scales, out, image_id=0):

@@ -49,13 +49,14 @@ def _pinned(a):
     return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
 
 
-def test_mixed_jobs_equal_single_runs_within_budget():
+@pytest.mark.parametrize("group", [False, True])
+def test_mixed_jobs_equal_single_runs_within_budget(group):
     import torch
     from paper_0908_3861_gb300 import Server
     jobs = [_job(100 + i, int(h), int(w), n) for i, (h, w, n) in
             enumerate([(40, 70, 1), (90, 33, 2), (64, 64, 2), (17, 120, 1), (50, 50, 2), (75, 40, 1), (33, 90, 2)])]
     budget = 256 << 20
-    srv = Server(budget, max_inflight=3, device="cuda:0")
+    srv = Server(budget, max_inflight=3, device="cuda:0", group_mesh=group)
     tickets, outs = [], []
     for img, sc, n in jobs:
         o = torch.zeros(img.shape, dtype=torch.float32).pin_memory()
@@ -227,4 +228,37 @@ def test_concurrent_jobs_overlap_on_the_device():
     assert a["t_gpu_start_us"] < b["t_gpu_end_us"] and b["t_gpu_start_us"] < a["t_gpu_end_us"]
     for (img, sc, n), o in zip(jobs, outs):
         assert torch.equal(o, _alone(img, sc, n))
+    srv.close()
+
+
+def test_grouped_launch_keeps_results_and_status_per_job():
+    """Jobs admitted in one round (submitted while paused) share one batched
+    launch of the adaptive step: every result equals the job run alone, and
+    the one job with an invalid scale is the only one whose status shows it."""
+    import torch
+    from paper_0908_3861_gb300 import Server
+    specs = [(40, 70, 1), (90, 33, 2), (64, 64, 2), (17, 120, 1), (50, 50, 2)]
+    jobs = [_job(900 + i, h, w, n) for i, (h, w, n) in enumerate(specs)]
+    img2, sc2, n2 = jobs[2]
+    bad = sc2.copy()
+    bad[3, 4, 0] = np.nan
+    jobs[2] = (img2, bad, n2)
+    srv = Server(256 << 20, max_inflight=len(jobs), device="cuda:0", group_mesh=True)
+    srv.pause(True)
+    outs, tickets = [], []
+    for img, sc, n in jobs:
+        o = torch.zeros(img.shape, dtype=torch.float32).pin_memory()
+        tickets.append(srv.submit(_desc(img, n), _pinned(img), _pinned(sc), o))
+        outs.append(o)
+    srv.pause(False)
+    st = [srv.wait(t, timeout_s=120) for t in tickets]
+    assert all(s["status"] == 0 for s in st)
+    assert [s["device_status"] for s in st] == [0, 0, 1, 0, 0]
+    for k, ((img, sc, n), o) in enumerate(zip(jobs, outs)):
+        if k == 2:
+            ref = _alone(img, sc2, n)
+            ok = ~torch.isnan(o)
+            assert int((~ok).sum()) == 1 and torch.equal(o[ok], ref[ok])
+        else:
+            assert torch.equal(o, _alone(img, sc, n))
     srv.close()
