@@ -164,7 +164,7 @@ abf_status abf_integrate(abf_plan plan, const void* d_f, size_t f_pitch, void* d
  *   - The current device must be the plan's device (else ABF_ERR_INVALID).
  *   - Plans whose workspace (abf_plan_query) exceeds 32 MiB are rejected with
  *     ABF_ERR_UNSUPPORTED (e.g. order 2, two limbs, steps up to 150: images up
- *     to about 2048 x 2048).
+ *     to about 3300 x 3300).
  *   - Every call shares the one array and clears the parts that must start at
  *     zero; calls that overlap on the GPU (other streams, other threads) race
  *     on it and give wrong results: serialise them.                          */

@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
 // therefore sums T_{dR}(A) over the d-th band below until a band that has
 // published its inclusive state P, which enters as T_{dR}(P).
 
-constexpr int kBand = 32;         // rows per band
+constexpr int kBand = 64;         // rows per band (fewer bands: a shorter look-back chain)
 // Lines per CTA (one per thread): the band is staged in shared memory,
 // kBand x lines x L limbs (32 KB at most, so that several CTAs per SM keep
 // their copies in flight while others wait in the look-back).
 template <int L>
-__host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 64 : 32; }
+__host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 32 : 16; }
 template <int L>
 __host__ __device__ constexpr int band_smem_bytes() { return kBand * lines_per_cta<L>() * L * 8; }
 constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;

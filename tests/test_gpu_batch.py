@@ -151,10 +151,13 @@ def test_batched_integrate_equals_single_integrates():
                                max_scale=5.0 + i, out="f64", device=dev)
         fl.append(f)
         imgs.append(gu.to_device(img, dev))
+    def box(f):   # the lattice box's columns (the pitch padding is never written)
+        hl = f.info["halo_lrbt"]
+        return f.integrated()[:, : f.W + hl[0] + hl[1]]
     ref = []
     for f, im in zip(fl, imgs):
         f.integrate(im)
-        ref.append(f.integrated().clone())
+        ref.append(box(f).clone())
     assert len(set((f.n, f.limbs) for f in fl)) >= 3
     b = Batch(fl, dev)
     for _ in range(2):
@@ -163,5 +166,5 @@ def test_batched_integrate_equals_single_integrates():
         b.integrate(imgs)
         torch.cuda.synchronize()
         for k, (f, r) in enumerate(zip(fl, ref)):
-            assert torch.equal(f.integrated(), r), "image %d" % k
+            assert torch.equal(box(f), r), "image %d" % k
     assert all(f.device_status() == 0 for f in fl)
