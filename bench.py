@@ -404,7 +404,9 @@ def run_batch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     __graft_entry__.build()
-    jobs = synthetic.batch_workload(seed_offset=rank)
+    small = args.workload == "c4s"
+    jobs = (synthetic.batch_workload(count=512, lo=32, hi=256, seed_offset=rank) if small
+            else synthetic.batch_workload(seed_offset=rank))
     fl, imgs, scs, outs = [], [], [], []
     for w in jobs:
         H, W = w["image"].shape
@@ -449,14 +451,17 @@ def run_batch(args):
     torch.cuda.synchronize()
     single_ms = t0.elapsed_time(t1)
     same = all(torch.equal(a, b) for a, b in zip(ref, outs))
-    # per image a row scan and three line scans, then one batch launch per
-    # (order, limbs) group present
-    n_launch = 4 * len(jobs) + len(set((w["n"], f.limbs) for w, f in zip(jobs, fl)))
+    # one clear, then per (limbs, order, input type) group a row pass and three
+    # line passes, then one batch launch per (order, limbs, path) group present
+    groups = set((w["n"], f.limbs) for w, f in zip(jobs, fl))
+    n_launch = 1 + 4 * len(groups) + len(groups)
     line = {"metric": METRIC, "value": round(pix / (batch_ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(batch_ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64 limbs (2 or 4 per image)", "data": "synthetic",
-            "config": {"workload": "64 images, sides U{128..2048}, n U{1,2,3}, f32 2^-16 grid, a_k in [1,32], "
-                                   "Q=8, exact form; one persistent launch, CUDA graph replay",
+            "config": {"workload": ("512 images, sides U{32..256}" if small else "64 images, sides U{128..2048}")
+                                   + ", n U{1,2,3}, f32 2^-16 grid, a_k in [1,32], Q=8, exact form; one launch per "
+                                   "pass and group for the non-adaptive step, one persistent launch per group for "
+                                   "the adaptive step, CUDA graph replay",
                        "pixels_per_step": int(pix), "l2": "inputs larger than L2"},
             "gpu_launches": int(K * n_launch),
             "batched_vs_single": {"batched_ms": round(batch_ms, 3), "single_ms": round(single_ms, 3),
@@ -1002,7 +1007,7 @@ def main():
     args.compare = [c for c in args.compare.split(",") if c]
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "c4":
+    elif args.workload in ("c4", "c4s"):
         run_batch(args)
     elif args.workload == "c5":
         run_serve(args)
