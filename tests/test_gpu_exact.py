@@ -272,10 +272,11 @@ def test_lookback_wait_times_out_then_the_context_recovers():
     process then filters correctly."""
     import torch
     from paper_0908_3861_gb300 import AdaptiveFilter, _abf
-    w = _small_workload(1, (40, 60), 4, "u8", 77)
+    w = _small_workload(1, (100, 60), 4, "u8", 77)   # two bands of 64 rows: band 1 waits on band 0
     H, W = w["image"].shape
     filt = AdaptiveFilter(W, H, 1, torch.uint8, scale_kind="a4", q_bits=4, frac_bits=0, max_scale=w["cmax"],
                           out="f64", value_bound=255.0, device="cuda:0")
+    assert 64 < H + filt.info["halo_lrbt"][3] <= 128
     _abf.abf_debug_starved_lookback(filt.plan, filt.g, filt.ws)
     torch.cuda.synchronize()
     assert filt.device_status() & _abf.ABF_DEV_TIMEOUT
