@@ -344,26 +344,49 @@ __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __r
       st_store<L, NF>(ws.agg + slot * NF * L, agg);
       __threadfence();
       st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);
+      // Up to kLook predecessor flags are read per round trip (relaxed loads,
+      // then one acquire fence before the values they publish are read): the
+      // walk back to the nearest published prefix takes a quarter of the trips.
+      constexpr int kLook = 4;
       int bb = band - 1;
       long long dist = 0;  // rows between the end of band bb and the start of this band
       long long spins = 0;
       while (bb >= 0) {
-        const size_t s2 = (size_t)bb * ws.nlines + l;
-        const uint32_t fl = ld_acquire(ws.flags + s2);
-        if ((fl >> 2) != epoch || (fl & 3u) == 0u) {
+        uint32_t fl[kLook];
+#pragma unroll
+        for (int q = 0; q < kLook; ++q)
+          fl[q] = bb - q >= 0 ? ld_relaxed(ws.flags + (size_t)(bb - q) * ws.nlines + l) : 0u;
+        int ready = 0;
+        bool prefix = false;
+#pragma unroll
+        for (int q = 0; q < kLook; ++q) {
+          if (ready != q || bb - q < 0) break;
+          if ((fl[q] >> 2) != epoch || (fl[q] & 3u) == 0u) break;
+          ++ready;
+          if ((fl[q] & 3u) == kFlagPrefix) {
+            prefix = true;
+            break;
+          }
+        }
+        if (ready == 0) {
           if (++spins > kSpinLimit) {
             raise_status(status, ABF_DEV_TIMEOUT);
             break;
           }
           continue;
         }
-        if ((fl & 3u) == kFlagPrefix) {
-          st_add_transported<L, NF>(carry, st_load<L, NF>(ws.pref + s2 * NF * L), dist);
-          break;
+        fence_acquire();
+        for (int q = 0; q < ready; ++q) {
+          const size_t s2 = (size_t)(bb - q) * ws.nlines + l;
+          if (prefix && q == ready - 1) {
+            st_add_transported<L, NF>(carry, st_load<L, NF>(ws.pref + s2 * NF * L), dist);
+          } else {
+            st_add_transported<L, NF>(carry, st_load<L, NF>(ws.agg + s2 * NF * L), dist);
+            dist += kBand;
+          }
         }
-        st_add_transported<L, NF>(carry, st_load<L, NF>(ws.agg + s2 * NF * L), dist);
-        dist += kBand;
-        --bb;
+        if (prefix) break;
+        bb -= ready;
       }
     }
     LineState<L, NF> incl = agg;
