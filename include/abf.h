@@ -100,6 +100,20 @@ typedef struct {
   double value_bound;         /* upper bound on |f|; 0 means the dtype's range (u8,   *
                                * u16 only: required for float inputs)                 */
   double max_scale_product;   /* upper bound on c1 c2 c3 c4; 0 means max_scale^4      */
+  /* Directional order N of Sec. 4 Eq. (def): 0 or 4 (theta = 0, pi/4, pi/2,
+   * 3pi/4; Sec. 7), or 2 (theta = 0, pi/2: tensor box splines, the other
+   * member of the family whose running-sum filters of Eq. (RS_filter) lie on
+   * the lattice).  With N = 2 only c1 and c3 shape the kernel; c2 and c4 are
+   * read and must be valid; order n >= 2 unless a model is used (n = 1 alone
+   * is a discontinuous box); scale kinds c4 and a4 only.                    */
+  int32_t directions;
+  /* Image model of Sec. 6, f(x) = sum_k c[k] phi(x - k): 0 for phi = delta
+   * (Sec. 7 (1)); E >= 1 for the tensor B-spline phi = beta^{E-1} (x)
+   * beta^{E-1} (E unit boxes per axis, E <= 6).  For E >= 3 the coefficients
+   * c = f * (b^{E-1})^-1 are irrational and are rounded to the 2^-F grid
+   * (c_q = rint(c 2^F)) by a separable prefilter in abf_integrate; the rest
+   * is exact on c_q.  Models and N = 2 need q_bits <= 7 and the exact form. */
+  int32_t model_boxes;
 } abf_desc;
 
 typedef struct abf_plan_s* abf_plan;
@@ -127,6 +141,19 @@ abf_status abf_plan_destroy(abf_plan plan);
  * Any output pointer may be NULL.                                            */
 abf_status abf_plan_query(abf_plan plan, size_t* integrated_bytes, size_t* workspace_bytes,
                           int32_t* halo_lrbt, int32_t* limbs, int64_t* g_pitch_elems);
+
+/* Host-only: the interpolation table of a generalised plan (directions N,
+ * order n, model_boxes E; Eq. (mask): the box spline with the lattice
+ * directions v1..v4 taken (n + E, n, n + E, n) times, or (n + E, 0, n + E, 0)
+ * for N = 2) on the 2^-P grid, P = q_bits + 1, without touching a device.
+ * Layout: (2^P)^2 rows, row index ry 2^P + rx for the offset r = (rx, ry) 2^-P
+ * of a tap from its floor point; each row holds D M(r - d) for the *R
+ * neighbours d, listed in stencil_xy as (dx, dy) pairs (caller array of 512
+ * int32); *wbytes-byte little-endian words.  With out = NULL only the sizes,
+ * the stencil and D are returned.                                           */
+abf_status abf_general_table_host(int32_t directions, int32_t n, int32_t model_boxes, int32_t q_bits, void* out,
+                                  size_t out_bytes, size_t* needed_bytes, int32_t* wbytes, int32_t* R,
+                                  int32_t* stencil_xy, uint32_t* D_words4);
 
 /* Non-adaptive step (Sec. 7 (1), Eq. (RS)) of the exact form: the four
  * running-sum recursions, each n times, in the paper's order (0, pi/4, pi/2,

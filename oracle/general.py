@@ -223,6 +223,19 @@ class MeshWeights:
         """D M(x, y) (centred) at (Xq, Yq) 2^-P."""
         return self.uncentred(Xq + self.CX, Yq + self.CY)
 
+    def row(self, rx, ry):
+        """Weights of a point p + r, r = (rx, ry) 2^-P in [0, 1)^2, for the
+        neighbours p + d, d in [dminx, dminx + wx) x [dminy, dminy + wy), as a
+        list indexed [iy][ix] (memoised per offset)."""
+        key = (rx, ry)
+        hit = self.cache.get(key)
+        if hit is None:
+            P = self.P
+            hit = [[self.value(rx - ((self.dminx + ix) << P), ry - ((self.dminy + iy) << P))
+                    for ix in range(self.wx)] for iy in range(self.wy)]
+            self.cache[key] = hit
+        return hit
+
 
 # ------------------------------------------------------------ the method
 
@@ -330,14 +343,15 @@ class Method:
             assert yx.denominator == 1 and yy.denominator == 1
             X, Y = int(yx), int(yy)
             px, py = X >> self.P, Y >> self.P
+            wrow = mw.row(X - (px << self.P), Y - (py << self.P))
             acc = 0
             for iy in range(mw.wy):
                 k2 = py + mw.dminy + iy
+                line = wrow[iy]
                 for ix in range(mw.wx):
-                    k1 = px + mw.dminx + ix
-                    wt = mw.value(X - (k1 << self.P), Y - (k2 << self.P))
+                    wt = line[ix]
                     if wt:
-                        acc += int(gget(k1, k2)) * wt
+                        acc += int(gget(px + mw.dminx + ix, k2)) * wt
             S += w * acc
         return S
 
@@ -381,6 +395,36 @@ def filter_pixels(c_int, origin, C, r, n1, q_bits, f_bits, pixels):
     return S_out, s_out
 
 
+def filter_image(c_int, origin, C, r, n1, q_bits, f_bits):
+    """Every pixel of an H x W image (C: H x W x 4 integer steps), with one
+    lattice box for all of them: returns (S, s) as lists in row-major order."""
+    c_int = np.asarray(c_int, dtype=object)
+    ox, oy = origin
+    C = np.asarray(C)
+    H, W = C.shape[:2]
+    meth = Method(r, n1, q_bits)
+    cm = [int(C[..., k].max()) for k in range(4)]
+    left, right, below, above = meth.reach(cm)
+    x0, x1 = -left - ox, W + right + c_int.shape[1]
+    y0, y1 = -below - oy, H + above + c_int.shape[0]
+    # c on the box, in box coordinates: element [i, j] of c_int is image point (j - ox, i - oy)
+    local = np.zeros((y1 - y0, x1 - x0), dtype=object)
+    local[:, :] = 0
+    local[-oy - y0:-oy - y0 + c_int.shape[0], -ox - x0:-ox - x0 + c_int.shape[1]] = c_int
+    g = integrate(local, meth.r, 0, x1 - x0, 0, y1 - y0)
+
+    def gget(k1, k2):
+        return g[k2 - y0, k1 - x0]
+
+    S_out, s_out = [], []
+    for m2 in range(H):
+        for m1 in range(W):
+            Sm = meth.numerator(gget, m1, m2, C[m2, m1])
+            S_out.append(Sm)
+            s_out.append(Fr(Sm) / meth.denominator(C[m2, m1], f_bits))
+    return S_out, s_out
+
+
 def filter_direct(c_int, origin, C, r, n1, q_bits, f_bits, pixels):
     """s[m] = sum_k c[k] B(m - k) from the definition (exact Fractions)."""
     c_int = np.asarray(c_int, dtype=object)
@@ -393,9 +437,16 @@ def filter_direct(c_int, origin, C, r, n1, q_bits, f_bits, pixels):
         kb = kernels.get(key)
         if kb is None:
             kb = kernels[key] = kernel_direct(c, r, n1)
+        # the centred kernel vanishes beyond half the sum of |direction components|
+        hx = sum(abs(d[0]) * k for d, k in zip(kb.dirs, kb.counts)) / 2
+        hy = sum(abs(d[1]) * k for d, k in zip(kb.dirs, kb.counts)) / 2
         acc = Fr(0)
         for i in range(c_int.shape[0]):
+            if abs(m2 - (i - oy)) >= hy:
+                continue
             for j in range(c_int.shape[1]):
+                if abs(m1 - (j - ox)) >= hx:
+                    continue
                 v = int(c_int[i, j])
                 if v:
                     acc += v * kb.centred_value(m1 - (j - ox), m2 - (i - oy))

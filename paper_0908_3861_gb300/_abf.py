@@ -46,7 +46,8 @@ class abf_desc(ctypes.Structure):
                 ("scale_kind", ctypes.c_int32), ("q_bits", ctypes.c_int32),
                 ("in_frac_bits", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("max_scale", ctypes.c_double), ("min_scale", ctypes.c_double),
-                ("value_bound", ctypes.c_double), ("max_scale_product", ctypes.c_double)]
+                ("value_bound", ctypes.c_double), ("max_scale_product", ctypes.c_double),
+                ("directions", ctypes.c_int32), ("model_boxes", ctypes.c_int32)]
 
 
 class abf1d_desc(ctypes.Structure):
@@ -96,6 +97,8 @@ def signatures():
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
         "abf_integrate_batch": ([P(abf_integrate_job), i32, vp, sz, vp], st),
         "abf_integrate_batch_max_jobs": ([], i32),
+        "abf_general_table_host": ([i32, i32, i32, i32, vp, sz, P(sz), P(i32), P(i32), P(i32), P(ctypes.c_uint32)],
+                                   st),
         "abf_batch_max_jobs": ([], i32),
         "abf_plan_autotune": ([vp, vp, vp, sz, vp, sz, vp, P(i32), P(ctypes.c_float)], st),
         "abf_batch_autotune": ([P(abf_job), i32, vp, sz, vp, P(i32), P(ctypes.c_float)], st),
@@ -244,6 +247,28 @@ def abf_integrate_batch(jobs, ws, stream=None):
     arr = (abf_integrate_job * len(jobs))(*jobs)
     _check(lib().abf_integrate_batch(arr, len(jobs), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "abf_integrate_batch")
+
+
+def abf_general_table_host(directions, n, model_boxes, q_bits, with_weights=True):
+    """The generalised interpolation table on the host: returns (weights as
+    a list of rows of Python ints, stencil [(dx, dy)], D, wbytes)."""
+    need, wb, R = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32()
+    st = (ctypes.c_int32 * 512)()
+    D4 = (ctypes.c_uint32 * 4)()
+    _check(lib().abf_general_table_host(directions, n, model_boxes, q_bits, None, 0, ctypes.byref(need),
+                                        ctypes.byref(wb), ctypes.byref(R), st, D4), "abf_general_table_host")
+    stencil = [(st[2 * i], st[2 * i + 1]) for i in range(R.value)]
+    D = sum(int(D4[i]) << (32 * i) for i in range(4))
+    rows = None
+    if with_weights:
+        buf = (ctypes.c_uint8 * need.value)()
+        _check(lib().abf_general_table_host(directions, n, model_boxes, q_bits, buf, need.value, None, None, None,
+                                            None, None), "abf_general_table_host")
+        raw = bytes(buf)
+        w, Rv = wb.value, R.value
+        rows = [[int.from_bytes(raw[(r * Rv + c) * w:(r * Rv + c + 1) * w], "little") for c in range(Rv)]
+                for r in range(need.value // (w * Rv))]
+    return rows, stencil, D, wb.value
 
 
 def abf_integrate_batch_max_jobs():

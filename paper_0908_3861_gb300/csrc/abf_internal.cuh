@@ -421,6 +421,33 @@ __device__ __forceinline__ void wmac2_u32(Wide<2>& acc, const Wide<2>& g, uint32
   acc.w[1] = ((uint64_t)r3 << 32) | r2;
 }
 
+// Weight table element types per order: D < 2^32 (n = 1), < 2^60 (n = 2), < 2^121 (n = 3)
+// (room for the FD weight |w_j| <= 16, resp. 81, folded into the table weight).
+template <int N> struct WeightT;
+template <> struct WeightT<1> { using T = uint32_t; };
+template <> struct WeightT<2> { using T = uint64_t; };
+template <> struct WeightT<3> { using T = ulonglong2; };
+
+// acc += g * w for the table word types.
+template <int L, typename WT>
+__device__ __forceinline__ void mac_weight(Wide<L>& acc, const Wide<L>& gv, const WT w) {
+  if constexpr (sizeof(WT) == 16) {
+    if constexpr (L == 1) wmac<1>(acc, gv, w.x);
+    else if constexpr (L == 2) wmac_w4_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
+    else if constexpr (L == 3) wmac_w6_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
+    else wmac_w8_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
+  } else if constexpr (sizeof(WT) == 8) {
+    if constexpr (L == 1) wmac<1>(acc, gv, w);
+    else if constexpr (L == 2) wmac2_u64(acc, gv, w);
+    else if constexpr (L == 3) wmac_w6_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
+    else wmac_w8_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
+  } else if constexpr (L == 2) {
+    wmac2_u32(acc, gv, w);
+  } else {
+    wmac<L>(acc, gv, (uint64_t)w);
+  }
+}
+
 // -a (mod 2^(64L))
 template <int L>
 __device__ __forceinline__ Wide<L> wneg(const Wide<L>& a) {
@@ -596,6 +623,14 @@ struct PlanView {
   int table_bytes_per_w;          // 4, 8 or 16
   const void* table;              // (2^P)^2 rows of (3n)^2 weights
   const void* table_fold;         // n = 3: the table folded by the square's symmetries, else null
+  // Running sums per direction v1..v4 (n each for the four-direction filter;
+  // (n, 0, n, 0) for N = 2), and, for the generalised mesh, the unit boxes E
+  // per axis of the model phi, the kernel's stencil and the output origin.
+  int r[4];
+  int E;                          // 0: phi = delta
+  int R, dminx, dminy;            // generalised table: neighbours per row, stencil box origin
+  const int2* stencil;            // generalised table: the R neighbours (dx, dy)
+  int ox, oy;                     // output pixel m sits at lattice point m + (ox, oy)
 };
 
 // ------------------------------------------------------ per-pixel scale reading
@@ -735,9 +770,35 @@ struct abf_plan_s {
   int32_t* d_status = nullptr;
   size_t g_bytes = 0, ws_bytes = 0;
   int mesh_warps = 8;          // rows per CTA of the exact mesh (abf_plan_autotune)
+  // Generalised plans (N = 2, or a B-spline model phi): pv is the mesh's view
+  // (output pixels, origin); sv the running sums' view of their input (the
+  // image, or the model coefficients staged on an extended frame).
+  bool general = false;
+  abf::PlanView sv{};
+  void* d_stage = nullptr;     // model coefficients c_q (int64), sv.W x sv.H
+  void* d_pf_tmp = nullptr;    // prefilter intermediate (int64), H rows x sv.W, and the column pass' state
+  size_t pf_tmp_bytes = 0;
+  void* pf = nullptr;          // prefilter constants (host copy)
+  void* d_stencil = nullptr;
 };
 
 namespace abf {
+// The 1-D interpolation prefilter's constants (Sec. 3; its kernels are in
+// line1d.cu), shared with the 2-D model's separable prefilter.
+constexpr int kPfHalo = 64;                         // >= every warm-up length W_p
+constexpr int kPfMaxPoles = 2;
+struct PrefilterView {
+  int length, Gw, left, G, npoles;
+  int W[kPfMaxPoles];            // warm-up samples per pole
+  long long Z[kPfMaxPoles];      // rint(z_p 2^64)
+  long long A[kPfMaxPoles];      // rint(A_p 2^60)
+  double scale;                  // 2^F
+  long long bound;               // floor(value_bound 2^F)
+};
+abf_status prefilter2d_setup(int n1, double xmax, PrefilterView* pf, double* hnorm, int* tail);
+cudaError_t run_prefilter_rows_raw(const PrefilterView& v, int count, int in_dtype, const void* f, size_t f_pitch,
+                                   long long* c, long long c_pitch, int32_t* status, cudaStream_t st);
+
 // One image of a batched adaptive step (run_mesh_batch).
 struct BatchIn {
   PlanView pv;

@@ -1,0 +1,666 @@
+// Generalised plans: the directional order N = 2 and the B-spline model phi.
+//
+// Sec. 4 Eq. (def) builds beta^N_a from the directions theta_k = (k-1) pi/N;
+// the RS filters of Eq. (RS_filter) exist on the lattice only when
+// b cos theta and b sin theta are integers, which among N >= 2 holds for
+// N = 4 (Sec. 7, the plain plans) and N = 2: theta = 0, pi/2, b = (1, 1), the
+// tensor box splines (Sec. 4: rect = beta^2_(1,1)).  N = 2 uses the directions
+// v1 and v3 alone: running sums and FD only along them.
+//
+// Sec. 6 writes the image as f(x) = sum_k c[k] phi(x - k), c = f * (b^n)^-1;
+// Eq. (NA) without interpolation runs the running sums on c and Eq. (mask)
+// interpolates with phi * beta^N_b.  Here phi = beta^{E-1}(x1) beta^{E-1}(x2),
+// E unit boxes per axis (a reading: Sec. 6 leaves phi open), so the
+// interpolation kernel is the box spline with the lattice directions v_k taken
+// r_k + (E along v1 and v3) times.  For E >= 3 (degree >= 2) c is irrational:
+// c_q = rint(c 2^F) is computed by the separable prefilter (the 1-D filter's
+// recursions along rows, unrounded, then along columns, rounded) on a frame
+// that extends T samples beyond every image edge, and the method runs exactly
+// on c_q.
+//
+// Every tap lies on the 2^-(Q+1) grid (P = Q + 1: tau = (1/2) sum_k r_k (c_k -
+// 1) v_k and the kernel's centre are half-integers at most), where D M is an
+// integer (D = D0 2^((sum m - 2) P), the refinement equation); the table holds
+// one row per fractional offset r in [0, 1)^2 (p = floor(y)) with the
+// neighbours d that carry a weight.  The numerator S = D sum_j w_j g_I(y_j) is
+// formed modulo 2^(64 L) as in the plain form, and
+// s = S 2^(Q sum r - F) / (D prod_k C_k^{r_k}).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "abf_internal.cuh"
+
+namespace abf {
+cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
+                          uint32_t* epoch, int32_t* status, cudaStream_t st);
+size_t line_ws_bytes(int Gw, int Gh, int L, int n, int* nbands_out, int* nlines_out);
+
+constexpr int kGenMaxR = 256;    // neighbours per table row
+constexpr int kGenMaxTaps = 81;  // prod_k (r_k + 1)
+constexpr int kGenWarps = 8;     // rows per CTA
+
+// ------------------------------------------------------------- mesh kernel
+
+// One warp per run of 32 pixels of a row, as the plain form's generic path:
+// lane i reads pixel x0 + i's steps; for each pixel of the run the lanes
+// tabulate its taps (grouped by FD weight) in shared memory and then deal the
+// (tap, neighbour) pairs of each group among themselves.
+template <int L, typename WT>
+__global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  __shared__ int2 s_st[kGenMaxR];
+  __shared__ unsigned char s_order[kGenMaxTaps];
+  __shared__ int s_gbeg[12], s_gw[11], s_ng, s_taps;
+  __shared__ int4 s_tap[kGenWarps][kGenMaxTaps];
+  const int R = pv.R;
+  for (int i = threadIdx.x; i < R; i += blockDim.x) s_st[i] = pv.stencil[i];
+  const int r0 = pv.r[0], r1 = pv.r[1], r2 = pv.r[2], r3 = pv.r[3];
+  if (threadIdx.x == 0) {
+    const int taps = (r0 + 1) * (r1 + 1) * (r2 + 1) * (r3 + 1);
+    int wt[kGenMaxTaps];
+    for (int t = 0; t < taps; ++t) {
+      int u = t, w = 1;
+      for (int k = 0; k < 4; ++k) {
+        const int rk = pv.r[k], j = u % (rk + 1);
+        u /= rk + 1;
+        int b = 1;  // binom(rk, j), rk <= 3
+        for (int i = 0; i < j; ++i) b = b * (rk - i) / (i + 1);
+        w *= (j & 1) ? -b : b;
+      }
+      wt[t] = w;
+    }
+    int ng = 0, c = 0;
+    for (int t = 0; t < taps; ++t) {
+      bool seen = false;
+      for (int q = 0; q < ng; ++q) seen |= s_gw[q] == wt[t];
+      if (!seen) s_gw[ng++] = wt[t];
+    }
+    for (int q = 0; q < ng; ++q) {
+      s_gbeg[q] = c;
+      for (int t = 0; t < taps; ++t)
+        if (wt[t] == s_gw[q]) s_order[c++] = (unsigned char)t;
+    }
+    s_gbeg[ng] = c;
+    s_ng = ng;
+    s_taps = taps;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.y * kGenWarps + warp;
+  if (y >= pv.H) return;
+  const int x0 = blockIdx.x * 32;
+  const int myx = x0 + lane;
+  const int Q = pv.Q, P = pv.P, one = 1 << Q, mask = (1 << P) - 1;
+  int C0 = 0, C1 = 0, C2 = 0, C3 = 0, ok = 0;  // 0 outside, 1 good, 2 range, 3 bad scale
+  if (myx < pv.W) {
+    int C[4];
+    if (!pixel_steps(pv, scales, scale_pitch, myx, y, C)) {
+      ok = 3;
+    } else {
+      C0 = C[0]; C1 = C[1]; C2 = C[2]; C3 = C[3];
+      float lb = pv.log2_base;
+      for (int k = 0; k < 4; ++k) lb += (float)pv.r[k] * (__log2f((float)C[k]) - (float)Q);
+      if (pv.E == 0) {
+        const float q = (float)one;
+        lb += __log2f((1.0f + q / (float)C[0]) * (1.0f + q / (float)C[2]));
+      }
+      ok = (lb + 0.05f < 64.0f * L - 1.0f) ? 1 : 2;
+    }
+  }
+  const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
+  const int taps = s_taps, ng = s_ng;
+  int4* tp = s_tap[warp];
+  Wide<L> mine;
+  wzero<L>(mine);
+  for (int pp = 0; pp < 32; ++pp) {
+    if (__shfl_sync(0xffffffffu, ok, pp) != 1) continue;
+    const int c0 = __shfl_sync(0xffffffffu, C0, pp), c1 = __shfl_sync(0xffffffffu, C1, pp);
+    const int c2 = __shfl_sync(0xffffffffu, C2, pp), c3 = __shfl_sync(0xffffffffu, C3, pp);
+    // tau 2^P = sum_k r_k (C_k - 2^Q) v_k; c_k 2^P = 2 C_k
+    const int tx = r0 * (c0 - one) + r1 * (c1 - one) - r3 * (c3 - one);
+    const int ty = r1 * (c1 - one) + r2 * (c2 - one) + r3 * (c3 - one);
+    const int Y0x = ((x0 + pp + pv.ox) << P) + tx;
+    const int Y0y = ((y + pv.oy) << P) + ty;
+    __syncwarp();
+    for (int slot = lane; slot < taps; slot += 32) {
+      int u = s_order[slot];
+      const int j1 = u % (r0 + 1); u /= r0 + 1;
+      const int j2 = u % (r1 + 1); u /= r1 + 1;
+      const int j3 = u % (r2 + 1); u /= r2 + 1;
+      const int j4 = u;
+      const int Yx = Y0x - 2 * (j1 * c0 + j2 * c1 - j4 * c3);
+      const int Yy = Y0y - 2 * (j2 * c1 + j3 * c2 + j4 * c3);
+      tp[slot] = make_int4((Yx >> P) + pv.left, Yy >> P, ((Yy & mask) << P) | (Yx & mask), 0);
+    }
+    __syncwarp();
+    Wide<L> acc;
+    wzero<L>(acc);
+    for (int gi = 0; gi < ng; ++gi) {
+      const int tb = s_gbeg[gi], npairs = (s_gbeg[gi + 1] - tb) * R;
+      Wide<L> part;
+      wzero<L>(part);
+      for (int idx = lane; idx < npairs; idx += 32) {
+        const int q = idx / R;
+        const int cand = idx - q * R;
+        const int4 ti = tp[tb + q];
+        const int2 d = s_st[cand];
+        const int k2 = ti.y + d.y;
+        if (k2 < 0) continue;  // rows below the box: g = 0
+        const Wide<L> gv = wload<L>(g + ((size_t)k2 * (size_t)pv.Gp + (size_t)(ti.x + d.x)) * L);
+        mac_weight<L, WT>(part, gv, __ldg(table + (size_t)ti.z * R + cand));
+      }
+      const int w = s_gw[gi];
+      Wide<L> sc;
+      wzero<L>(sc);
+      wmac<L>(sc, part, (uint64_t)(w < 0 ? -w : w));
+      if (w < 0) wsub<L>(acc, sc);
+      else wadd<L>(acc, sc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      Wide<L> other;
+#pragma unroll
+      for (int i = 0; i < L; ++i) other.w[i] = __shfl_xor_sync(0xffffffffu, acc.w[i], o);
+      wadd<L>(acc, other);
+    }
+    if (lane == pp) mine = acc;
+  }
+  if (myx >= pv.W) return;
+  const bool f64 = pv.out_dtype == ABF_F64;
+  if (ok != 1) {
+    raise_status(status, ok == 3 ? ABF_DEV_BAD_SCALE : ABF_DEV_RANGE);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (s) {
+      char* row = reinterpret_cast<char*>(s) + (size_t)y * s_pitch;
+      if (f64) reinterpret_cast<double*>(row)[myx] = nan;
+      else reinterpret_cast<float*>(row)[myx] = (float)nan;
+    }
+    return;
+  }
+  if (num) {
+    uint64_t* q = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(num) + (size_t)y * num_pitch) + (size_t)myx * L;
+#pragma unroll
+    for (int i = 0; i < L; ++i) q[i] = mine.w[i];
+  }
+  if (s) {
+    double den = pv.Dd;
+    const int Cv[4] = {C0, C1, C2, C3};
+    int rs = 0;
+    for (int k = 0; k < 4; ++k) {
+      for (int e = 0; e < pv.r[k]; ++e) den *= (double)Cv[k];
+      rs += pv.r[k];
+    }
+    const double v = ldexp(wto_double<L>(mine), Q * rs - pv.F) / den;
+    char* row = reinterpret_cast<char*>(s) + (size_t)y * s_pitch;
+    if (f64) reinterpret_cast<double*>(row)[myx] = v;
+    else reinterpret_cast<float*>(row)[myx] = (float)v;
+  }
+}
+
+template <int L>
+static cudaError_t launch_gen_L(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
+                                size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
+  dim3 grid((unsigned)((pv.W + 31) / 32), (unsigned)((pv.H + kGenWarps - 1) / kGenWarps));
+  if (pv.table_bytes_per_w == 16)
+    mesh_gen_kernel<L, ulonglong2><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s,
+                                                                    s_pitch, num, num_pitch, status);
+  else
+    mesh_gen_kernel<L, uint64_t><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s,
+                                                                  s_pitch, num, num_pitch, status);
+  return cudaGetLastError();
+}
+
+cudaError_t run_mesh_general(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
+                             size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
+  switch (pv.limbs) {
+    case 1: return launch_gen_L<1>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    case 2: return launch_gen_L<2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    case 3: return launch_gen_L<3>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    default: return launch_gen_L<4>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+  }
+}
+
+// ------------------------------------------------- prefilter, column pass
+
+// The second pass of the separable prefilter: along every column of the row
+// pass' output x (c_row 2^(F + G - 4), rows 0 .. H-1, zero above and below),
+// the causal and anti-causal recursions of each pole run over the whole
+// extended column, rows -T .. H+T-1; c 2^(F + G - 8) = sum_p A_p (y+ - x + y-)
+// is rounded to c_q = rint(c 2^F), ties to even.  One thread per column (the
+// warp's loads and stores are consecutive columns); the causal sums wait in
+// yf (npoles planes of (H + 2T) x W elements).
+__global__ void prefilter_cols_kernel(const PrefilterView v, int H, int T, int W, const long long* __restrict__ x,
+                                      long long x_pitch, long long* __restrict__ yf, long long* __restrict__ c,
+                                      long long c_pitch) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= W) return;
+  const int He = H + 2 * T;
+  const size_t plane = (size_t)He * W;
+  auto xin = [&](int ye) -> long long {
+    const int y = ye - T;
+    return (y >= 0 && y < H) ? x[(size_t)y * x_pitch + col] : 0ll;
+  };
+  for (int p = 0; p < v.npoles; ++p) {
+    long long y1 = 0;
+    const long long Z = v.Z[p];
+    for (int ye = 0; ye < He; ++ye) {
+      y1 = xin(ye) + __mul64hi(y1, Z);
+      yf[p * plane + (size_t)ye * W + col] = y1;
+    }
+  }
+  long long yb[kPfMaxPoles] = {0, 0};
+  const int sh = v.G - 8;
+  const long long half = 1ll << (sh - 1);
+  for (int ye = He - 1; ye >= 0; --ye) {
+    const long long xv = xin(ye);
+    long long acc = 0;
+    for (int p = 0; p < v.npoles; ++p) {
+      yb[p] = xv + __mul64hi(yb[p], v.Z[p]);
+      acc += __mul64hi(yf[p * plane + (size_t)ye * W + col] - xv, v.A[p]) + __mul64hi(yb[p], v.A[p]);
+    }
+    long long q = acc >> sh;  // floor
+    const long long rem = acc - q * (1ll << sh);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    c[(size_t)ye * c_pitch + col] = q;
+  }
+}
+
+}  // namespace abf
+
+// ---------------------------------------------------------------- host side
+
+using u128 = unsigned __int128;
+
+namespace {
+
+struct GenTable {
+  std::vector<uint8_t> bytes;  // (2^P)^2 rows x R weights, little-endian
+  std::vector<int2> stencil;   // the R neighbours (dx, dy)
+  u128 D = 0;
+  int wbytes = 0;
+};
+
+u128 gcd_u128(u128 a, u128 b) {
+  while (b) {
+    const u128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// The box spline M with the lattice directions v1..v4 taken m_k times: its
+// values at the integer points (the eigenvector of the refinement equation
+// restricted to them, found in floating point, snapped to a rational with
+// denominator 2 (N-2)! 2^t and verified exactly), refined to the 2^-P grid
+// (M(y) = 2^(2-N) sum_k a_k M(2y - k), a = the coefficients of
+// prod_k (1 + z^{v_k})^{m_k}), then one row per fractional offset.
+bool build_gen_table(const int m[4], int P, GenTable& out) {
+  const int V[4][2] = {{1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+  const int N = m[0] + m[1] + m[2] + m[3];
+  const int x0 = -m[3], x1 = m[0] + m[1], y1 = m[1] + m[2] + m[3];
+  const int mw = x1 - x0 + 1, mh = y1 + 1;
+  std::vector<int64_t> a((size_t)mw * mh, 0);
+  a[(size_t)(0 - x0)] = 1;
+  for (int k = 0; k < 4; ++k)
+    for (int rep = 0; rep < m[k]; ++rep) {
+      std::vector<int64_t> b = a;
+      for (int y = 0; y < mh; ++y)
+        for (int xi = 0; xi < mw; ++xi) {
+          const int64_t v = a[(size_t)y * mw + xi];
+          if (!v) continue;
+          const int nx = xi + V[k][0], ny = y + V[k][1];
+          if (nx < 0 || nx >= mw || ny >= mh) return false;
+          b[(size_t)ny * mw + nx] += v;
+        }
+      a.swap(b);
+    }
+  auto mask_at = [&](int kx, int ky) -> int64_t {
+    const int xi = kx - x0;
+    if (xi < 0 || xi >= mw || ky < 0 || ky >= mh) return 0;
+    return a[(size_t)ky * mw + xi];
+  };
+  const int npts = mw * mh;
+  std::vector<long double> v(npts, 1.0L / npts), nv(npts);
+  for (int it = 0; it < 600; ++it) {
+    long double sum = 0;
+    for (int p = 0; p < npts; ++p) {
+      const int px = p % mw + x0, py = p / mw;
+      long double acc = 0;
+      for (int q = 0; q < npts; ++q) {
+        const int64_t c = mask_at(2 * px - (q % mw + x0), 2 * py - q / mw);
+        if (c) acc += (long double)c * v[q];
+      }
+      nv[p] = acc;
+      sum += acc;
+    }
+    for (int p = 0; p < npts; ++p) v[p] = nv[p] / sum;
+  }
+  u128 Dc = 2;
+  for (int i = 2; i <= N - 2; ++i) Dc *= (u128)i;
+  std::vector<u128> Vq(npts);
+  bool ok = false;
+  for (int attempt = 0; attempt < 8 && !ok; ++attempt, Dc *= 2) {
+    ok = true;
+    u128 sum = 0;
+    for (int p = 0; p < npts; ++p) {
+      const long double xv = v[p] * (long double)Dc;
+      const long double r = std::floor(xv + 0.5L);
+      if (std::fabs((double)(xv - r)) > 1e-3 || r < 0) { ok = false; break; }
+      Vq[p] = (u128)r;
+      sum += Vq[p];
+    }
+    if (!ok || sum != Dc) { ok = false; continue; }
+    const u128 scale = (u128)1 << (N - 2);
+    for (int p = 0; p < npts && ok; ++p) {
+      const int px = p % mw + x0, py = p / mw;
+      u128 acc = 0;
+      for (int q = 0; q < npts; ++q) {
+        const int64_t c = mask_at(2 * px - (q % mw + x0), 2 * py - q / mw);
+        if (c) acc += (u128)c * Vq[q];
+      }
+      if (acc != scale * Vq[p]) ok = false;
+    }
+  }
+  if (!ok) return false;
+  u128 gg = 0;
+  for (int p = 0; p < npts; ++p) gg = gcd_u128(gg, Vq[p]);
+  if (gg == 0) return false;
+  Dc /= 2;  // the loop doubled it once more after success
+  const u128 D0 = Dc / gg;
+  for (int p = 0; p < npts; ++p) Vq[p] /= gg;
+  int d0bits = 0;
+  for (u128 t = D0; t; t >>= 1) ++d0bits;
+  if (d0bits + (N - 2) * P > 126) return false;  // D < 2^126: one 128-bit weight word
+  // refinement cascade: level l point (i, j) <-> (x0 + i 2^-l, j 2^-l)
+  std::vector<u128> cur(Vq), nxt;
+  int sx = mw, sy = mh;
+  std::vector<std::tuple<int, int, int64_t>> mk;
+  for (int ky = 0; ky < mh; ++ky)
+    for (int kx = x0; kx <= x1; ++kx)
+      if (mask_at(kx, ky)) mk.emplace_back(kx, ky, mask_at(kx, ky));
+  for (int l = 1; l <= P; ++l) {
+    const int nsx = (mw - 1) * (1 << l) + 1, nsy = (mh - 1) * (1 << l) + 1;
+    nxt.assign((size_t)nsx * nsy, 0);
+    const int h = 1 << (l - 1);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < nsy; ++j)
+      for (int i = 0; i < nsx; ++i) {
+        u128 acc = 0;
+        for (const auto& t : mk) {
+          const int ip = i + (x0 - std::get<0>(t)) * h;
+          const int jp = j - std::get<1>(t) * h;
+          if (ip < 0 || ip >= sx || jp < 0 || jp >= sy) continue;
+          acc += (u128)std::get<2>(t) * cur[(size_t)jp * sx + ip];
+        }
+        nxt[(size_t)j * nsx + i] = acc;
+      }
+    cur.swap(nxt);
+    sx = nsx;
+    sy = nsy;
+  }
+  const u128 D = D0 << ((N - 2) * P);
+  const int one = 1 << P;
+  // centre of the uncentred kernel, units 2^-P
+  const long CX = (long)(m[0] + m[1] - m[3]) * (one / 2), CY = (long)(m[1] + m[2] + m[3]) * (one / 2);
+  auto weight = [&](int rx, int ry, int dx, int dy) -> u128 {
+    const long X = (long)rx - (long)dx * one + CX, Y = (long)ry - (long)dy * one + CY;
+    const long i = X - (long)x0 * one, j = Y;
+    if (i < 0 || i >= sx || j < 0 || j >= sy) return 0;
+    return cur[(size_t)j * sx + i];
+  };
+  // candidate neighbours: the centred support lies in |x| <= (x1 - x0)/2, |y| <= y1/2
+  const int hx = (x1 - x0) / 2 + 2, hy = y1 / 2 + 2;
+  std::vector<int2> cand;
+  for (int dy = -hy; dy <= hy; ++dy)
+    for (int dx = -hx; dx <= hx; ++dx) {
+      bool any = false;
+      for (int ry = 0; ry < one && !any; ++ry)
+        for (int rx = 0; rx < one && !any; ++rx) any = weight(rx, ry, dx, dy) != 0;
+      if (any) cand.push_back(make_int2(dx, dy));
+    }
+  const int R = (int)cand.size();
+  if (R < 1 || R > abf::kGenMaxR) return false;
+  const int wb = D < ((u128)1 << 64) ? 8 : 16;
+  const size_t rows = (size_t)one * one;
+  out.bytes.assign(rows * R * wb, 0);
+  bool sums_ok = true;
+#pragma omp parallel for schedule(static) reduction(&& : sums_ok)
+  for (int ry = 0; ry < one; ++ry)
+    for (int rx = 0; rx < one; ++rx) {
+      u128 rowsum = 0;
+      for (int c = 0; c < R; ++c) {
+        const u128 w = weight(rx, ry, cand[c].x, cand[c].y);
+        rowsum += w;
+        uint8_t* dst = &out.bytes[(((size_t)ry * one + rx) * R + c) * wb];
+        for (int b = 0; b < wb; ++b) dst[b] = (uint8_t)(w >> (8 * b));
+      }
+      if (rowsum != D) sums_ok = false;  // unit lattice sum: the kernel holds unit v1 and v3
+    }
+  if (!sums_ok) return false;
+  out.stencil = cand;
+  out.D = D;
+  out.wbytes = wb;
+  return true;
+}
+
+struct GenDevTable {
+  void* ptr = nullptr;
+  int2* stencil = nullptr;
+  int R = 0, wbytes = 0;
+  u128 D = 0;
+};
+
+std::mutex g_gen_mu;
+std::map<std::tuple<int, int, int, int, int, int>, GenDevTable> g_gen_tables;  // (device, m1..m4, P); until exit
+
+abf_status get_gen_table(int device, const int m[4], int P, GenDevTable* out) {
+  std::lock_guard<std::mutex> lk(g_gen_mu);
+  const auto key = std::make_tuple(device, m[0], m[1], m[2], m[3], P);
+  auto it = g_gen_tables.find(key);
+  if (it != g_gen_tables.end()) {
+    *out = it->second;
+    return ABF_OK;
+  }
+  GenTable ht;
+  try {
+    if (!build_gen_table(m, P, ht)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  GenDevTable dt;
+  dt.R = (int)ht.stencil.size();
+  dt.wbytes = ht.wbytes;
+  dt.D = ht.D;
+  if (cudaMalloc(&dt.ptr, ht.bytes.size()) != cudaSuccess) return ABF_ERR_OOM;
+  if (cudaMalloc((void**)&dt.stencil, ht.stencil.size() * sizeof(int2)) != cudaSuccess) {
+    cudaFree(dt.ptr);
+    return ABF_ERR_OOM;
+  }
+  if (cudaMemcpy(dt.ptr, ht.bytes.data(), ht.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dt.stencil, ht.stencil.data(), ht.stencil.size() * sizeof(int2), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaFree(dt.ptr);
+    cudaFree(dt.stencil);
+    return ABF_ERR_CUDA;
+  }
+  g_gen_tables[key] = dt;
+  *out = dt;
+  return ABF_OK;
+}
+
+double u128_d(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073709551616.0 + (double)(uint64_t)v; }
+
+}  // namespace
+
+namespace abf {
+
+// Plan for N = 2 or a model (abf_plan_create hands these over); the
+// descriptor has been validated as for the plain plans.
+abf_status create_general_plan(const abf_desc* d, abf_plan p) {
+  const int n = d->order_n, N = d->directions == 2 ? 2 : 4, E = d->model_boxes;
+  if (E < 0 || E > 6) return ABF_ERR_INVALID;
+  if (N == 2 && E == 0 && n < 2) return ABF_ERR_UNSUPPORTED;  // rect: a discontinuous kernel
+  if (N == 2 && d->scale_kind == ABF_SCALES_ELLIPSE) return ABF_ERR_INVALID;
+  const int Q = d->q_bits, P = Q + 1;
+  if (Q > 7) return ABF_ERR_UNSUPPORTED;   // table of (2^(Q+1))^2 rows
+  int r[4] = {n, N == 4 ? n : 0, n, N == 4 ? n : 0};
+  int m[4] = {r[0] + E, r[1], r[2] + E, r[3]};
+  const int dev = p->device;
+  GenDevTable tab;
+  abf_status s = get_gen_table(dev, m, P, &tab);
+  if (s != ABF_OK) return s;
+  const double qd = std::ldexp(1.0, Q);
+  const int Cmax = (int)std::lrint(d->max_scale * qd);
+  const double min_scale = d->min_scale > 0 ? d->min_scale : 1.0;
+  int Cmin = (int)std::ceil(min_scale * qd - 1e-9);
+  if (Cmin < 1) Cmin = 1;
+  double vb = d->value_bound;
+  if (!(vb > 0)) vb = d->in_dtype == ABF_U8 ? 255.0 : (d->in_dtype == ABF_U16 ? 65535.0 : 0.0);
+  if (!(vb > 0)) return ABF_ERR_INVALID;
+  // model coefficients and their bound
+  const double xmax = std::ldexp(vb, d->in_frac_bits);
+  PrefilterView pf{};
+  double hnorm = 1.0, cbound = vb;
+  int T = 0;
+  const int n1 = E - 1;
+  if (E >= 3) {
+    s = prefilter2d_setup(n1, xmax, &pf, &hnorm, &T);
+    if (s != ABF_OK) return s;
+    cbound = hnorm * hnorm * vb + std::ldexp(1.0, -d->in_frac_bits);
+  }
+  // limbs: |S| <= D prod_k c_k^{r_k} |c|max 2^F (unit lattice sum with a model;
+  // (1 + 1/c1)(1 + 1/c3) for phi = delta)
+  const double cmax = (double)Cmax / qd, cmin = (double)Cmin / qd;
+  double lp = 0.0;
+  for (int k = 0; k < 4; ++k) lp += r[k] * std::log2(cmax);
+  if (d->max_scale_product > 0 && N == 4) lp = n * std::log2(d->max_scale_product);
+  const double lb = std::log2(u128_d(tab.D)) + lp + std::log2(cbound) + d->in_frac_bits +
+                    (E == 0 ? 2.0 * std::log2(1.0 + 1.0 / cmin) : 0.0) + 1e-6;
+  const int L = (int)std::floor((lb + 1.0) / 64.0) + 1;
+  if (L > kMaxLimbs) return ABF_ERR_RANGE;
+  // lattice box: taps within sum_k r_k (cmax + 1) |v_k| of the pixel, plus the stencil
+  double ex = 0.0, ey = 0.0;
+  const int V[4][2] = {{1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+  for (int k = 0; k < 4; ++k) {
+    ex += r[k] * (cmax + 1.0) * std::abs(V[k][0]);
+    ey += r[k] * (cmax + 1.0) * std::abs(V[k][1]);
+  }
+  int dminx = 0, dmaxx = 0, dminy = 0, dmaxy = 0;
+  {
+    std::vector<int2> st((size_t)tab.R);
+    if (cudaMemcpy(st.data(), tab.stencil, st.size() * sizeof(int2), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return ABF_ERR_CUDA;
+    for (const int2& q : st) {
+      dminx = std::min(dminx, q.x); dmaxx = std::max(dmaxx, q.x);
+      dminy = std::min(dminy, q.y); dmaxy = std::max(dmaxy, q.y);
+    }
+  }
+  const int Wi = d->width + 2 * T, Hi = d->height + 2 * T;
+  PlanView& pv = p->pv;
+  pv = PlanView{};
+  pv.W = d->width; pv.H = d->height; pv.n = n; pv.Q = Q; pv.P = P; pv.F = d->in_frac_bits;
+  pv.left = (int)std::ceil(ex) - dminx + 2;
+  pv.right = (int)std::ceil(ex) + dmaxx + 2;
+  pv.above = (int)std::ceil(ey) + dmaxy + 2;
+  pv.Gw = Wi + pv.left + pv.right;
+  pv.Gh = Hi + pv.above;
+  pv.Gp = ((long long)pv.Gw + 3) / 4 * 4;
+  if ((long long)(pv.Gh + 8) * pv.Gp >= (1ll << 40)) return ABF_ERR_INVALID;
+  pv.Cmax = Cmax; pv.Cmin = Cmin;
+  pv.scale_kind = d->scale_kind; pv.in_dtype = d->in_dtype; pv.out_dtype = d->out_dtype;
+  pv.limbs = L;
+  pv.value_bound = vb;
+  pv.log2D = std::log2(u128_d(tab.D));
+  pv.log2_base = (float)(pv.log2D + std::log2(cbound) + d->in_frac_bits);
+  pv.Dd = u128_d(tab.D);
+  pv.table_bytes_per_w = tab.wbytes;
+  pv.table = tab.ptr;
+  pv.table_fold = nullptr;
+  for (int k = 0; k < 4; ++k) pv.r[k] = r[k];
+  pv.E = E;
+  pv.R = tab.R;
+  pv.stencil = tab.stencil;
+  pv.ox = T;
+  pv.oy = T;
+  p->D = tab.D;
+  // the running sums' view: the image (E < 3) or the staged c_q frame
+  PlanView& sv = p->sv;
+  sv = pv;
+  sv.W = Wi;
+  sv.H = Hi;
+  sv.F = d->in_frac_bits;
+  if (E >= 3) {
+    sv.in_dtype = kStageI64;
+    pf.length = d->width;
+    pf.Gw = Wi;
+    pf.left = T;
+    pf.scale = std::ldexp(1.0, d->in_frac_bits);
+    const double bd = std::floor(xmax);
+    pf.bound = bd < 4.0e18 ? (long long)bd : 4000000000000000000ll;
+    PrefilterView* hp = new (std::nothrow) PrefilterView(pf);
+    if (!hp) return ABF_ERR_OOM;
+    p->pf = hp;
+    const size_t stage = (size_t)Wi * Hi * 8;
+    const size_t inter = (size_t)Wi * d->height * 8;
+    const size_t yf = (size_t)pf.npoles * Wi * Hi * 8;
+    p->pf_tmp_bytes = inter + yf;
+    if (cudaMalloc(&p->d_stage, stage) != cudaSuccess) return ABF_ERR_OOM;
+    if (cudaMalloc(&p->d_pf_tmp, p->pf_tmp_bytes) != cudaSuccess) return ABF_ERR_OOM;
+  }
+  p->general = true;
+  p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
+  p->ws_bytes = line_ws_bytes(pv.Gw, pv.Gh, L, n, nullptr, nullptr);
+  return ABF_OK;
+}
+
+void destroy_general_plan(abf_plan p) {
+  if (p->d_stage) cudaFree(p->d_stage);
+  if (p->d_pf_tmp) cudaFree(p->d_pf_tmp);
+  delete (PrefilterView*)p->pf;
+  p->d_stage = p->d_pf_tmp = nullptr;
+  p->pf = nullptr;
+}
+
+// Non-adaptive step of a generalised plan: the model's prefilter when it has
+// one (rows, then columns into the staged c_q frame), then the running sums
+// of the running sums' view.
+cudaError_t run_integrate_general(abf_plan p, const void* f, size_t f_pitch, uint64_t* g, void* ws, uint32_t* epoch,
+                                  int32_t* status, cudaStream_t st) {
+  if (p->pv.E >= 3) {
+    const PrefilterView& pf = *(const PrefilterView*)p->pf;
+    const int W = p->pv.W, H = p->pv.H, T = p->pv.ox, Wi = p->sv.W;
+    long long* inter = (long long*)p->d_pf_tmp;
+    long long* yf = inter + (size_t)Wi * H;
+    cudaError_t e = run_prefilter_rows_raw(pf, H, p->desc.in_dtype, f, f_pitch, inter, Wi, status, st);
+    if (e != cudaSuccess) return e;
+    (void)W;
+    prefilter_cols_kernel<<<(Wi + 127) / 128, 128, 0, st>>>(pf, H, T, Wi, inter, Wi, yf, (long long*)p->d_stage, Wi);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return run_integrate(p->sv, p->d_stage, (size_t)Wi * 8, g, ws, epoch, status, st);
+  }
+  return run_integrate(p->sv, f, f_pitch, g, ws, epoch, status, st);
+}
+
+// Host-only: the generalised interpolation table (for checks against the
+// oracle without a device).
+bool general_table_host(const int m[4], int P, std::vector<uint8_t>& bytes, std::vector<int2>& stencil, u128* D,
+                        int* wbytes) {
+  GenTable t;
+  if (!build_gen_table(m, P, t)) return false;
+  bytes.swap(t.bytes);
+  stencil.swap(t.stencil);
+  *D = t.D;
+  *wbytes = t.wbytes;
+  return true;
+}
+
+}  // namespace abf

@@ -206,23 +206,15 @@ static cudaError_t run_mesh1d(const Line1dView& v, const uint64_t* g, const floa
 constexpr int kPfThreads = 128;
 constexpr int kPfSeg = 32;                          // outputs per thread
 constexpr int kPfTile = kPfThreads * kPfSeg;        // outputs per CTA
-constexpr int kPfHalo = 64;                         // >= every W_p
 constexpr int kPfStage = kPfTile + 2 * kPfHalo;     // staged samples
 constexpr int kPfSmem = kPfStage + kPfStage / 32 + 1;
-constexpr int kPfMaxPoles = 2;
-
-struct PrefilterView {
-  int length, Gw, left, G, npoles;
-  int W[kPfMaxPoles];            // warm-up samples per pole
-  long long Z[kPfMaxPoles];      // rint(z_p 2^64)
-  long long A[kPfMaxPoles];      // rint(A_p 2^60)
-  double scale;                  // 2^F
-  long long bound;               // floor(value_bound 2^F)
-};
 
 __device__ __forceinline__ int pf_pad(int j) { return j + (j >> 5); }
 
-template <typename TIn, typename TOut>
+// ROUND = false (the first, row-wise pass of the 2-D model's separable
+// prefilter): the sums are written as they are, c 2^(F + G - 4), for the
+// column pass to continue from.
+template <typename TIn, typename TOut, bool ROUND = true>
 __global__ void __launch_bounds__(kPfThreads, 3) prefilter_kernel(const PrefilterView v, const TIn* __restrict__ f,
                                                                   size_t f_pitch, TOut* __restrict__ c,
                                                                   long long c_pitch, int32_t* status) {
@@ -268,9 +260,12 @@ __global__ void __launch_bounds__(kPfThreads, 3) prefilter_kernel(const Prefilte
   const long long half = 1ll << (sh - 1);
 #pragma unroll
   for (int e = 0; e < kPfSeg; ++e) {
-    long long q = acc[e] >> sh;  // floor
-    const long long r = acc[e] - q * (1ll << sh);
-    if (r > half || (r == half && (q & 1))) ++q;
+    long long q = acc[e];
+    if (ROUND) {
+      q = acc[e] >> sh;  // floor
+      const long long r = acc[e] - q * (1ll << sh);
+      if (r > half || (r == half && (q & 1))) ++q;
+    }
     sx[pf_pad(threadIdx.x * kPfSeg + e)] = q;
   }
   __syncthreads();
@@ -292,6 +287,26 @@ static cudaError_t launch_prefilter_in(const PrefilterView& v, int count, const 
     prefilter_kernel<TIn, int32_t><<<grid, kPfThreads, 0, st>>>(v, (const TIn*)f, f_pitch, (int32_t*)c, c_pitch,
                                                                 status);
   return cudaGetLastError();
+}
+
+// The row-wise first pass of the 2-D model's prefilter: unrounded sums
+// c_row 2^(F + G - 4) as int64, rows of v.Gw elements (pitch c_pitch elements).
+template <typename TIn>
+static cudaError_t launch_prefilter_raw(const PrefilterView& v, int count, const void* f, size_t f_pitch,
+                                        long long* c, long long c_pitch, int32_t* status, cudaStream_t st) {
+  dim3 grid((unsigned)((v.Gw + kPfTile - 1) / kPfTile), (unsigned)count);
+  prefilter_kernel<TIn, long long, false><<<grid, kPfThreads, 0, st>>>(v, (const TIn*)f, f_pitch, c, c_pitch, status);
+  return cudaGetLastError();
+}
+
+cudaError_t run_prefilter_rows_raw(const PrefilterView& v, int count, int in_dtype, const void* f, size_t f_pitch,
+                                   long long* c, long long c_pitch, int32_t* status, cudaStream_t st) {
+  switch (in_dtype) {
+    case ABF_U8: return launch_prefilter_raw<uint8_t>(v, count, f, f_pitch, c, c_pitch, status, st);
+    case ABF_U16: return launch_prefilter_raw<uint16_t>(v, count, f, f_pitch, c, c_pitch, status, st);
+    case ABF_F32: return launch_prefilter_raw<float>(v, count, f, f_pitch, c, c_pitch, status, st);
+    default: return launch_prefilter_raw<double>(v, count, f, f_pitch, c, c_pitch, status, st);
+  }
 }
 
 static cudaError_t run_prefilter(const PrefilterView& v, int count, int in_dtype, const void* f, size_t f_pitch,
@@ -400,6 +415,45 @@ static bool interp_poles(int n1, PoleSet& ps) {
   }
   return true;
 }
+
+namespace abf {
+// Constants of the 2-D model's separable prefilter (degree n1 in 2..5; the
+// same recursions as the 1-D filter's, run along rows and then along
+// columns): poles and weights in 64-bit fixed point, guard bits G for samples
+// up to xmax = |f|max 2^F, and the tail T of coefficients kept beyond each
+// image edge (beyond it |c| 2^F < 1/4, counting the other axis' gain hnorm).
+abf_status prefilter2d_setup(int n1, double xmax, PrefilterView* pf, double* hnorm, int* tail) {
+  PoleSet ps{};
+  if (!interp_poles(n1, ps)) return ABF_ERR_UNSUPPORTED;
+  double zmax = 0.0;
+  for (int q = 0; q < ps.M; ++q) zmax = std::max(zmax, std::fabs(ps.z[q]));
+  const double x2 = xmax * ps.hnorm;  // the column pass' input bound
+  const int G = (int)std::floor(61.0 - std::log2(std::max(xmax, x2) * (2.0 / (1.0 - zmax) + 1.0)));
+  if (G < 24) return ABF_ERR_RANGE;
+  *pf = PrefilterView{};
+  pf->G = std::min(G, 40);
+  pf->npoles = ps.M;
+  for (int q = 0; q < ps.M; ++q) {
+    const double az = std::fabs(ps.z[q]);
+    pf->W[q] = std::min(kPfHalo, (int)std::ceil(66.0 / -std::log2(az)));
+    pf->Z[q] = std::llrint(std::ldexp(ps.z[q], 64));
+    pf->A[q] = std::llrint(std::ldexp(ps.A[q], 60));
+    if (!(std::fabs(ps.A[q]) < 7.0)) return ABF_ERR_UNSUPPORTED;
+  }
+  int T = 0;
+  for (; T < 4096; ++T) {
+    double t = 0.0;
+    for (int q = 0; q < ps.M; ++q) {
+      const double az = std::fabs(ps.z[q]);
+      t += std::fabs(ps.A[q]) * std::pow(az, T + 1) / (1.0 - az);
+    }
+    if (x2 * t < 0.25) break;
+  }
+  *hnorm = ps.hnorm;
+  *tail = T;
+  return ABF_OK;
+}
+}  // namespace abf
 
 struct abf1d_plan_s {
   abf1d_desc desc;
@@ -513,6 +567,7 @@ abf_status abf1d_plan_create(const abf1d_desc* d, abf1d_plan* out) {
   abf::PlanView& r = p->rows;
   r = abf::PlanView{};
   r.H = d->count; r.n = d->n2 + 1; r.Q = d->q_bits; r.P = P; r.F = d->in_frac_bits;
+  r.r[0] = d->n2 + 1;  // the row pass: n2 + 1 cascaded sums
   r.above = 0; r.Gw = (int)Gw; r.Gh = d->count; r.Gp = v.Gp;
   r.out_dtype = d->out_dtype; r.limbs = L; r.value_bound = vb;
   if (d->n1 >= 2) {

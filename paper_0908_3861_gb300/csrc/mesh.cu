@@ -43,33 +43,6 @@ __device__ __forceinline__ int signed_binom(int j) {
   return (j & 1) ? -c : c;
 }
 
-// Weight table element types per order: D < 2^32 (n = 1), < 2^60 (n = 2), < 2^121 (n = 3)
-// (room for the FD weight |w_j| <= 16, resp. 81, folded into the table weight).
-template <int N> struct WeightT;
-template <> struct WeightT<1> { using T = uint32_t; };
-template <> struct WeightT<2> { using T = uint64_t; };
-template <> struct WeightT<3> { using T = ulonglong2; };
-
-// acc += g * w for the table word types.
-template <int L, typename WT>
-__device__ __forceinline__ void mac_weight(Wide<L>& acc, const Wide<L>& gv, const WT w) {
-  if constexpr (sizeof(WT) == 16) {
-    if constexpr (L == 1) wmac<1>(acc, gv, w.x);
-    else if constexpr (L == 2) wmac_w4_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
-    else if constexpr (L == 3) wmac_w6_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
-    else wmac_w8_b4(acc, gv, (uint32_t)w.x, (uint32_t)(w.x >> 32), (uint32_t)w.y, (uint32_t)(w.y >> 32));
-  } else if constexpr (sizeof(WT) == 8) {
-    if constexpr (L == 1) wmac<1>(acc, gv, w);
-    else if constexpr (L == 2) wmac2_u64(acc, gv, w);
-    else if constexpr (L == 3) wmac_w6_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
-    else wmac_w8_b2(acc, gv, (uint32_t)w, (uint32_t)(w >> 32));
-  } else if constexpr (L == 2) {
-    wmac2_u32(acc, gv, w);
-  } else {
-    wmac<L>(acc, gv, (uint64_t)w);
-  }
-}
-
 // Table weight times the FD weight |w_j| (a power of two for n <= 2).
 template <int N, typename WT>
 __device__ __forceinline__ WT scale_weight(WT w, int aw) {

@@ -60,6 +60,14 @@ struct IntIn {
   int32_t* status;
 };
 int integrate_batch_max_jobs();
+abf_status create_general_plan(const abf_desc* d, abf_plan p);
+void destroy_general_plan(abf_plan p);
+cudaError_t run_integrate_general(abf_plan p, const void* f, size_t f_pitch, uint64_t* g, void* ws, uint32_t* epoch,
+                                  int32_t* status, cudaStream_t st);
+cudaError_t run_mesh_general(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
+                             size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st);
+bool general_table_host(const int m[4], int P, std::vector<uint8_t>& bytes, std::vector<int2>& stencil,
+                        unsigned __int128* D, int* wbytes);
 cudaError_t run_integrate_batch(const IntIn* in, int njobs, uint32_t* ws, uint32_t epoch0, cudaStream_t st);
 }  // namespace abf
 
@@ -459,6 +467,8 @@ abf_status abf::integrate_with_status(abf_plan p, const void* d_f, size_t f_pitc
   if (f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
   if (((uintptr_t)d_g & 15) || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
   uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
+  if (p->general)
+    return cuda_status(abf::run_integrate_general(p, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, d_status, st));
   return cuda_status(abf::run_integrate(p->pv, d_f, f_pitch, (uint64_t*)d_g, d_ws, &ep, d_status, st));
 }
 
@@ -469,6 +479,9 @@ abf_status abf::filter_with_status(abf_plan p, const void* d_g, const void* d_sc
   const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
   if (scale_pitch < (size_t)p->pv.W * 16 || s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  if (p->general)
+    return cuda_status(abf::run_mesh_general(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, d_s, s_pitch, nullptr,
+                                             0, d_status, st));
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, d_s, s_pitch, nullptr, 0,
                                          d_status, p->mesh_warps, st));
 }
@@ -523,6 +536,10 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   }
   // binary32 pairs reach 1e-5 (times the value bound) at order 1 only: see abf.h
   if (d->form == ABF_FORM_TILE_F32 && n != 1) return ABF_ERR_UNSUPPORTED;
+  if (d->directions != 0 && d->directions != 2 && d->directions != 4) return ABF_ERR_INVALID;
+  if (d->model_boxes < 0 || d->model_boxes > 6) return ABF_ERR_INVALID;
+  const bool general = d->directions == 2 || d->model_boxes > 0;
+  if (general && !exact) return ABF_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
 
@@ -530,6 +547,19 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (!p) return ABF_ERR_OOM;
   p->desc = *d;
   p->device = dev;
+  if (general) {
+    abf_status gs = abf::create_general_plan(d, p);
+    if (gs == ABF_OK && cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) gs = ABF_ERR_OOM;
+    if (gs == ABF_OK && cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) gs = ABF_ERR_CUDA;
+    if (gs != ABF_OK) {
+      abf::destroy_general_plan(p);
+      if (p->d_status) cudaFree(p->d_status);
+      delete p;
+      return gs;
+    }
+    *out = p;
+    return ABF_OK;
+  }
   DeviceTable tab;
   abf_status s = get_table(dev, n, P, &tab);
   if (s != ABF_OK) { delete p; return s; }
@@ -566,6 +596,9 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   pv.table_bytes_per_w = tab.wbytes;
   pv.table = tab.ptr;
   pv.table_fold = tab.fold;
+  for (int k = 0; k < 4; ++k) pv.r[k] = n;
+  pv.E = 0;
+  pv.ox = pv.oy = 0;
   if (exact) {
     p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
     p->ws_bytes = abf::line_ws_bytes(pv.Gw, pv.Gh, L, n, nullptr, nullptr);
@@ -591,6 +624,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
 
 abf_status abf_plan_destroy(abf_plan p) {
   if (!p) return ABF_ERR_INVALID;
+  if (p->general) abf::destroy_general_plan(p);
   if (p->d_status) cudaFree(p->d_status);
   delete p;
   return ABF_OK;
@@ -640,7 +674,7 @@ abf_status abf_integrate_noalloc(abf_plan p, const void* d_f, size_t f_pitch, vo
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
   if (dev != p->device) return ABF_ERR_INVALID;
-  if (p->ws_bytes > abf::noalloc_scratch_bytes()) return ABF_ERR_UNSUPPORTED;
+  if (p->ws_bytes > abf::noalloc_scratch_bytes() || p->general) return ABF_ERR_UNSUPPORTED;
   uint32_t ep = reserve_epochs(3u * (uint32_t)p->pv.n);
   return cuda_status(abf::run_integrate_noalloc(p->pv, d_f, f_pitch, (uint64_t*)d_g, &ep, p->d_status, st));
 }
@@ -668,6 +702,9 @@ abf_status abf_filter_numerator(abf_plan p, const void* d_g, const void* d_scale
   if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
   if (scale_pitch < (size_t)p->pv.W * 16 || num_pitch < (size_t)p->pv.W * 8 * p->pv.limbs) return ABF_ERR_INVALID;
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;
+  if (p->general)
+    return cuda_status(abf::run_mesh_general(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, nullptr, 0,
+                                             (uint64_t*)d_num, num_pitch, p->d_status, st));
   return cuda_status(abf::run_mesh_exact(p->pv, (const uint64_t*)d_g, d_scales, scale_pitch, nullptr, 0,
                                          (uint64_t*)d_num, num_pitch, p->d_status, p->mesh_warps, st));
 }
@@ -688,7 +725,7 @@ static abf_status batch_inputs(const abf_job* jobs, int32_t njobs, std::vector<a
     const abf_job& j = jobs[i];
     abf_plan p = j.plan;
     if (!p || !j.d_g || !j.d_scales || !j.d_s) return ABF_ERR_INVALID;
-    if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+    if (p->desc.form != ABF_FORM_EXACT || p->general) return ABF_ERR_UNSUPPORTED;
     const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
     if (j.scale_pitch < (size_t)p->pv.W * 16 || j.s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
     if (((uintptr_t)j.d_scales & 15) || (j.scale_pitch & 15)) return ABF_ERR_INVALID;
@@ -765,7 +802,7 @@ abf_status abf_integrate_batch(const abf_integrate_job* jobs, int32_t njobs, voi
     const abf_integrate_job& j = jobs[i];
     abf_plan p = j.plan;
     if (!p || !j.d_f || !j.d_g || !j.d_ws) return ABF_ERR_INVALID;
-    if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+    if (p->desc.form != ABF_FORM_EXACT || p->general) return ABF_ERR_UNSUPPORTED;
     const size_t esz = p->pv.in_dtype == ABF_U8 ? 1 : p->pv.in_dtype == ABF_U16 ? 2 : p->pv.in_dtype == ABF_F32 ? 4 : 8;
     if (j.f_pitch < (size_t)p->pv.W * esz) return ABF_ERR_INVALID;
     if (((uintptr_t)j.d_g & 15) || ((uintptr_t)j.d_ws & 15)) return ABF_ERR_INVALID;
@@ -781,6 +818,38 @@ abf_status abf_integrate_batch(const abf_integrate_job* jobs, int32_t njobs, voi
 }
 
 int32_t abf_integrate_batch_max_jobs(void) { return abf::integrate_batch_max_jobs(); }
+
+abf_status abf_general_table_host(int32_t directions, int32_t n, int32_t model_boxes, int32_t q_bits, void* out,
+                                  size_t out_bytes, size_t* needed_bytes, int32_t* wbytes, int32_t* R,
+                                  int32_t* stencil_xy, uint32_t* D_words4) {
+  if (directions != 2 && directions != 4) return ABF_ERR_INVALID;
+  if (n < 1 || n > 3 || model_boxes < 0 || model_boxes > 6 || q_bits < 1 || q_bits > 7) return ABF_ERR_INVALID;
+  const int m[4] = {n + model_boxes, directions == 4 ? n : 0, n + model_boxes, directions == 4 ? n : 0};
+  std::vector<uint8_t> bytes;
+  std::vector<int2> st;
+  u128 D = 0;
+  int wb = 0;
+  try {
+    if (!abf::general_table_host(m, q_bits + 1, bytes, st, &D, &wb)) return ABF_ERR_UNSUPPORTED;
+  } catch (const std::bad_alloc&) {
+    return ABF_ERR_OOM;
+  }
+  if (needed_bytes) *needed_bytes = bytes.size();
+  if (wbytes) *wbytes = wb;
+  if (R) *R = (int32_t)st.size();
+  if (stencil_xy)
+    for (size_t i = 0; i < st.size() && i < 256; ++i) {
+      stencil_xy[2 * i] = st[i].x;
+      stencil_xy[2 * i + 1] = st[i].y;
+    }
+  if (D_words4)
+    for (int i = 0; i < 4; ++i) D_words4[i] = (uint32_t)(D >> (32 * i));
+  if (out) {
+    if (out_bytes < bytes.size()) return ABF_ERR_INVALID;
+    std::memcpy(out, bytes.data(), bytes.size());
+  }
+  return ABF_OK;
+}
 
 abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t st) {
   if (!jobs || njobs < 0 || !d_ws || ws_bytes < 256 || ((uintptr_t)d_ws & 15)) return ABF_ERR_INVALID;
@@ -801,7 +870,7 @@ abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size
 abf_status abf_plan_autotune(abf_plan p, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_s,
                              size_t s_pitch, cudaStream_t st, int32_t* warps_out, float* ms3) {
   if (!p || !d_g || !d_scales || !d_s) return ABF_ERR_INVALID;
-  if (p->desc.form != ABF_FORM_EXACT) return ABF_ERR_UNSUPPORTED;
+  if (p->desc.form != ABF_FORM_EXACT || p->general) return ABF_ERR_UNSUPPORTED;
   const size_t osz = p->pv.out_dtype == ABF_F64 ? 8 : 4;
   if (scale_pitch < (size_t)p->pv.W * 16 || s_pitch < (size_t)p->pv.W * osz) return ABF_ERR_INVALID;
   if (((uintptr_t)d_scales & 15) || (scale_pitch & 15)) return ABF_ERR_INVALID;

@@ -217,7 +217,7 @@ __host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 32 : 16; }
 template <int L>
 __host__ __device__ constexpr int band_smem_bytes() { return kBand * lines_per_cta<L>() * L * 8; }
 constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;
-constexpr long long kSpinLimit = 1ll << 22;
+constexpr long long kSpinLimit = 1ll << 20;  // polls, 100 ns apart: about a second
 
 struct LineWs {
   uint32_t* flags;    // [nbands][nlines]
@@ -342,8 +342,7 @@ __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __r
   if (line_ok) {
     if (band > 0) {
       st_store<L, NF>(ws.agg + slot * NF * L, agg);
-      __threadfence();
-      st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);
+      st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);  // release: the aggregate is visible first
       // Up to kLook predecessor flags are read per round trip (relaxed loads,
       // then one acquire fence before the values they publish are read): the
       // walk back to the nearest published prefix takes a quarter of the trips.
@@ -373,6 +372,7 @@ __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __r
             raise_status(status, ABF_DEV_TIMEOUT);
             break;
           }
+          __nanosleep(100);  // back off: waiting CTAs should not crowd the flags' L2 lines
           continue;
         }
         fence_acquire();
@@ -392,7 +392,6 @@ __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __r
     LineState<L, NF> incl = agg;
     st_add_transported<L, NF>(incl, carry, kBand);
     st_store<L, NF>(ws.pref + slot * NF * L, incl);
-    __threadfence();
     st_release(ws.flags + slot, (epoch << 2) | kFlagPrefix);
   }
 
@@ -426,20 +425,23 @@ __global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const Pla
 
 // ----------------------------------------------------------------- launchers
 
+// The row pass: r1 running sums along v1 (the 1-D filter's plans keep r1 = n,
+// the number of cascaded sums of its rows).
 template <int L, typename TIn>
 static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g,
                                int32_t* status, cudaStream_t st) {
   const int blocks = pv.Gh;  // one CTA per row
   const int threads = 32 * kRowWarps;
   const TIn* fin = (const TIn*)f;
-  if (pv.n == 1) row_scan_kernel<L, TIn, 1><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
-  else if (pv.n == 2) row_scan_kernel<L, TIn, 2><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
-  else if (pv.n == 3) row_scan_kernel<L, TIn, 3><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+  const int nf = pv.r[0];
+  if (nf == 1) row_scan_kernel<L, TIn, 1><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+  else if (nf == 2) row_scan_kernel<L, TIn, 2><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+  else if (nf == 3) row_scan_kernel<L, TIn, 3><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
   else row_scan_kernel<L, TIn, 4><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
   return cudaGetLastError();
 }
 
-// The row pass alone (pv.n cascaded sums, 1..4, along rows of the box), for
+// The row pass alone (pv.r[0] cascaded sums, 1..4, along rows of the box), for
 // the 1-D filter: rows are signals, W the signal length, left = 0.
 template <int L>
 static cudaError_t rows_L(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, int32_t* status,
@@ -540,15 +542,26 @@ static LineWs carve(void* ws, int Gw, int Gh, int n, int DIR) {
 }
 
 template <int L, int NF>
-static cudaError_t lines_NF(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
-                            cudaStream_t st) {
+static cudaError_t line_dir_NF(int dir, const PlanView& pv, uint64_t* g, void* ws, uint32_t ep, int32_t* status,
+                               cudaStream_t st) {
+  const LineWs w = carve<L>(ws, pv.Gw, pv.Gh, NF, dir);
+  if (dir == 2) return launch_lines<L, 2, NF>(pv, g, w, ep, status, st);
+  if (dir == 3) return launch_lines<L, 3, NF>(pv, g, w, ep, status, st);
+  return launch_lines<L, 4, NF>(pv, g, w, ep, status, st);
+}
+
+// v2, v3, v4 in the paper's order, r_k cascaded sums each (none where r_k = 0).
+template <int L>
+static cudaError_t lines_all(const PlanView& pv, uint64_t* g, void* ws, uint32_t* epoch, int32_t* status,
+                             cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   for (int dir = 2; dir <= 4 && e == cudaSuccess; ++dir) {
+    const int nf = pv.r[dir - 1];
+    if (nf == 0) continue;
     const uint32_t ep = (*epoch = (*epoch + 1) & 0x3fffffffu);
-    const LineWs w = carve<L>(ws, pv.Gw, pv.Gh, NF, dir);
-    if (dir == 2) e = launch_lines<L, 2, NF>(pv, g, w, ep, status, st);
-    else if (dir == 3) e = launch_lines<L, 3, NF>(pv, g, w, ep, status, st);
-    else e = launch_lines<L, 4, NF>(pv, g, w, ep, status, st);
+    if (nf == 1) e = line_dir_NF<L, 1>(dir, pv, g, ws, ep, status, st);
+    else if (nf == 2) e = line_dir_NF<L, 2>(dir, pv, g, ws, ep, status, st);
+    else e = line_dir_NF<L, 3>(dir, pv, g, ws, ep, status, st);
   }
   return e;
 }
@@ -561,14 +574,11 @@ static cudaError_t integrate_L(const PlanView& pv, const void* f, size_t f_pitch
     case ABF_U8: e = launch_rows<L, uint8_t>(pv, f, f_pitch, g, status, st); break;
     case ABF_U16: e = launch_rows<L, uint16_t>(pv, f, f_pitch, g, status, st); break;
     case ABF_F32: e = launch_rows<L, float>(pv, f, f_pitch, g, status, st); break;
+    case kStageI64: e = launch_rows<L, long long>(pv, f, f_pitch, g, status, st); break;
     default: e = launch_rows<L, double>(pv, f, f_pitch, g, status, st); break;
   }
   if (e != cudaSuccess) return e;
-  switch (pv.n) {
-    case 1: return lines_NF<L, 1>(pv, g, ws, epoch, status, st);
-    case 2: return lines_NF<L, 2>(pv, g, ws, epoch, status, st);
-    default: return lines_NF<L, 3>(pv, g, ws, epoch, status, st);
-  }
+  return lines_all<L>(pv, g, ws, epoch, status, st);
 }
 
 // Test hook for the bounded look-back wait: one v3 pass whose band-0 CTAs

@@ -233,9 +233,10 @@ struct abf_server_s {
     }
   }
 
-  // Jobs whose adaptive step may share a grouped launch: any exact-form plan
-  // (the batched mesh runs every order and limb count).
-  static bool grouping_ok(abf_plan p) { return p && p->desc.form == ABF_FORM_EXACT; }
+  // Jobs whose adaptive step may share a grouped launch: exact-form plans of
+  // the four-direction filter with phi = delta (the batched mesh runs every
+  // order and limb count of those).
+  static bool grouping_ok(abf_plan p) { return p && p->desc.form == ABF_FORM_EXACT && !p->general; }
 
   // The adaptive step of jobs admitted together, in one batched launch per
   // (order, limbs) group on the first job's stream, after every job's own

@@ -13,7 +13,8 @@ class AdaptiveFilter:
     """s = adaptive box-spline filter of f (abf_integrate + abf_filter)."""
 
     def __init__(self, width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0, max_scale=8.0,
-                 out="f64", form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0, device=None):
+                 out="f64", form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0, device=None,
+                 directions=4, model_boxes=0):
         self.device = torch.device(device or "cuda")
         self.W, self.H, self.n = int(width), int(height), int(n)
         self.in_dtype = in_dtype
@@ -31,6 +32,8 @@ class AdaptiveFilter:
         d.min_scale = float(min_scale)
         d.value_bound = float(value_bound)
         d.max_scale_product = float(max_scale_product)
+        d.directions = int(directions)
+        d.model_boxes = int(model_boxes)
         self.desc = d
         with torch.cuda.device(self.device):
             self.plan = C.abf_plan_create(d)
@@ -161,7 +164,7 @@ class Batch:
 
 
 def make_desc(width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0, max_scale=8.0, out="f64",
-              form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0):
+              form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0, directions=4, model_boxes=0):
     d = C.abf_desc()
     d.width, d.height, d.order_n = int(width), int(height), int(n)
     d.in_dtype = _DT[in_dtype]
@@ -175,6 +178,8 @@ def make_desc(width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0
     d.min_scale = float(min_scale)
     d.value_bound = float(value_bound)
     d.max_scale_product = float(max_scale_product)
+    d.directions = int(directions)
+    d.model_boxes = int(model_boxes)
     return d
 
 

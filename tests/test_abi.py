@@ -186,3 +186,26 @@ def test_plan_refuses_forms_that_cannot_meet_their_tolerance(lib):
     for form in ("exact", "plain_f64", "tile_f32"):
         d = make_desc(64, 64, 1, torch.float32, form=form, q_bits=4, frac_bits=16, max_scale=8.0, value_bound=0.0)
         assert lib.abf_plan_create(ctypes.byref(d), ctypes.byref(plan)) == _abf.ABF_ERR_INVALID
+
+
+@pytest.mark.parametrize("directions,n,E,q", [(2, 2, 0, 2), (2, 3, 0, 1), (4, 1, 1, 2), (4, 1, 2, 2), (2, 1, 2, 2),
+                                              (4, 1, 4, 1)])
+def test_general_table_equals_oracle(lib, directions, n, E, q):
+    """Generalised interpolation tables (N = 2, B-spline models): the library's
+    refinement cascade against the oracle's de Boor pieces (oracle.general),
+    every row and every neighbour; D the same; neighbours outside the listed
+    stencil carry no weight (rows sum to D)."""
+    from paper_0908_3861_gb300 import _abf
+    from oracle import general
+    rows, stencil, D, wb = _abf.abf_general_table_host(directions, n, E, q)
+    r = (n, n if directions == 4 else 0, n, n if directions == 4 else 0)
+    mw = general.MeshWeights(general.interp_counts(r, E - 1 if E else None), q + 1)
+    assert D == mw.D
+    P = q + 1
+    one = 1 << P
+    for ry in range(one):
+        for rx in range(one):
+            row = rows[ry * one + rx]
+            assert sum(row) == D
+            for (dx, dy), w in zip(stencil, row):
+                assert w == mw.value(rx - (dx << P), ry - (dy << P)), (rx, ry, dx, dy)

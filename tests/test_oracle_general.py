@@ -136,3 +136,15 @@ def test_prefilter2d_planted_causal_only_inverse_is_caught():
             acc = sum(rows[y][j] * line1d.bspline(3, x - j) for j in range(5))
             worst = max(worst, abs(acc - int(f[y, x])))
     assert worst > 1
+
+
+def test_whole_image_evaluation_equals_per_pixel_windows():
+    """filter_image (one lattice box) == filter_pixels (a window per pixel)."""
+    rng = np.random.default_rng(67)
+    cq = rng.integers(-500, 500, (9, 11))
+    C = rng.integers(2, 9, (7, 9, 4))
+    pix = [(x, y) for y in range(7) for x in range(9)]
+    for r, n1 in (((1, 1, 1, 1), 3), ((2, 0, 2, 0), None)):
+        S1, s1 = general.filter_image(cq, (1, 1), C, r, n1, 2, 3)
+        S2, s2 = general.filter_pixels(cq, (1, 1), C, r, n1, 2, 3, pix)
+        assert S1 == S2 and s1 == s2
