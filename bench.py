@@ -305,6 +305,19 @@ def run_ours(args):
     clk = clk.summary()
     sm_mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     peak_macs = 152 * 64 * sm_mhz * 1e6 / imad_per_mac
+    # the probes behind the derived peak, measured now (ops/s -> per clock per SM at the sampled clock)
+    probe = {}
+    try:
+        from paper_0908_3861_gb300 import _abf as _A
+        with ClockSampler(local) as pclk:
+            imad_s = _A.abf_probe_alu(0)
+            mac_s = _A.abf_probe_alu(1)
+        pmhz = pclk.summary()["sm_mhz"] or sm_mhz
+        probe = {"imad_per_clk_per_sm": round(imad_s / (152 * pmhz * 1e6), 2),
+                 "mac2x64_per_clk_per_sm": round(mac_s / (152 * pmhz * 1e6), 3),
+                 "sm_mhz": pmhz, "source": "abf_probe_alu (independent chains, every SM)"}
+    except Exception as e:  # the probe is context for the peak, not part of the step
+        probe = {"error": str(e)[:120]}
     achieved = macs / (mesh_ms * 1e-3)
     hl = filt.info["halo_lrbt"]
     gw, gh = W + hl[0] + hl[1], H + hl[3]
@@ -336,7 +349,8 @@ def run_ours(args):
                      "kernel": "mesh_exact_kernel",
                      "peak_note": "derived: 152 SM x 64 INT32 multiply-add lanes x median SM clock / %d "
                                   "32-bit multiply-adds per MAC; achieved = (n+1)^4 x 7n^2 stencil MACs per pixel"
-                                  % imad_per_mac},
+                                  % imad_per_mac,
+                     "probe": probe},
         "roofline_integrate": {"bound": "hbm", "achieved": round(integ_bytes / (integ_ms * 1e-3) / 1e9, 1),
                                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                                "frac": (round(integ_bytes / (integ_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
@@ -744,6 +758,118 @@ def run_constant_cost(args):
     print(json.dumps(line), flush=True)
 
 
+GENERAL = {
+    # N = 2 (theta = 0, pi/2), order 2, steps c1, c3 in [1, 24], phi = delta
+    "n2": dict(directions=2, n=2, model_boxes=0, lo=1.0, hi=24.0, q_bits=6,
+               text="N = 2 (tensor box splines), order n=2, steps c1, c3 in [1,24] from S(64) fields, phi = delta"),
+    # N = 4, order 1 (Sec. 7), cubic B-spline model phi with its 2-D prefilter
+    "m3": dict(directions=4, n=1, model_boxes=4, lo=1.0, hi=8.0, q_bits=6,
+               text="N = 4, order n=1, cubic B-spline model phi (prefilter in the step), paper scales a_k in [1,8]"),
+}
+
+
+def _stencil_macs(directions, n, E):
+    """Algorithmic MACs per pixel of a generalised plan: taps prod (r_k + 1)
+    times the area of the interpolation kernel's support (the zonotope of its
+    directions: sum over pairs m_i m_j |det(v_i, v_j)|, its average count of
+    non-zero lattice weights)."""
+    V = ((1, 0), (1, 1), (0, 1), (-1, 1))
+    r = (n, n if directions == 4 else 0, n, n if directions == 4 else 0)
+    m = (r[0] + E, r[1], r[2] + E, r[3])
+    area = sum(m[i] * m[j] * abs(V[i][0] * V[j][1] - V[i][1] * V[j][0]) for i in range(4) for j in range(i + 1, 4))
+    taps = 1
+    for rk in r:
+        taps *= rk + 1
+    return taps * area
+
+
+def run_general(args):
+    """Generalised plans on the 2048^2 image of the order-2 recipe: N = 2
+    ('n2') or the cubic B-spline model ('m3'): Mpixel/s of integrate (with the
+    model's prefilter) + filter, exact form, and the mesh against the derived
+    integer peak."""
+    import torch
+    import synthetic
+    from paper_0908_3861_gb300 import AdaptiveFilter
+    import __graft_entry__
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    cfg = GENERAL[args.workload]
+    shp = _shape(args) or (2048, 2048)
+    w = synthetic.workload("c2", shape=shp, seed_offset=rank)
+    img = w["image"]
+    H, W = img.shape
+    rng = np.random.default_rng(synthetic.SEED_BASE + 5)
+    sc = synthetic.scales_a4(rng, (H, W), cfg["lo"], cfg["hi"], 64.0).astype(np.float32)
+    kind = "a4"
+    if cfg["directions"] == 2:
+        sc[..., 1] = 1.0
+        sc[..., 3] = 1.0
+        kind = "c4"
+    filt = AdaptiveFilter(W, H, cfg["n"], torch.float32, scale_kind=kind, q_bits=cfg["q_bits"], frac_bits=16,
+                          max_scale=cfg["hi"], out="f32", value_bound=255.0, device=dev,
+                          directions=cfg["directions"], model_boxes=cfg["model_boxes"])
+    f_t = torch.from_numpy(img).to(dev)
+    s_t = torch.from_numpy(sc).to(dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        filt.integrate(f_t)
+        filt.filter(s_t, out)
+    torch.cuda.synchronize()
+    assert filt.device_status() == 0
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            filt.integrate(f_t)
+            ev[i][1].record(stream)
+            filt.filter(s_t, out)
+            ev[i][2].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1) / K
+    integ_ms = sum(a.elapsed_time(b) for a, b, c in ev) / K
+    mesh_ms = sum(b.elapsed_time(c) for a, b, c in ev) / K
+    assert filt.device_status() == 0
+    pix = float(H * W)
+    L = filt.limbs
+    clk = clk.summary()
+    sm_mhz = clk["sm_mhz"] or _peaks().get("sm_max_mhz", 2070.0)
+    D = filt.denominator()
+    Dv = sum(int(v) << (32 * i) for i, v in enumerate(D)) if not isinstance(D, int) else D
+    wwords = 2 if Dv < (1 << 64) else 4   # 64-bit or 128-bit table weights
+    imad = (sum(1 for i in range(2 * L) for j in range(wwords) if i + j <= 2 * L - 1)
+            + sum(1 for i in range(2 * L) for j in range(wwords) if i + j <= 2 * L - 2))
+    macs = _stencil_macs(cfg["directions"], cfg["n"], cfg["model_boxes"]) * pix
+    peak = 152 * 64 * sm_mhz * 1e6 / imad
+    achieved = macs / (mesh_ms * 1e-3)
+    line = {"metric": "Mpixel/s adaptive filter, generalised plan (%s)" % args.workload,
+            "value": round(pix / (total_ms * 1e-3) / 1e6, 3), "unit": "Mpixel/s", "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(total_ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64x%d" % L, "data": "synthetic",
+            "config": {"workload": "%dx%d f32 (2^-16 grid) image of the order-2 recipe; %s; Q=%d; exact form"
+                                   % (H, W, cfg["text"], cfg["q_bits"]), "l2": "inputs larger than L2"},
+            "gpu_launches": int(K * (5 if cfg["model_boxes"] >= 3 else 3) + K * (1 if cfg["directions"] == 2 else 3)),
+            "kernels_ms": {"integrate": round(integ_ms, 4), "mesh": round(mesh_ms, 4)},
+            "roofline": {"bound": "alu", "achieved": round(achieved / 1e9, 2), "peak": round(peak / 1e9, 2),
+                         "unit": "G MAC/s (%d-limb integer x %d-bit weight)" % (L, 32 * wwords),
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "mesh_gen_kernel",
+                         "peak_note": "derived as for the main line; achieved = taps x support area of the "
+                                      "interpolation kernel (%d MACs per pixel)"
+                                      % _stencil_macs(cfg["directions"], cfg["n"], cfg["model_boxes"])},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    filt.close()
+
+
 def _serve_pool(npool, inflight, dev, rank=0):
     """Distinct jobs of the serving recipe: sides U{256..4096}, float32 images
     on the 2^-16 grid (smooth field + edges), ellipse fields as the 2048^2
@@ -1017,6 +1143,8 @@ def main():
         run_scale_map(args)
     elif args.workload == "cc":
         run_constant_cost(args)
+    elif args.workload in GENERAL:
+        run_general(args)
     else:
         run_ours(args)
 

@@ -545,6 +545,14 @@ abf_status abf1d_prefilter_host(int32_t n1, int32_t* npoles, double* z, double* 
  * it on small plans.  d_g is left undefined.  Exact form only.              */
 abf_status abf_debug_starved_lookback(abf_plan plan, void* d_g, void* d_ws, cudaStream_t stream);
 
+/* Throughput probes behind the mesh's integer roofline (no counterpart in
+ * the paper): kind 0 measures 32-bit integer multiply-adds per second, kind 1
+ * the two-limb x 64-bit carry-chained multiply-accumulates per second (the
+ * mesh's per-weight operation at order 2), both on eight independent chains
+ * per thread over 8 CTAs of 256 threads per SM.  Synchronises the device;
+ * allocates 32 KB for the duration of the call.                            */
+abf_status abf_probe_alu(int32_t kind, double* ops_per_s);
+
 /* Library version, for the bindings. */
 int32_t abf_version(void);
 

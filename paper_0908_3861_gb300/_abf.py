@@ -97,6 +97,7 @@ def signatures():
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
         "abf_integrate_batch": ([P(abf_integrate_job), i32, vp, sz, vp], st),
         "abf_integrate_batch_max_jobs": ([], i32),
+        "abf_probe_alu": ([i32, P(ctypes.c_double)], st),
         "abf_general_table_host": ([i32, i32, i32, i32, vp, sz, P(sz), P(i32), P(i32), P(i32), P(ctypes.c_uint32)],
                                    st),
         "abf_batch_max_jobs": ([], i32),
@@ -269,6 +270,12 @@ def abf_general_table_host(directions, n, model_boxes, q_bits, with_weights=True
         rows = [[int.from_bytes(raw[(r * Rv + c) * w:(r * Rv + c + 1) * w], "little") for c in range(Rv)]
                 for r in range(need.value // (w * Rv))]
     return rows, stencil, D, wb.value
+
+
+def abf_probe_alu(kind):
+    v = ctypes.c_double()
+    _check(lib().abf_probe_alu(int(kind), ctypes.byref(v)), "abf_probe_alu")
+    return v.value
 
 
 def abf_integrate_batch_max_jobs():
