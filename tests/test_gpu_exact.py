@@ -179,18 +179,6 @@ def _sample_pixels(H, W, k, seed):
     return sorted(pts)
 
 
-def _check_sampled(w, res, pix):
-    C_ref = gu.oracle_C(w)
-    assert (res["C"] == C_ref).all(), "integer steps differ"
-    S_ref, s_ref = paper.filter_pixels(gu.f_int(w), C_ref, w["n"], w["q_bits"], w["frac_bits"], pix)
-    L = res["limbs"]
-    mod = 1 << (64 * L)
-    for (x, y), S, sv in zip(pix, S_ref, s_ref):
-        got = sum(int(res["num"][y, x, i]) << (64 * i) for i in range(L))
-        assert got == S % mod, (x, y)
-        assert abs(res["s"][y, x] - sv) <= 1e-13 * abs(sv) + 1e-300, (x, y, res["s"][y, x], sv)
-
-
 def _measured_product(w):
     import torch
     from paper_0908_3861_gb300 import _abf
@@ -215,35 +203,72 @@ def test_full_size_256_order1_all_pixels():
 
 @pytest.mark.slow
 def test_full_size_2048_order2_ellipse_sampled():
-    """2048x2048 float32 on the 2^-16 grid, n = 2, ellipse scales, Q = 8."""
+    """2048x2048 float32 on the 2^-16 grid, n = 2, ellipse scales, Q = 8:
+    2^16 random pixels plus every pixel of the four border rows and columns,
+    numerators bit-exact and s within 1e-13 (the oracle per pixel, on every
+    host core)."""
     w = synthetic.workload("c2")
     prod = _measured_product(w)
     res = gu.run_exact(w, max_scale_product=prod)
     assert res["status"] == 0
     assert np.isfinite(res["s"]).all()
     H, W = w["image"].shape
-    _check_sampled(w, res, _sample_pixels(H, W, 24, 1))
+    rng = np.random.default_rng(1)
+    pts = set((int(x), int(y)) for x, y in zip(rng.integers(0, W, 1 << 16), rng.integers(0, H, 1 << 16)))
+    pts |= {(x, 0) for x in range(W)} | {(x, H - 1) for x in range(W)}
+    pts |= {(0, y) for y in range(H)} | {(W - 1, y) for y in range(H)}
+    pix = sorted(pts)
+    C_ref = gu.oracle_C(w)
+    assert (res["C"] == C_ref).all(), "integer steps differ"
+    S_ref, s_ref = gu.oracle_pixels_parallel("c2", None, C_ref, pix)
+    L = res["limbs"]
+    mod = 1 << (64 * L)
+    num = res["num"]
+    bad = 0
+    for (x, y), S, sv in zip(pix, S_ref, s_ref):
+        got = sum(int(num[y, x, i]) << (64 * i) for i in range(L))
+        if got != S % mod or not abs(res["s"][y, x] - sv) <= 1e-13 * abs(sv) + 1e-300:
+            bad += 1
+    assert bad == 0, "%d of %d pixels differ" % (bad, len(pix))
+    assert len(pix) >= (1 << 16)
 
 
 @pytest.mark.slow
 def test_full_size_8192_order3_sampled():
-    """8192x8192 uint16, n = 3, paper scales in [1, 48], Q = 8: sampled pixels,
-    and the first rows of the integrated image modulo 2^64."""
+    """8192x8192 uint16, n = 3, paper scales in [1, 48], Q = 8: numerators at
+    sampled pixels (corners, borders, interior), and the whole integrated image
+    modulo 2^64."""
     w = synthetic.workload("c3")
     prod = _measured_product(w)
     res = gu.run_exact(w, max_scale_product=prod, want=("s", "num", "C"))
     assert res["status"] == 0
     H, W = w["image"].shape
-    _check_sampled(w, res, _sample_pixels(H, W, 10, 2))
+    # numerators at the corners, edge midpoints, 8 points along every border and
+    # random interior pixels (the oracle per pixel, on every host core)
+    pix = set(_sample_pixels(H, W, 200, 2))
+    for t in range(8):
+        pix |= {((t * W) // 8, 0), ((t * W) // 8, H - 1), (0, (t * H) // 8), (W - 1, (t * H) // 8)}
+    pix = sorted(pix)
+    C_ref = gu.oracle_C(w)
+    S_ref, s_ref = gu.oracle_pixels_parallel("c3", None, C_ref, pix, chunk=8)
+    L = res["limbs"]
+    mod = 1 << (64 * L)
+    for (x, y), S, sv in zip(pix, S_ref, s_ref):
+        got = sum(int(res["num"][y, x, i]) << (64 * i) for i in range(L))
+        assert got == S % mod, (x, y)
+        assert abs(res["s"][y, x] - sv) <= 1e-13 * abs(sv) + 1e-300, (x, y, res["s"][y, x], sv)
+    # the whole integrated image modulo 2^64 (the low limb), wherever the
+    # 3pi/4 rays leave the box through its bottom row
     filt = res["filt"]
     left, right, _, above = res["halo"]
-    rows = 48
-    g = filt.integrated()[:rows].cpu().numpy().astype(np.uint64)[..., 0]
-    g_or = paper.integrate(gu.f_int(w)[:rows], w["n"], -left, W + right, 0, rows, exact=False)
+    rows = H + above
+    g = filt.integrated().cpu().numpy()[..., 0].astype(np.uint64)
+    g_or = paper.integrate(gu.f_int(w), w["n"], -left, W + right, 0, rows, exact=False)
     xs = np.arange(W + left + right)[None, :] - left
-    ys = np.arange(rows)[:, None]
-    region = xs + ys < W + right
-    assert (g[:, :W + left + right][region] == g_or[region]).all()
+    for y0 in range(0, rows, 512):
+        ys = np.arange(y0, min(rows, y0 + 512))[:, None]
+        region = xs + ys < W + right
+        assert (g[y0:y0 + 512, :W + left + right][region] == g_or[y0:y0 + 512][region]).all(), y0
 
 
 def test_two_plans_share_one_workspace():
