@@ -87,42 +87,30 @@ _POOL_CACHE = {}
 
 def _pool_init(name, shape):
     """Worker set-up: the workload regenerated from its seed (the same bytes as
-    the parent's) and its integer image."""
+    the parent's), its integer image and its integer steps."""
     import synthetic
     w = synthetic.workload(name, shape=shape)
     _POOL_CACHE["w"] = w
     _POOL_CACHE["fi"] = f_int(w)
+    _POOL_CACHE["C"] = oracle_C(w)
 
 
-class _SparseC:
-    """C[m2, m1] for the pixels of one chunk (the oracle reads no other entry)."""
-
-    def __init__(self, pix, rows):
-        self.d = {(y, x): r for (x, y), r in zip(pix, rows)}
-
-    def __getitem__(self, key):
-        return self.d[key]
-
-
-def _pool_chunk(args):
+def _pool_chunk(pix):
     from oracle import paper
-    pix, rows = args
     w = _POOL_CACHE["w"]
-    S, s = paper.filter_pixels(_POOL_CACHE["fi"], _SparseC(pix, rows), w["n"], w["q_bits"], w["frac_bits"], pix)
+    S, s = paper.filter_pixels(_POOL_CACHE["fi"], _POOL_CACHE["C"], w["n"], w["q_bits"], w["frac_bits"], pix)
     return S, list(s)
 
 
-def oracle_pixels_parallel(name, shape, C, pix, chunk=256, procs=None):
+def oracle_pixels_parallel(name, shape, pix, chunk=256, procs=None):
     """paper.filter_pixels on many pixels of a named workload, in a pool of
-    spawned processes (one per host core): returns (S list, s list)."""
+    spawned processes (one per host core), each regenerating the workload from
+    its seed: returns (S list, s list) in the order of pix."""
     import multiprocessing as mp
     import os
     from concurrent.futures import ProcessPoolExecutor
     procs = procs or os.cpu_count() or 1
-    jobs = []
-    for i in range(0, len(pix), chunk):
-        part = pix[i:i + chunk]
-        jobs.append((part, [np.asarray(C[y, x]) for x, y in part]))
+    jobs = [pix[i:i + chunk] for i in range(0, len(pix), chunk)]
     S, s = [], []
     with ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn"), initializer=_pool_init,
                              initargs=(name, shape)) as ex:
