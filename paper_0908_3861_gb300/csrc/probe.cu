@@ -13,13 +13,13 @@ __global__ void __launch_bounds__(kProbeThreads) probe_imad_kernel(uint32_t* sin
   uint32_t a[kProbeChains];
 #pragma unroll
   for (int k = 0; k < kProbeChains; ++k) a[k] = seed ^ (threadIdx.x * 2654435761u + k);
-  // a[k] <- a[k] a[k^1] + c: products of two variables, so no two iterations
-  // fold into one multiply-add (a constant multiplier would let the compiler
-  // compose the affine steps)
+  // a[k] <- a[k] a[k+1 mod 8] + c: distinct products of two variables, so no
+  // two iterations fold into one multiply-add and no product is shared (a
+  // constant multiplier would let the compiler compose the affine steps)
   for (int i = 0; i < iters; ++i) {
     uint32_t b[kProbeChains];
 #pragma unroll
-    for (int k = 0; k < kProbeChains; ++k) b[k] = a[k] * a[k ^ 1] + (uint32_t)(2 * k + 1);
+    for (int k = 0; k < kProbeChains; ++k) b[k] = a[k] * a[(k + 1) % kProbeChains] + (uint32_t)(2 * k + 1);
 #pragma unroll
     for (int k = 0; k < kProbeChains; ++k) a[k] = b[k];
   }
