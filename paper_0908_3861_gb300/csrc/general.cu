@@ -45,84 +45,147 @@ constexpr int kGenMaxR = 256;    // neighbours per table row
 constexpr int kGenMaxTaps = 81;  // prod_k (r_k + 1)
 constexpr int kGenWarps = 8;     // rows per CTA
 
-// ------------------------------------------------------------- mesh kernel
+// ------------------------------------------------------------- mesh kernels
 
-// One warp per run of 32 pixels of a row, as the plain form's generic path:
-// lane i reads pixel x0 + i's steps; for each pixel of the run the lanes
-// tabulate its taps (grouped by FD weight) in shared memory and then deal the
-// (tap, neighbour) pairs of each group among themselves.
-template <int L, typename WT>
-__global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
-    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
-    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
-  __shared__ int2 s_st[kGenMaxR];
-  __shared__ unsigned char s_order[kGenMaxTaps];
-  __shared__ int s_gbeg[12], s_gw[11], s_ng, s_taps;
-  __shared__ int4 s_tap[kGenWarps][kGenMaxTaps];
-  const int R = pv.R;
-  for (int i = threadIdx.x; i < R; i += blockDim.x) s_st[i] = pv.stencil[i];
-  const int r0 = pv.r[0], r1 = pv.r[1], r2 = pv.r[2], r3 = pv.r[3];
+// Per CTA: the stencil of the table rows, and the taps j = (j1..j4) ordered by
+// their FD weight w_j = prod_k (-1)^{j_k} binom(r_k, j_k) (Eq. (RS_filter)),
+// one group per distinct weight, each tap's j packed two bits per direction.
+struct GenShared {
+  int2 st[kGenMaxR];
+  unsigned char order[kGenMaxTaps];
+  int gbeg[12], gw[11], ng, taps;
+};
+
+__device__ void gen_setup(const PlanView& pv, GenShared& sh) {
+  for (int i = threadIdx.x; i < pv.R; i += blockDim.x) sh.st[i] = pv.stencil[i];
   if (threadIdx.x == 0) {
-    const int taps = (r0 + 1) * (r1 + 1) * (r2 + 1) * (r3 + 1);
+    const int taps = (pv.r[0] + 1) * (pv.r[1] + 1) * (pv.r[2] + 1) * (pv.r[3] + 1);
     int wt[kGenMaxTaps];
+    unsigned char jj[kGenMaxTaps];
     for (int t = 0; t < taps; ++t) {
-      int u = t, w = 1;
+      int u = t, w = 1, packed = 0;
       for (int k = 0; k < 4; ++k) {
         const int rk = pv.r[k], j = u % (rk + 1);
         u /= rk + 1;
         int b = 1;  // binom(rk, j), rk <= 3
         for (int i = 0; i < j; ++i) b = b * (rk - i) / (i + 1);
         w *= (j & 1) ? -b : b;
+        packed |= j << (2 * k);
       }
       wt[t] = w;
+      jj[t] = (unsigned char)packed;
     }
     int ng = 0, c = 0;
     for (int t = 0; t < taps; ++t) {
       bool seen = false;
-      for (int q = 0; q < ng; ++q) seen |= s_gw[q] == wt[t];
-      if (!seen) s_gw[ng++] = wt[t];
+      for (int q = 0; q < ng; ++q) seen |= sh.gw[q] == wt[t];
+      if (!seen) sh.gw[ng++] = wt[t];
     }
     for (int q = 0; q < ng; ++q) {
-      s_gbeg[q] = c;
+      sh.gbeg[q] = c;
       for (int t = 0; t < taps; ++t)
-        if (wt[t] == s_gw[q]) s_order[c++] = (unsigned char)t;
+        if (wt[t] == sh.gw[q]) sh.order[c++] = jj[t];
     }
-    s_gbeg[ng] = c;
-    s_ng = ng;
-    s_taps = taps;
+    sh.gbeg[ng] = c;
+    sh.ng = ng;
+    sh.taps = taps;
   }
+}
+
+// This lane's pixel -> integer steps C_k and a verdict: 0 outside the image,
+// 1 good, 2 numerator bound beyond 64 L - 1 bits, 3 bad scale.
+template <int L>
+__device__ __forceinline__ int gen_lane_steps(const PlanView& pv, const float4* scales, size_t scale_pitch, int x, int y,
+                                              int C[4]) {
+  C[0] = C[1] = C[2] = C[3] = 0;
+  if (x >= pv.W) return 0;
+  if (!pixel_steps(pv, scales, scale_pitch, x, y, C)) return 3;
+  float lb = pv.log2_base;
+  for (int k = 0; k < 4; ++k) lb += (float)pv.r[k] * (__log2f((float)C[k]) - (float)pv.Q);
+  if (pv.E == 0) {
+    const float q = (float)(1 << pv.Q);
+    lb += __log2f((1.0f + q / (float)C[0]) * (1.0f + q / (float)C[2]));
+  }
+  return (lb + 0.05f < 64.0f * L - 1.0f) ? 1 : 2;
+}
+
+// Stores the numerator and s = S 2^(Q sum r - F) / (D prod_k C_k^{r_k}) of the
+// lane's pixel (NaN and a device status for a refused pixel).
+template <int L>
+__device__ __forceinline__ void gen_store(const PlanView& pv, void* s, size_t s_pitch, uint64_t* num, size_t num_pitch,
+                                          int32_t* status, int x, int y, int ok, const int C[4], const Wide<L>& S) {
+  if (x >= pv.W) return;
+  const bool f64 = pv.out_dtype == ABF_F64;
+  char* row = s ? reinterpret_cast<char*>(s) + (size_t)y * s_pitch : nullptr;
+  if (ok != 1) {
+    raise_status(status, ok == 3 ? ABF_DEV_BAD_SCALE : ABF_DEV_RANGE);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (row) {
+      if (f64) reinterpret_cast<double*>(row)[x] = nan;
+      else reinterpret_cast<float*>(row)[x] = (float)nan;
+    }
+    return;
+  }
+  if (num) {
+    uint64_t* q = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(num) + (size_t)y * num_pitch) + (size_t)x * L;
+#pragma unroll
+    for (int i = 0; i < L; ++i) q[i] = S.w[i];
+  }
+  if (row) {
+    double den = pv.Dd;
+    int rs = 0;
+    for (int k = 0; k < 4; ++k) {
+      for (int e = 0; e < pv.r[k]; ++e) den *= (double)C[k];
+      rs += pv.r[k];
+    }
+    const double v = ldexp(wto_double<L>(S), pv.Q * rs - pv.F) / den;
+    if (f64) reinterpret_cast<double*>(row)[x] = v;
+    else reinterpret_cast<float*>(row)[x] = (float)v;
+  }
+}
+
+// acc += w part for the FD weight w of a tap group.
+template <int L>
+__device__ __forceinline__ void gen_apply_weight(Wide<L>& acc, const Wide<L>& part, int w) {
+  Wide<L> sc;
+  wzero<L>(sc);
+  wmac<L>(sc, part, (uint64_t)(w < 0 ? -w : w));
+  if (w < 0) wsub<L>(acc, sc);
+  else wadd<L>(acc, sc);
+}
+
+// Wide stencils (R > 32 neighbours): one warp per run of 32 pixels of a row,
+// as the plain form's generic path.  Lane i reads pixel x0 + i's steps; for
+// each pixel of the run the lanes tabulate its taps (grouped by FD weight) in
+// shared memory and then deal the (tap, neighbour) pairs of each group among
+// themselves.
+template <int L, typename WT>
+__global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  __shared__ GenShared sh;
+  __shared__ int4 s_tap[kGenWarps][kGenMaxTaps];
+  gen_setup(pv, sh);
   __syncthreads();
+  const int R = pv.R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int y = blockIdx.y * kGenWarps + warp;
   if (y >= pv.H) return;
   const int x0 = blockIdx.x * 32;
   const int myx = x0 + lane;
   const int Q = pv.Q, P = pv.P, one = 1 << Q, mask = (1 << P) - 1;
-  int C0 = 0, C1 = 0, C2 = 0, C3 = 0, ok = 0;  // 0 outside, 1 good, 2 range, 3 bad scale
-  if (myx < pv.W) {
-    int C[4];
-    if (!pixel_steps(pv, scales, scale_pitch, myx, y, C)) {
-      ok = 3;
-    } else {
-      C0 = C[0]; C1 = C[1]; C2 = C[2]; C3 = C[3];
-      float lb = pv.log2_base;
-      for (int k = 0; k < 4; ++k) lb += (float)pv.r[k] * (__log2f((float)C[k]) - (float)Q);
-      if (pv.E == 0) {
-        const float q = (float)one;
-        lb += __log2f((1.0f + q / (float)C[0]) * (1.0f + q / (float)C[2]));
-      }
-      ok = (lb + 0.05f < 64.0f * L - 1.0f) ? 1 : 2;
-    }
-  }
+  const int r0 = pv.r[0], r1 = pv.r[1], r3 = pv.r[3], r2 = pv.r[2];
+  int C[4];
+  const int ok = gen_lane_steps<L>(pv, scales, scale_pitch, myx, y, C);
   const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
-  const int taps = s_taps, ng = s_ng;
+  const int taps = sh.taps, ng = sh.ng;
   int4* tp = s_tap[warp];
   Wide<L> mine;
   wzero<L>(mine);
   for (int pp = 0; pp < 32; ++pp) {
     if (__shfl_sync(0xffffffffu, ok, pp) != 1) continue;
-    const int c0 = __shfl_sync(0xffffffffu, C0, pp), c1 = __shfl_sync(0xffffffffu, C1, pp);
-    const int c2 = __shfl_sync(0xffffffffu, C2, pp), c3 = __shfl_sync(0xffffffffu, C3, pp);
+    const int c0 = __shfl_sync(0xffffffffu, C[0], pp), c1 = __shfl_sync(0xffffffffu, C[1], pp);
+    const int c2 = __shfl_sync(0xffffffffu, C[2], pp), c3 = __shfl_sync(0xffffffffu, C[3], pp);
     // tau 2^P = sum_k r_k (C_k - 2^Q) v_k; c_k 2^P = 2 C_k
     const int tx = r0 * (c0 - one) + r1 * (c1 - one) - r3 * (c3 - one);
     const int ty = r1 * (c1 - one) + r2 * (c2 - one) + r3 * (c3 - one);
@@ -130,11 +193,8 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     const int Y0y = ((y + pv.oy) << P) + ty;
     __syncwarp();
     for (int slot = lane; slot < taps; slot += 32) {
-      int u = s_order[slot];
-      const int j1 = u % (r0 + 1); u /= r0 + 1;
-      const int j2 = u % (r1 + 1); u /= r1 + 1;
-      const int j3 = u % (r2 + 1); u /= r2 + 1;
-      const int j4 = u;
+      const int u = sh.order[slot];
+      const int j1 = u & 3, j2 = (u >> 2) & 3, j3 = (u >> 4) & 3, j4 = u >> 6;
       const int Yx = Y0x - 2 * (j1 * c0 + j2 * c1 - j4 * c3);
       const int Yy = Y0y - 2 * (j2 * c1 + j3 * c2 + j4 * c3);
       tp[slot] = make_int4((Yx >> P) + pv.left, Yy >> P, ((Yy & mask) << P) | (Yx & mask), 0);
@@ -143,25 +203,20 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     Wide<L> acc;
     wzero<L>(acc);
     for (int gi = 0; gi < ng; ++gi) {
-      const int tb = s_gbeg[gi], npairs = (s_gbeg[gi + 1] - tb) * R;
+      const int tb = sh.gbeg[gi], npairs = (sh.gbeg[gi + 1] - tb) * R;
       Wide<L> part;
       wzero<L>(part);
       for (int idx = lane; idx < npairs; idx += 32) {
         const int q = idx / R;
         const int cand = idx - q * R;
         const int4 ti = tp[tb + q];
-        const int2 d = s_st[cand];
+        const int2 d = sh.st[cand];
         const int k2 = ti.y + d.y;
         if (k2 < 0) continue;  // rows below the box: g = 0
         const Wide<L> gv = wload<L>(g + ((size_t)k2 * (size_t)pv.Gp + (size_t)(ti.x + d.x)) * L);
         mac_weight<L, WT>(part, gv, __ldg(table + (size_t)ti.z * R + cand));
       }
-      const int w = s_gw[gi];
-      Wide<L> sc;
-      wzero<L>(sc);
-      wmac<L>(sc, part, (uint64_t)(w < 0 ? -w : w));
-      if (w < 0) wsub<L>(acc, sc);
-      else wadd<L>(acc, sc);
+      gen_apply_weight<L>(acc, part, sh.gw[gi]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -172,48 +227,126 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     }
     if (lane == pp) mine = acc;
   }
-  if (myx >= pv.W) return;
-  const bool f64 = pv.out_dtype == ABF_F64;
-  if (ok != 1) {
-    raise_status(status, ok == 3 ? ABF_DEV_BAD_SCALE : ABF_DEV_RANGE);
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    if (s) {
-      char* row = reinterpret_cast<char*>(s) + (size_t)y * s_pitch;
-      if (f64) reinterpret_cast<double*>(row)[myx] = nan;
-      else reinterpret_cast<float*>(row)[myx] = (float)nan;
+  gen_store<L>(pv, s, s_pitch, num, num_pitch, status, myx, y, ok, C, mine);
+}
+
+// Stencils of R <= G <= 32 neighbours (e.g. the 2 x 2 of N = 2, n = 2): the
+// warp owns a run of 32 pixels of a row and works in groups of G lanes, one
+// pixel per group, 32 / G neighbouring pixels at once; lane k of a group
+// takes neighbour k of every tap (its table weight is word k of the tap's
+// row, so a group reads one contiguous row piece), computes the tap positions
+// itself (no shared tap table) and the group sums its lanes by butterfly.
+// After each round the group leaders hand the numerators to the lanes that
+// own those pixels.
+template <int L, typename WT, int G>
+__global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
+    const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
+    void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
+  static_assert(G == 4 || G == 16 || G == 32, "group of 4, 16 or 32 lanes");
+  constexpr int PPR = 32 / G;  // pixels per round
+  __shared__ GenShared sh;
+  gen_setup(pv, sh);
+  __syncthreads();
+  const int R = pv.R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y = blockIdx.y * kGenWarps + warp;
+  if (y >= pv.H) return;
+  const int x0 = blockIdx.x * 32;
+  const int myx = x0 + lane;
+  const int Q = pv.Q, P = pv.P, one = 1 << Q, mask = (1 << P) - 1;
+  const int r0 = pv.r[0], r1 = pv.r[1], r3 = pv.r[3], r2 = pv.r[2];
+  int C[4];
+  const int ok = gen_lane_steps<L>(pv, scales, scale_pitch, myx, y, C);
+  const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
+  const int ng = sh.ng;
+  const int grp = lane / G, gl = lane % G;
+  const bool has_d = gl < R;
+  const int2 d = has_d ? sh.st[gl] : make_int2(0, 0);
+  const long long Gp = pv.Gp;
+  Wide<L> mine;
+  wzero<L>(mine);
+  for (int q = 0; q < G; ++q) {
+    const int pp = q * PPR + grp;
+    const int okp = __shfl_sync(0xffffffffu, ok, pp);
+    const int c0 = __shfl_sync(0xffffffffu, C[0], pp), c1 = __shfl_sync(0xffffffffu, C[1], pp);
+    const int c2 = __shfl_sync(0xffffffffu, C[2], pp), c3 = __shfl_sync(0xffffffffu, C[3], pp);
+    Wide<L> acc;
+    wzero<L>(acc);
+    if (okp == 1 && has_d) {
+      const int tx = r0 * (c0 - one) + r1 * (c1 - one) - r3 * (c3 - one);
+      const int ty = r1 * (c1 - one) + r2 * (c2 - one) + r3 * (c3 - one);
+      const int Y0x = ((x0 + pp + pv.ox) << P) + tx;
+      const int Y0y = ((y + pv.oy) << P) + ty;
+      for (int gi = 0; gi < ng; ++gi) {
+        Wide<L> part;
+        wzero<L>(part);
+        const int te = sh.gbeg[gi + 1];
+        for (int slot = sh.gbeg[gi]; slot < te; ++slot) {
+          const int u = sh.order[slot];
+          const int j1 = u & 3, j2 = (u >> 2) & 3, j3 = (u >> 4) & 3, j4 = u >> 6;
+          const int Yx = Y0x - 2 * (j1 * c0 + j2 * c1 - j4 * c3);
+          const int Yy = Y0y - 2 * (j2 * c1 + j3 * c2 + j4 * c3);
+          const int k2 = (Yy >> P) + d.y;
+          if (k2 < 0) continue;  // rows below the box: g = 0
+          const int row = ((Yy & mask) << P) | (Yx & mask);
+          const Wide<L> gv = wload<L>(g + ((size_t)k2 * Gp + (size_t)((Yx >> P) + pv.left + d.x)) * L);
+          mac_weight<L, WT>(part, gv, __ldg(table + (size_t)row * R + gl));
+        }
+        gen_apply_weight<L>(acc, part, sh.gw[gi]);
+      }
     }
-    return;
-  }
-  if (num) {
-    uint64_t* q = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(num) + (size_t)y * num_pitch) + (size_t)myx * L;
 #pragma unroll
-    for (int i = 0; i < L; ++i) q[i] = mine.w[i];
-  }
-  if (s) {
-    double den = pv.Dd;
-    const int Cv[4] = {C0, C1, C2, C3};
-    int rs = 0;
-    for (int k = 0; k < 4; ++k) {
-      for (int e = 0; e < pv.r[k]; ++e) den *= (double)Cv[k];
-      rs += pv.r[k];
+    for (int o = G / 2; o > 0; o >>= 1) {
+      Wide<L> other;
+#pragma unroll
+      for (int i = 0; i < L; ++i) other.w[i] = __shfl_xor_sync(0xffffffffu, acc.w[i], o);
+      wadd<L>(acc, other);
     }
-    const double v = ldexp(wto_double<L>(mine), Q * rs - pv.F) / den;
-    char* row = reinterpret_cast<char*>(s) + (size_t)y * s_pitch;
-    if (f64) reinterpret_cast<double*>(row)[myx] = v;
-    else reinterpret_cast<float*>(row)[myx] = (float)v;
+    // lane l's pixel was this round's if l / PPR == q, summed by group l % PPR
+    Wide<L> t;
+#pragma unroll
+    for (int i = 0; i < L; ++i) t.w[i] = __shfl_sync(0xffffffffu, acc.w[i], (lane % PPR) * G);
+    if (lane / PPR == q) mine = t;
+  }
+  gen_store<L>(pv, s, s_pitch, num, num_pitch, status, myx, y, ok, C, mine);
+}
+
+// Lanes per pixel for a table of R neighbours: a group of 4 (the 2 x 2 stencil
+// of N = 2, n = 2), 16 (3 x 3 and 4 x 4) or the whole warp (up to 32), else 0
+// (the pair-dealt warp kernel).
+static int gen_group_lanes(int R) { return R <= 4 ? 4 : R <= 16 ? 16 : R <= 32 ? 32 : 0; }
+
+template <int L, typename WT>
+static void launch_gen_WT(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
+                          size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
+  dim3 grid((unsigned)((pv.W + 31) / 32), (unsigned)((pv.H + kGenWarps - 1) / kGenWarps));
+  const float4* sc = (const float4*)scales;
+  switch (gen_group_lanes(pv.R)) {
+    case 4:
+      mesh_gen_group_kernel<L, WT, 4><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                      num_pitch, status);
+      break;
+    case 16:
+      mesh_gen_group_kernel<L, WT, 16><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                       num_pitch, status);
+      break;
+    case 32:
+      mesh_gen_group_kernel<L, WT, 32><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                       num_pitch, status);
+      break;
+    default:
+      mesh_gen_kernel<L, WT><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch,
+                                                             status);
   }
 }
 
 template <int L>
 static cudaError_t launch_gen_L(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
                                 size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
-  dim3 grid((unsigned)((pv.W + 31) / 32), (unsigned)((pv.H + kGenWarps - 1) / kGenWarps));
   if (pv.table_bytes_per_w == 16)
-    mesh_gen_kernel<L, ulonglong2><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s,
-                                                                    s_pitch, num, num_pitch, status);
+    launch_gen_WT<L, ulonglong2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
   else
-    mesh_gen_kernel<L, uint64_t><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, (const float4*)scales, scale_pitch, s,
-                                                                  s_pitch, num, num_pitch, status);
+    launch_gen_WT<L, uint64_t>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
   return cudaGetLastError();
 }
 

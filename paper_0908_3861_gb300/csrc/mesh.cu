@@ -20,6 +20,10 @@
 // rounding C_k = rint(c_k 2^Q) use binary64 with explicit round-to-nearest
 // intrinsics (no contraction into fused multiply-adds), so the integers agree
 // with any other IEEE implementation of the same operation sequence.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "abf_internal.cuh"
 
 
@@ -723,12 +727,48 @@ static bool mesh_fast_ok(const PlanView& pv) {
 }
 
 // Dynamic shared memory of a launch with `warps` rows per CTA: one tap table
-// per warp; above 48 KB the kernel must opt in.
+// per warp; above 48 KB the kernel must opt in.  The shared-memory carveout is
+// also set to what the CTAs that the register file admits per SM need, so that
+// the rest of the unified L1/shared storage stays L1 for the g patches and the
+// table rows.  The carveout is a property of the kernel, not of a launch: it is
+// set again whenever the rows per CTA of the next launch need another one.
 template <typename K>
 static cudaError_t tap_smem(K kernel, int taps, int warps, size_t* bytes) {
   *bytes = (size_t)warps * taps * sizeof(int4);
-  if (*bytes > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+  cudaError_t e = cudaSuccess;
+  if (*bytes > 48 * 1024) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> pct_of;  // (kernel, rows per CTA) -> carveout percent
+  static std::map<const void*, int> set_to;                  // kernel -> carveout last set
+  std::lock_guard<std::mutex> lk(mu);
+  const std::pair<const void*, int> key((const void*)kernel, warps);
+  auto it = pct_of.find(key);
+  if (it == pct_of.end()) {
+    int pct = -1;
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0;
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        fa.numRegs > 0 && smem_sm > 0) {
+      const int threads = 32 * warps;
+      int ctas = 65536 / (fa.numRegs * threads);
+      if (ctas < 1) ctas = 1;
+      const size_t need = (size_t)ctas * (fa.sharedSizeBytes + *bytes + 1024);
+      pct = (int)((need * 100 + smem_sm - 1) / smem_sm);
+      if (pct > 100) pct = 100;
+    }
+    cudaGetLastError();
+    it = pct_of.emplace(key, pct).first;
+  }
+  if (it->second >= 0) {
+    auto s = set_to.find(key.first);
+    if (s == set_to.end() || s->second != it->second) {
+      if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, it->second) == cudaSuccess)
+        set_to[key.first] = it->second;
+      cudaGetLastError();
+    }
+  }
   return cudaSuccess;
 }
 
