@@ -630,6 +630,8 @@ struct PlanView {
   int E;                          // 0: phi = delta
   int R, dminx, dminy;            // generalised table: neighbours per row, stencil box origin
   const int2* stencil;            // generalised table: the R neighbours (dx, dy)
+  const void* gtaps;              // generalised mesh: the taps grouped by FD weight
+  double out_scale;               // generalised mesh: 2^(Q sum r - F) / D
   int ox, oy;                     // output pixel m sits at lattice point m + (ox, oy)
 };
 
@@ -694,6 +696,23 @@ __device__ __forceinline__ bool pixel_steps(const PlanView& pv, const float4* sc
                                             int x, int y, int C[4]) {
   const float4 sc = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(scales) +
                                                      (size_t)y * scale_pitch + (size_t)x * sizeof(float4));
+  if (pv.scale_kind == ABF_SCALES_C4) {
+    // direct steps: c 2^Q is exact in binary32 (a power-of-two scaling; inf
+    // when it overflows) and rintf rounds it as rint would in binary64, so the
+    // same integers come out without the binary64 pipe
+    const float cf[4] = {sc.x, sc.y, sc.z, sc.w};
+    const float q = ldexpf(1.0f, pv.Q);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!isfinite(cf[k]) || !(cf[k] > 0.0f)) return false;
+      const float v = cf[k] * q;
+      if (!(v < 2147483648.0f)) return false;
+      const int r = __float2int_rn(v);
+      if (r < 1 || r > pv.Cmax) return false;
+      C[k] = r;
+    }
+    return C[0] >= pv.Cmin && C[2] >= pv.Cmin;
+  }
   double c[4];
   const double cmax = ldexp((double)pv.Cmax, -pv.Q);
   if (!read_steps(pv.scale_kind, sc, pv.n, cmax, c)) return false;
@@ -779,7 +798,7 @@ struct abf_plan_s {
   void* d_pf_tmp = nullptr;    // prefilter intermediate (int64), H rows x sv.W, and the column pass' state
   size_t pf_tmp_bytes = 0;
   void* pf = nullptr;          // prefilter constants (host copy)
-  void* d_stencil = nullptr;
+  void* d_gtaps = nullptr;     // generalised mesh: the taps grouped by FD weight
 };
 
 namespace abf {

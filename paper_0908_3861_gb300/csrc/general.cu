@@ -47,49 +47,27 @@ constexpr int kGenWarps = 8;     // rows per CTA
 
 // ------------------------------------------------------------- mesh kernels
 
-// Per CTA: the stencil of the table rows, and the taps j = (j1..j4) ordered by
-// their FD weight w_j = prod_k (-1)^{j_k} binom(r_k, j_k) (Eq. (RS_filter)),
-// one group per distinct weight, each tap's j packed two bits per direction.
+// The taps j = (j1..j4) of a plan ordered by their FD weight
+// w_j = prod_k (-1)^{j_k} binom(r_k, j_k) (Eq. (RS_filter)), one group per
+// distinct weight, each tap's j packed two bits per direction (r_k <= 3).
+// Built on the host with the plan; a CTA copies it into shared memory.
+struct GenTaps {
+  int taps, ng;
+  int gbeg[12], gw[11];
+  unsigned char order[84];
+};
+static_assert(sizeof(GenTaps) % 4 == 0 && kGenMaxTaps <= 84, "GenTaps is copied as 32-bit words");
+
 struct GenShared {
+  GenTaps t;
   int2 st[kGenMaxR];
-  unsigned char order[kGenMaxTaps];
-  int gbeg[12], gw[11], ng, taps;
 };
 
-__device__ void gen_setup(const PlanView& pv, GenShared& sh) {
+__device__ __forceinline__ void gen_setup(const PlanView& pv, GenShared& sh) {
+  const int* src = reinterpret_cast<const int*>(pv.gtaps);
+  int* dst = reinterpret_cast<int*>(&sh.t);
+  for (int i = threadIdx.x; i < (int)(sizeof(GenTaps) / 4); i += blockDim.x) dst[i] = src[i];
   for (int i = threadIdx.x; i < pv.R; i += blockDim.x) sh.st[i] = pv.stencil[i];
-  if (threadIdx.x == 0) {
-    const int taps = (pv.r[0] + 1) * (pv.r[1] + 1) * (pv.r[2] + 1) * (pv.r[3] + 1);
-    int wt[kGenMaxTaps];
-    unsigned char jj[kGenMaxTaps];
-    for (int t = 0; t < taps; ++t) {
-      int u = t, w = 1, packed = 0;
-      for (int k = 0; k < 4; ++k) {
-        const int rk = pv.r[k], j = u % (rk + 1);
-        u /= rk + 1;
-        int b = 1;  // binom(rk, j), rk <= 3
-        for (int i = 0; i < j; ++i) b = b * (rk - i) / (i + 1);
-        w *= (j & 1) ? -b : b;
-        packed |= j << (2 * k);
-      }
-      wt[t] = w;
-      jj[t] = (unsigned char)packed;
-    }
-    int ng = 0, c = 0;
-    for (int t = 0; t < taps; ++t) {
-      bool seen = false;
-      for (int q = 0; q < ng; ++q) seen |= sh.gw[q] == wt[t];
-      if (!seen) sh.gw[ng++] = wt[t];
-    }
-    for (int q = 0; q < ng; ++q) {
-      sh.gbeg[q] = c;
-      for (int t = 0; t < taps; ++t)
-        if (wt[t] == sh.gw[q]) sh.order[c++] = jj[t];
-    }
-    sh.gbeg[ng] = c;
-    sh.ng = ng;
-    sh.taps = taps;
-  }
 }
 
 // This lane's pixel -> integer steps C_k and a verdict: 0 outside the image,
@@ -132,13 +110,11 @@ __device__ __forceinline__ void gen_store(const PlanView& pv, void* s, size_t s_
     for (int i = 0; i < L; ++i) q[i] = S.w[i];
   }
   if (row) {
-    double den = pv.Dd;
-    int rs = 0;
-    for (int k = 0; k < 4; ++k) {
+    // s = S (2^(Q sum r - F) / D) / prod_k C_k^{r_k}
+    double den = 1.0;
+    for (int k = 0; k < 4; ++k)
       for (int e = 0; e < pv.r[k]; ++e) den *= (double)C[k];
-      rs += pv.r[k];
-    }
-    const double v = ldexp(wto_double<L>(S), pv.Q * rs - pv.F) / den;
+    const double v = (wto_double<L>(S) * pv.out_scale) / den;
     if (f64) reinterpret_cast<double*>(row)[x] = v;
     else reinterpret_cast<float*>(row)[x] = (float)v;
   }
@@ -178,7 +154,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
   int C[4];
   const int ok = gen_lane_steps<L>(pv, scales, scale_pitch, myx, y, C);
   const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
-  const int taps = sh.taps, ng = sh.ng;
+  const int taps = sh.t.taps, ng = sh.t.ng;
   int4* tp = s_tap[warp];
   Wide<L> mine;
   wzero<L>(mine);
@@ -193,7 +169,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     const int Y0y = ((y + pv.oy) << P) + ty;
     __syncwarp();
     for (int slot = lane; slot < taps; slot += 32) {
-      const int u = sh.order[slot];
+      const int u = sh.t.order[slot];
       const int j1 = u & 3, j2 = (u >> 2) & 3, j3 = (u >> 4) & 3, j4 = u >> 6;
       const int Yx = Y0x - 2 * (j1 * c0 + j2 * c1 - j4 * c3);
       const int Yy = Y0y - 2 * (j2 * c1 + j3 * c2 + j4 * c3);
@@ -203,7 +179,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     Wide<L> acc;
     wzero<L>(acc);
     for (int gi = 0; gi < ng; ++gi) {
-      const int tb = sh.gbeg[gi], npairs = (sh.gbeg[gi + 1] - tb) * R;
+      const int tb = sh.t.gbeg[gi], npairs = (sh.t.gbeg[gi + 1] - tb) * R;
       Wide<L> part;
       wzero<L>(part);
       for (int idx = lane; idx < npairs; idx += 32) {
@@ -216,7 +192,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
         const Wide<L> gv = wload<L>(g + ((size_t)k2 * (size_t)pv.Gp + (size_t)(ti.x + d.x)) * L);
         mac_weight<L, WT>(part, gv, __ldg(table + (size_t)ti.z * R + cand));
       }
-      gen_apply_weight<L>(acc, part, sh.gw[gi]);
+      gen_apply_weight<L>(acc, part, sh.t.gw[gi]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -258,7 +234,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
   int C[4];
   const int ok = gen_lane_steps<L>(pv, scales, scale_pitch, myx, y, C);
   const WT* __restrict__ table = reinterpret_cast<const WT*>(pv.table);
-  const int ng = sh.ng;
+  const int ng = sh.t.ng;
   const int grp = lane / G, gl = lane % G;
   const bool has_d = gl < R;
   const int2 d = has_d ? sh.st[gl] : make_int2(0, 0);
@@ -280,9 +256,9 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
       for (int gi = 0; gi < ng; ++gi) {
         Wide<L> part;
         wzero<L>(part);
-        const int te = sh.gbeg[gi + 1];
-        for (int slot = sh.gbeg[gi]; slot < te; ++slot) {
-          const int u = sh.order[slot];
+        const int te = sh.t.gbeg[gi + 1];
+        for (int slot = sh.t.gbeg[gi]; slot < te; ++slot) {
+          const int u = sh.t.order[slot];
           const int j1 = u & 3, j2 = (u >> 2) & 3, j3 = (u >> 4) & 3, j4 = u >> 6;
           const int Yx = Y0x - 2 * (j1 * c0 + j2 * c1 - j4 * c3);
           const int Yy = Y0y - 2 * (j2 * c1 + j3 * c2 + j4 * c3);
@@ -292,7 +268,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
           const Wide<L> gv = wload<L>(g + ((size_t)k2 * Gp + (size_t)((Yx >> P) + pv.left + d.x)) * L);
           mac_weight<L, WT>(part, gv, __ldg(table + (size_t)row * R + gl));
         }
-        gen_apply_weight<L>(acc, part, sh.gw[gi]);
+        gen_apply_weight<L>(acc, part, sh.t.gw[gi]);
       }
     }
 #pragma unroll
@@ -631,6 +607,40 @@ abf_status get_gen_table(int device, const int m[4], int P, GenDevTable* out) {
 
 double u128_d(u128 v) { return (double)(uint64_t)(v >> 64) * 18446744073709551616.0 + (double)(uint64_t)v; }
 
+// The taps of direction counts r grouped by FD weight (groups in order of
+// first appearance, taps in index order within a group).
+void build_gen_taps(const int r[4], abf::GenTaps& gt) {
+  const int taps = (r[0] + 1) * (r[1] + 1) * (r[2] + 1) * (r[3] + 1);
+  std::vector<int> wt((size_t)taps), jj((size_t)taps);
+  for (int t = 0; t < taps; ++t) {
+    int u = t, w = 1, packed = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int rk = r[k], j = u % (rk + 1);
+      u /= rk + 1;
+      int b = 1;  // binom(rk, j)
+      for (int i = 0; i < j; ++i) b = b * (rk - i) / (i + 1);
+      w *= (j & 1) ? -b : b;
+      packed |= j << (2 * k);
+    }
+    wt[(size_t)t] = w;
+    jj[(size_t)t] = packed;
+  }
+  int ng = 0, c = 0;
+  for (int t = 0; t < taps; ++t) {
+    bool seen = false;
+    for (int q = 0; q < ng; ++q) seen |= gt.gw[q] == wt[(size_t)t];
+    if (!seen) gt.gw[ng++] = wt[(size_t)t];
+  }
+  for (int q = 0; q < ng; ++q) {
+    gt.gbeg[q] = c;
+    for (int t = 0; t < taps; ++t)
+      if (wt[(size_t)t] == gt.gw[q]) gt.order[c++] = (unsigned char)jj[(size_t)t];
+  }
+  gt.gbeg[ng] = c;
+  gt.ng = ng;
+  gt.taps = taps;
+}
+
 }  // namespace
 
 namespace abf {
@@ -714,6 +724,7 @@ abf_status create_general_plan(const abf_desc* d, abf_plan p) {
   pv.log2D = std::log2(u128_d(tab.D));
   pv.log2_base = (float)(pv.log2D + std::log2(cbound) + d->in_frac_bits);
   pv.Dd = u128_d(tab.D);
+  pv.out_scale = std::ldexp(1.0 / pv.Dd, Q * (r[0] + r[1] + r[2] + r[3]) - d->in_frac_bits);
   pv.table_bytes_per_w = tab.wbytes;
   pv.table = tab.ptr;
   pv.table_fold = nullptr;
@@ -748,6 +759,13 @@ abf_status create_general_plan(const abf_desc* d, abf_plan p) {
     if (cudaMalloc(&p->d_stage, stage) != cudaSuccess) return ABF_ERR_OOM;
     if (cudaMalloc(&p->d_pf_tmp, p->pf_tmp_bytes) != cudaSuccess) return ABF_ERR_OOM;
   }
+  {
+    GenTaps gt{};
+    build_gen_taps(r, gt);
+    if (cudaMalloc(&p->d_gtaps, sizeof(GenTaps)) != cudaSuccess) return ABF_ERR_OOM;
+    if (cudaMemcpy(p->d_gtaps, &gt, sizeof(GenTaps), cudaMemcpyHostToDevice) != cudaSuccess) return ABF_ERR_CUDA;
+    pv.gtaps = p->d_gtaps;
+  }
   p->general = true;
   p->g_bytes = (size_t)pv.Gp * (size_t)pv.Gh * (size_t)L * 8;
   p->ws_bytes = line_ws_bytes(pv.Gw, pv.Gh, L, n, nullptr, nullptr);
@@ -755,6 +773,8 @@ abf_status create_general_plan(const abf_desc* d, abf_plan p) {
 }
 
 void destroy_general_plan(abf_plan p) {
+  if (p->d_gtaps) cudaFree(p->d_gtaps);
+  p->d_gtaps = nullptr;
   if (p->d_stage) cudaFree(p->d_stage);
   if (p->d_pf_tmp) cudaFree(p->d_pf_tmp);
   delete (PrefilterView*)p->pf;

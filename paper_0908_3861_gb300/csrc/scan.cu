@@ -14,16 +14,19 @@
 // linearly along the line), which the FD of the mesh along v4 annihilates.
 //
 // Kernels:
-//   row_scan   : one CTA per row, its warps on contiguous segments; input
-//                conversion (a0) fused (the 1-D filter's prefiltered models pass
-//                integer coefficients staged by its prefilter instead), all n
-//                folds of v1 together (lane-local
-//                scans + warp shuffles, a running state per fold); segment
-//                states composed through shared memory (affine carries).
-//   line_scan  : v2 / v3 / v4, one thread per line (sheared so that a warp reads
-//                consecutive addresses), lines cut into bands of R rows; bands
-//                are chained by decoupled look-back on per-line flags, with a
-//                bounded wait that raises ABF_DEV_TIMEOUT instead of hanging.
+//   row_scan   : rows of up to 8192 cells: one warp per row in one pass;
+//                longer rows (the 1-D filter's signals): one CTA per row, its
+//                warps on contiguous segments, segment states composed through
+//                shared memory (affine carries).  Input conversion (a0) fused
+//                (the 1-D filter's prefiltered models pass integer
+//                coefficients staged by its prefilter instead), all n folds of
+//                v1 together (lane-local scans + warp shuffles, a running
+//                state per fold).
+//   line_scan  : v2 / v3 / v4, one thread per line and row segment (sheared so
+//                that a warp reads consecutive addresses), lines cut into bands
+//                of kBand rows; bands are chained by decoupled look-back on
+//                per-line flags, with a bounded wait that raises
+//                ABF_DEV_TIMEOUT instead of hanging.
 #include <mutex>
 #include <type_traits>
 
@@ -199,6 +202,53 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
   row_scan_body<L, TIn, NF>(pv, f, f_pitch, g, status, blockIdx.x);
 }
 
+// Rows of up to this many cells are scanned by one warp each, in one pass
+// (the serial chain of a row is then at most 64 chunks).
+constexpr int kRowWarpMaxCells = 8192;
+
+// One warp per row, one pass: the chunks in order, the running states carried
+// from chunk to chunk, the raw input fetched two chunks ahead.  f is read once
+// and g written once; a CTA holds kRowWarps rows.
+template <int L, typename TIn, int NF>
+__device__ __forceinline__ void row_scan_warp_body(const PlanView& pv, const TIn* __restrict__ f, size_t f_pitch,
+                                                   uint64_t* __restrict__ g, int32_t* status, int y, Wide<L>* tile) {
+  const int lane = threadIdx.x & 31;
+  const double scale = ldexp(1.0, pv.F);
+  const double bd = floor(pv.value_bound * scale);
+  const long long bound = bd < 4.0e18 ? (long long)bd : 4000000000000000000ll;
+  const TIn* frow = (y < pv.H) ? reinterpret_cast<const TIn*>(reinterpret_cast<const char*>(f) + (size_t)y * f_pitch)
+                               : nullptr;
+  uint64_t* grow = g + (size_t)y * (size_t)pv.Gp * L;
+  constexpr int chunk = 32 * kRowVec;
+  const int nchunks = (pv.Gw + chunk - 1) / chunk;
+  Wide<L> carry[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) wzero<L>(carry[k]);
+  TIn b0[kRowVec], b1[kRowVec], b2[kRowVec];
+  row_fetch<TIn>(pv, frow, 0, lane, b0);
+  if (nchunks > 1) row_fetch<TIn>(pv, frow, chunk, lane, b1);
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + 2 < nchunks) row_fetch<TIn>(pv, frow, (c + 2) * chunk, lane, b2);
+    row_chunk<L, TIn, NF, true>(pv, b0, grow, c * chunk, lane, scale, bound, status, carry, tile);
+#pragma unroll
+    for (int e = 0; e < kRowVec; ++e) {
+      b0[e] = b1[e];
+      b1[e] = b2[e];
+    }
+  }
+}
+
+template <int L, typename TIn, int NF>
+__global__ void __launch_bounds__(32 * kRowWarps) row_scan_warp_kernel(const PlanView pv, const TIn* __restrict__ f,
+                                                                       size_t f_pitch, uint64_t* __restrict__ g,
+                                                                       int32_t* status) {
+  __shared__ Wide<L> s_tile[kRowWarps][32 * kRowVec];
+  const int warp = threadIdx.x >> 5;
+  const int y = blockIdx.x * kRowWarps + warp;
+  if (y >= pv.Gh) return;
+  row_scan_warp_body<L, TIn, NF>(pv, f, f_pitch, g, status, y, s_tile[warp]);
+}
+
 // ---------------------------------------------------------- lines (v2, v3, v4)
 // One pass per direction carries all n cascaded running sums: per line a state
 // (s_1..s_n), updated per element x as s_1 += x, s_2 += s_1, ..., out = s_n.
@@ -209,11 +259,15 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
 // published its inclusive state P, which enters as T_{dR}(P).
 
 constexpr int kBand = 64;         // rows per band (fewer bands: a shorter look-back chain)
-// Lines per CTA (one per thread): the band is staged in shared memory,
-// kBand x lines x L limbs (32 KB at most, so that several CTAs per SM keep
-// their copies in flight while others wait in the look-back).
+constexpr int kSplit = 4;         // row segments per band, one thread per line and segment
+constexpr int kSeg = kBand / kSplit;
+// Lines per CTA: the band is staged in shared memory, kBand x lines x L limbs
+// (32 KB at most, so that several CTAs per SM keep their copies in flight
+// while others wait in the look-back).
 template <int L>
 __host__ __device__ constexpr int lines_per_cta() { return L <= 2 ? 32 : 16; }
+template <int L>
+__host__ __device__ constexpr int line_threads() { return lines_per_cta<L>() * kSplit; }
 template <int L>
 __host__ __device__ constexpr int band_smem_bytes() { return kBand * lines_per_cta<L>() * L * 8; }
 constexpr uint32_t kFlagAgg = 1, kFlagPrefix = 2;
@@ -303,24 +357,32 @@ __device__ __forceinline__ void cp_async_elem(uint64_t* dst, const uint64_t* src
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// One CTA = one band of kBand rows x lines_per_cta<L>() consecutive lines.  The
-// band's elements are copied once into shared memory (each thread its own
-// line, cp.async, so the copies of all rows are in flight together); the band
-// aggregate, the decoupled look-back and the rescan then work from shared
-// memory, and g is written once: one read and one write of g per pass.
+// One CTA = one band of kBand rows x lines_per_cta<L>() consecutive lines, one
+// thread per line and row segment (kSplit segments of kSeg rows).  Each thread
+// copies its segment of its line into shared memory (cp.async, the copies of
+// all rows in flight together) and sums it from a zero state; the segment
+// aggregates compose into the band aggregate (T_kSeg transports), the
+// segment-0 threads run the decoupled look-back for the band and hand every
+// segment its incoming state, and each thread rescans its staged segment into
+// g: one read and one write of g per pass, with the serial work of a band cut
+// into kSplit pieces that run side by side.
 template <int L, int DIR, int NF>
 __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __restrict__ g, const LineWs& ws,
                                                uint32_t epoch, int32_t* status, int band, int grp) {
   constexpr int LPC = lines_per_cta<L>();
+  constexpr int SW = NF * L;                          // words of one state
   extern __shared__ __align__(16) uint64_t s_band[];  // [kBand][LPC][L]
-  const int l = grp * LPC + threadIdx.x;
+  __shared__ __align__(16) uint64_t s_seg[kSplit * LPC * SW];  // [kSplit][LPC] states (16-byte vector accesses)
+  const int ln = threadIdx.x % LPC, seg = threadIdx.x / LPC;
+  const int l = grp * LPC + ln;
   const bool line_ok = l < ws.nlines;
-  const int y0 = band * kBand;
-  uint64_t* mine = s_band + (size_t)threadIdx.x * L;
+  const int y0 = band * kBand + seg * kSeg;
+  uint64_t* mine = s_band + ((size_t)seg * kSeg * LPC + ln) * L;
+  uint64_t* my_state = s_seg + ((size_t)seg * LPC + ln) * SW;
 
-  // stage the band (zeros outside the box)
+  // stage the segment (zeros outside the box)
 #pragma unroll 8
-  for (int i = 0; i < kBand; ++i) {
+  for (int i = 0; i < kSeg; ++i) {
     const int y = y0 + i;
     const int xi = line_col<DIR>(l, y, pv.Gh);
     const bool ok = line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw;
@@ -329,76 +391,97 @@ __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __r
   }
   cp_async_wait_all();
 
-  // band aggregate from a zero state
+  // segment aggregate from a zero state
   LineState<L, NF> agg;
   st_zero<L, NF>(agg);
 #pragma unroll 8
-  for (int i = 0; i < kBand; ++i) st_step<L, NF>(agg, wload<L>(mine + (size_t)i * LPC * L));
+  for (int i = 0; i < kSeg; ++i) st_step<L, NF>(agg, wload<L>(mine + (size_t)i * LPC * L));
+  st_store<L, NF>(my_state, agg);
+  __syncthreads();
 
-  // decoupled look-back over the bands below (same line)
-  LineState<L, NF> carry;
-  st_zero<L, NF>(carry);
-  const size_t slot = (size_t)band * ws.nlines + (line_ok ? l : 0);
-  if (line_ok) {
-    if (band > 0) {
-      st_store<L, NF>(ws.agg + slot * NF * L, agg);
-      st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);  // release: the aggregate is visible first
-      // Up to kLook predecessor flags are read per round trip (relaxed loads,
-      // then one acquire fence before the values they publish are read): the
-      // walk back to the nearest published prefix takes a quarter of the trips.
-      constexpr int kLook = 4;
-      int bb = band - 1;
-      long long dist = 0;  // rows between the end of band bb and the start of this band
-      long long spins = 0;
-      while (bb >= 0) {
-        uint32_t fl[kLook];
-#pragma unroll
-        for (int q = 0; q < kLook; ++q)
-          fl[q] = bb - q >= 0 ? ld_relaxed(ws.flags + (size_t)(bb - q) * ws.nlines + l) : 0u;
-        int ready = 0;
-        bool prefix = false;
-#pragma unroll
-        for (int q = 0; q < kLook; ++q) {
-          if (ready != q || bb - q < 0) break;
-          if ((fl[q] >> 2) != epoch || (fl[q] & 3u) == 0u) break;
-          ++ready;
-          if ((fl[q] & 3u) == kFlagPrefix) {
-            prefix = true;
-            break;
-          }
-        }
-        if (ready == 0) {
-          if (++spins > kSpinLimit) {
-            raise_status(status, ABF_DEV_TIMEOUT);
-            break;
-          }
-          __nanosleep(100);  // back off: waiting CTAs should not crowd the flags' L2 lines
-          continue;
-        }
-        fence_acquire();
-        for (int q = 0; q < ready; ++q) {
-          const size_t s2 = (size_t)(bb - q) * ws.nlines + l;
-          if (prefix && q == ready - 1) {
-            st_add_transported<L, NF>(carry, st_load<L, NF>(ws.pref + s2 * NF * L), dist);
-          } else {
-            st_add_transported<L, NF>(carry, st_load<L, NF>(ws.agg + s2 * NF * L), dist);
-            dist += kBand;
-          }
-        }
-        if (prefix) break;
-        bb -= ready;
-      }
+  if (seg == 0) {
+    // band aggregate: A <- T_kSeg(A) + (next segment's aggregate)
+    LineState<L, NF> A = agg;
+    for (int q = 1; q < kSplit; ++q) {
+      LineState<L, NF> nx = st_load<L, NF>(s_seg + ((size_t)q * LPC + ln) * SW);
+      st_add_transported<L, NF>(nx, A, kSeg);
+      A = nx;
     }
-    LineState<L, NF> incl = agg;
-    st_add_transported<L, NF>(incl, carry, kBand);
-    st_store<L, NF>(ws.pref + slot * NF * L, incl);
-    st_release(ws.flags + slot, (epoch << 2) | kFlagPrefix);
+    // decoupled look-back over the bands below (same line)
+    LineState<L, NF> carry;
+    st_zero<L, NF>(carry);
+    const size_t slot = (size_t)band * ws.nlines + (line_ok ? l : 0);
+    if (line_ok) {
+      if (band > 0) {
+        st_store<L, NF>(ws.agg + slot * NF * L, A);
+        st_release(ws.flags + slot, (epoch << 2) | kFlagAgg);  // release: the aggregate is visible first
+        // Up to kLook predecessor flags are read per round trip (relaxed loads,
+        // then one acquire fence before the values they publish are read): the
+        // walk back to the nearest published prefix takes a quarter of the trips.
+        constexpr int kLook = 4;
+        int bb = band - 1;
+        long long dist = 0;  // rows between the end of band bb and the start of this band
+        long long spins = 0;
+        while (bb >= 0) {
+          uint32_t fl[kLook];
+#pragma unroll
+          for (int q = 0; q < kLook; ++q)
+            fl[q] = bb - q >= 0 ? ld_relaxed(ws.flags + (size_t)(bb - q) * ws.nlines + l) : 0u;
+          int ready = 0;
+          bool prefix = false;
+#pragma unroll
+          for (int q = 0; q < kLook; ++q) {
+            if (ready != q || bb - q < 0) break;
+            if ((fl[q] >> 2) != epoch || (fl[q] & 3u) == 0u) break;
+            ++ready;
+            if ((fl[q] & 3u) == kFlagPrefix) {
+              prefix = true;
+              break;
+            }
+          }
+          if (ready == 0) {
+            if (++spins > kSpinLimit) {
+              raise_status(status, ABF_DEV_TIMEOUT);
+              break;
+            }
+            __nanosleep(100);  // back off: waiting CTAs should not crowd the flags' L2 lines
+            continue;
+          }
+          fence_acquire();
+          for (int q = 0; q < ready; ++q) {
+            const size_t s2 = (size_t)(bb - q) * ws.nlines + l;
+            if (prefix && q == ready - 1) {
+              st_add_transported<L, NF>(carry, st_load<L, NF>(ws.pref + s2 * NF * L), dist);
+            } else {
+              st_add_transported<L, NF>(carry, st_load<L, NF>(ws.agg + s2 * NF * L), dist);
+              dist += kBand;
+            }
+          }
+          if (prefix) break;
+          bb -= ready;
+        }
+      }
+      LineState<L, NF> incl = A;
+      st_add_transported<L, NF>(incl, carry, kBand);
+      st_store<L, NF>(ws.pref + slot * NF * L, incl);
+      st_release(ws.flags + slot, (epoch << 2) | kFlagPrefix);
+    }
+    // incoming state of every segment: in_0 = carry, in_q = T_kSeg(in_{q-1}) + agg_{q-1}
+    LineState<L, NF> in = carry;
+    for (int q = 0; q < kSplit; ++q) {
+      uint64_t* sq = s_seg + ((size_t)q * LPC + ln) * SW;
+      LineState<L, NF> nx = st_load<L, NF>(sq);
+      st_store<L, NF>(sq, in);
+      st_add_transported<L, NF>(nx, in, kSeg);
+      in = nx;
+    }
   }
+  __syncthreads();
 
-  // rescan the staged band from the carried state and write g
-  LineState<L, NF> st = carry;
+  // rescan the staged segment from its incoming state and write g
+  LineState<L, NF> st = st_load<L, NF>(my_state);
 #pragma unroll 8
-  for (int i = 0; i < kBand; ++i) {
+  for (int i = 0; i < kSeg; ++i) {
     const int y = y0 + i;
     const int xi = line_col<DIR>(l, y, pv.Gh);
     const bool ok = line_ok && y < pv.Gh && xi >= 0 && xi < pv.Gw;
@@ -410,7 +493,7 @@ __device__ __forceinline__ void line_scan_body(const PlanView& pv, uint64_t* __r
 // Bands are taken in ticket order, so every band a look-back waits on belongs
 // to a CTA that started earlier.
 template <int L, int DIR, int NF>
-__global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
+__global__ void __launch_bounds__(line_threads<L>()) line_scan_kernel(const PlanView pv, uint64_t* __restrict__ g,
                                                                        LineWs ws, uint32_t epoch,
                                                                        int32_t* status) {
   __shared__ uint32_t s_ticket;
@@ -430,10 +513,18 @@ __global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_kernel(const Pla
 template <int L, typename TIn>
 static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g,
                                int32_t* status, cudaStream_t st) {
-  const int blocks = pv.Gh;  // one CTA per row
   const int threads = 32 * kRowWarps;
   const TIn* fin = (const TIn*)f;
   const int nf = pv.r[0];
+  if (pv.Gw <= kRowWarpMaxCells) {  // a warp per row
+    const int blocks = (pv.Gh + kRowWarps - 1) / kRowWarps;
+    if (nf == 1) row_scan_warp_kernel<L, TIn, 1><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+    else if (nf == 2) row_scan_warp_kernel<L, TIn, 2><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+    else if (nf == 3) row_scan_warp_kernel<L, TIn, 3><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+    else row_scan_warp_kernel<L, TIn, 4><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+    return cudaGetLastError();
+  }
+  const int blocks = pv.Gh;  // one CTA per row
   if (nf == 1) row_scan_kernel<L, TIn, 1><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
   else if (nf == 2) row_scan_kernel<L, TIn, 2><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
   else if (nf == 3) row_scan_kernel<L, TIn, 3><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
@@ -492,7 +583,7 @@ static cudaError_t launch_lines(const PlanView& pv, uint64_t* g, const LineWs& w
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  line_scan_kernel<L, DIR, NF><<<ctas, lines_per_cta<L>(), smem, st>>>(pv, g, ws, epoch, status);
+  line_scan_kernel<L, DIR, NF><<<ctas, line_threads<L>(), smem, st>>>(pv, g, ws, epoch, status);
   return cudaGetLastError();
 }
 
@@ -699,8 +790,21 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_batch_kernel(const __
   row_scan_body<L, TIn, NF>(jb.pv, (const TIn*)jb.f, jb.f_pitch, jb.g, jb.status, (int)(b - jb.first));
 }
 
+// The same over the rows of all jobs with a warp per row (every job's rows
+// short enough).
+template <int L, typename TIn, int NF>
+__global__ void __launch_bounds__(32 * kRowWarps) row_scan_batch_warp_kernel(const __grid_constant__ IntJobs jobs) {
+  __shared__ Wide<L> s_tile[kRowWarps][32 * kRowVec];
+  const int warp = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kRowWarps + warp;
+  if (b >= jobs.total) return;
+  const IntJob& jb = jobs.job[find_int_job(jobs, b)];
+  row_scan_warp_body<L, TIn, NF>(jb.pv, (const TIn*)jb.f, jb.f_pitch, jb.g, jb.status, (int)(b - jb.first),
+                                 s_tile[warp]);
+}
+
 template <int L, int DIR, int NF>
-__global__ void __launch_bounds__(lines_per_cta<L>()) line_scan_batch_kernel(const __grid_constant__ IntJobs jobs,
+__global__ void __launch_bounds__(line_threads<L>()) line_scan_batch_kernel(const __grid_constant__ IntJobs jobs,
                                                                              uint32_t* ticket, uint32_t epoch) {
   __shared__ uint32_t s_ticket;
   if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
@@ -743,7 +847,7 @@ static cudaError_t launch_lines_batch(const IntIn* in, const int* idx, int m, ui
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  line_scan_batch_kernel<L, DIR, NF><<<(unsigned)t, lines_per_cta<L>(), smem, st>>>(jobs, ticket, epoch);
+  line_scan_batch_kernel<L, DIR, NF><<<(unsigned)t, line_threads<L>(), smem, st>>>(jobs, ticket, epoch);
   return cudaGetLastError();
 }
 
@@ -753,6 +857,7 @@ static cudaError_t integrate_group(const IntIn* in, const int* idx, int m, uint3
   IntJobs jobs;
   jobs.njobs = m;
   long long rows = 0;
+  bool short_rows = true;
   for (int k = 0; k < m; ++k) {
     const IntIn& b = in[idx[k]];
     IntJob& jb = jobs.job[k];
@@ -763,10 +868,15 @@ static cudaError_t integrate_group(const IntIn* in, const int* idx, int m, uint3
     jb.status = b.status;
     jb.first = rows;
     rows += b.pv.Gh;
+    short_rows = short_rows && b.pv.Gw <= kRowWarpMaxCells;
   }
   jobs.total = rows;
   if (rows >= (1ll << 31)) return cudaErrorInvalidValue;
-  row_scan_batch_kernel<L, TIn, NF><<<(unsigned)rows, 32 * kRowWarps, 0, st>>>(jobs);
+  if (short_rows)
+    row_scan_batch_warp_kernel<L, TIn, NF><<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0, st>>>(
+        jobs);
+  else
+    row_scan_batch_kernel<L, TIn, NF><<<(unsigned)rows, 32 * kRowWarps, 0, st>>>(jobs);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_lines_batch<L, 2, NF>(in, idx, m, tickets + 0, epoch0 + 1, st);
   if (e == cudaSuccess) e = launch_lines_batch<L, 3, NF>(in, idx, m, tickets + 1, epoch0 + 2, st);
