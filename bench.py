@@ -132,7 +132,7 @@ def _shape(args):
 MESH_DRAM_BYTES = 158725888 + 15484160
 # DRAM bytes (read + write) of the four integrate passes (row scan + v2, v3, v4
 # line scans) on the same workload, from one ncu capture of the current kernels
-INTEG_DRAM_BYTES = 639796992
+INTEG_DRAM_BYTES = 640559872
 
 
 def _algorithmic_macs(n):
@@ -1128,7 +1128,7 @@ def main():
     ap.add_argument("--pool", type=int, default=8, help="c5: distinct images in the request pool")
     ap.add_argument("--inflight", type=int, default=4, help="c5: concurrent jobs (slots)")
     ap.add_argument("--jobs", type=int, default=2000, help="c5: measured jobs per load (after a tenth as many)")
-    ap.add_argument("--sat-jobs", dest="sat_jobs", type=int, default=48, help="c5: jobs of the saturation burst")
+    ap.add_argument("--sat-jobs", dest="sat_jobs", type=int, default=200, help="c5: jobs of the saturation burst (long enough for a sustained rate)")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="default workload: skip the short serving leg")
     ap.add_argument("--compare", default="plain_f64,tile_f32",
