@@ -359,7 +359,7 @@ def run_ours(args):
                                "frac": (round(integ_bytes / (integ_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
                                         if peaks.get("hbm_gbs") else None),
                                "traffic": INTEG_DRAM_BYTES if (n == 2 and L == 2 and (H, W) == (2048, 2048)) else None,
-                               "kernel": "row_scan_kernel + 3 x line_scan_kernel",
+                               "kernel": "row_scan_warp_kernel + 3 x line_scan_kernel",
                                "bytes_note": "f read once, g written by the row scan, then read and written "
                                              "once per line direction: |f| + 7 |g| per integrate"},
         "clocks": clk,

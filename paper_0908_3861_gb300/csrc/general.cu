@@ -206,6 +206,49 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
   gen_store<L>(pv, s, s_pitch, num, num_pitch, status, myx, y, ok, C, mine);
 }
 
+// One pixel's share of a lane for N = 2, r = (NN, 0, NN, 0): the (NN + 1)^2
+// taps y_j = y0 - j1 c1 v1 - j3 c3 v3 in unrolled loops (positions stepped, no
+// tap table), each tap's product accumulated by its FD weight class: |w_j| =
+// NN^i with i = #{j1, j3 strictly inside 0..NN} (binom(NN, 1) = binom(NN,
+// NN - 1) = NN), the sign (-1)^(j1 + j3); the classes are combined at the end.
+template <int L, typename WT, int NN>
+__device__ __forceinline__ void gen2_pixel(Wide<L>& acc, const PlanView& pv, const uint64_t* __restrict__ g,
+                                           const WT* __restrict__ table, int R, int gl, int2 d, int Y0x, int Y0y,
+                                           int c0, int c2, int P, int mask) {
+  constexpr int K = NN >= 2 ? 3 : 1;
+  Wide<L> ap[K], an[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    wzero<L>(ap[i]);
+    wzero<L>(an[i]);
+  }
+  const int xoff = pv.left + d.x;
+#pragma unroll
+  for (int j3 = 0; j3 <= NN; ++j3) {
+    const int Yy = Y0y - 2 * j3 * c2;
+    const int k2 = (Yy >> P) + d.y;
+    if (k2 < 0) continue;  // taps below the box: g = 0
+    const uint64_t* grow = g + (size_t)k2 * (size_t)pv.Gp * L;
+    const WT* trow = table + (size_t)((Yy & mask) << P) * R + gl;
+#pragma unroll
+    for (int j1 = 0; j1 <= NN; ++j1) {
+      const int Yx = Y0x - 2 * j1 * c0;
+      const Wide<L> gv = wload<L>(grow + (size_t)((Yx >> P) + xoff) * L);
+      const WT wt = __ldg(trow + (size_t)(Yx & mask) * R);
+      const int cls = (j1 > 0 && j1 < NN ? 1 : 0) + (j3 > 0 && j3 < NN ? 1 : 0);
+      if ((j1 + j3) & 1) mac_weight<L, WT>(an[cls], gv, wt);
+      else mac_weight<L, WT>(ap[cls], gv, wt);
+    }
+  }
+  uint64_t m = 1;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    wsub<L>(ap[i], an[i]);
+    wmac<L>(acc, ap[i], m);
+    m *= (uint64_t)NN;
+  }
+}
+
 // Stencils of R <= G <= 32 neighbours (e.g. the 2 x 2 of N = 2, n = 2): the
 // warp owns a run of 32 pixels of a row and works in groups of G lanes, one
 // pixel per group, 32 / G neighbouring pixels at once; lane k of a group
@@ -214,7 +257,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
 // itself (no shared tap table) and the group sums its lanes by butterfly.
 // After each round the group leaders hand the numerators to the lanes that
 // own those pixels.
-template <int L, typename WT, int G>
+template <int L, typename WT, int G, int NN>
 __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
@@ -253,6 +296,9 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
       const int ty = r1 * (c1 - one) + r2 * (c2 - one) + r3 * (c3 - one);
       const int Y0x = ((x0 + pp + pv.ox) << P) + tx;
       const int Y0y = ((y + pv.oy) << P) + ty;
+      if constexpr (NN > 0) {
+        gen2_pixel<L, WT, NN>(acc, pv, g, table, R, gl, d, Y0x, Y0y, c0, c2, P, mask);
+      } else {
       for (int gi = 0; gi < ng; ++gi) {
         Wide<L> part;
         wzero<L>(part);
@@ -269,6 +315,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
           mac_weight<L, WT>(part, gv, __ldg(table + (size_t)row * R + gl));
         }
         gen_apply_weight<L>(acc, part, sh.t.gw[gi]);
+      }
       }
     }
 #pragma unroll
@@ -292,28 +339,45 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
 // (the pair-dealt warp kernel).
 static int gen_group_lanes(int R) { return R <= 4 ? 4 : R <= 16 ? 16 : R <= 32 ? 32 : 0; }
 
+template <int L, typename WT, int NN>
+static void launch_gen_group(int G, dim3 grid, const PlanView& pv, const uint64_t* g, const float4* sc,
+                             size_t scale_pitch, void* s, size_t s_pitch, uint64_t* num, size_t num_pitch,
+                             int32_t* status, cudaStream_t st) {
+  if (G == 4)
+    mesh_gen_group_kernel<L, WT, 4, NN><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                        num_pitch, status);
+  else if (G == 16)
+    mesh_gen_group_kernel<L, WT, 16, NN><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                         num_pitch, status);
+  else
+    mesh_gen_group_kernel<L, WT, 32, NN><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                         num_pitch, status);
+}
+
+// N = 2 (r = (n, 0, n, 0)) with 8-byte weights and at most two limbs takes the
+// unrolled tap loops of gen2_pixel; other plans with up to 32 neighbours the
+// run-time tap groups; wider stencils the pair-dealt warp kernel.
 template <int L, typename WT>
 static void launch_gen_WT(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
   dim3 grid((unsigned)((pv.W + 31) / 32), (unsigned)((pv.H + kGenWarps - 1) / kGenWarps));
   const float4* sc = (const float4*)scales;
-  switch (gen_group_lanes(pv.R)) {
-    case 4:
-      mesh_gen_group_kernel<L, WT, 4><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                      num_pitch, status);
-      break;
-    case 16:
-      mesh_gen_group_kernel<L, WT, 16><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                       num_pitch, status);
-      break;
-    case 32:
-      mesh_gen_group_kernel<L, WT, 32><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                       num_pitch, status);
-      break;
-    default:
-      mesh_gen_kernel<L, WT><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch,
-                                                             status);
+  const int G = gen_group_lanes(pv.R);
+  if (G == 0) {
+    mesh_gen_kernel<L, WT><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch,
+                                                           status);
+    return;
   }
+  const bool n2 = pv.r[1] == 0 && pv.r[3] == 0 && pv.r[0] == pv.r[2] && pv.r[0] >= 1 && pv.r[0] <= 3;
+  if constexpr (L <= 2 && sizeof(WT) == 8) {
+    if (n2) {
+      if (pv.r[0] == 1) launch_gen_group<L, WT, 1>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+      else if (pv.r[0] == 2) launch_gen_group<L, WT, 2>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+      else launch_gen_group<L, WT, 3>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+      return;
+    }
+  }
+  launch_gen_group<L, WT, 0>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
 }
 
 template <int L>

@@ -203,12 +203,14 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_kernel(const PlanView
 }
 
 // Rows of up to this many cells are scanned by one warp each, in one pass
-// (the serial chain of a row is then at most 64 chunks).
+// (the serial chain of a row is then at most 64 chunks).  There are only as
+// many warps as rows, so small CTAs spread them evenly over the SMs.
 constexpr int kRowWarpMaxCells = 8192;
+constexpr int kRowsPerCta = 2;
 
 // One warp per row, one pass: the chunks in order, the running states carried
 // from chunk to chunk, the raw input fetched two chunks ahead.  f is read once
-// and g written once; a CTA holds kRowWarps rows.
+// and g written once; a CTA holds kRowsPerCta rows.
 template <int L, typename TIn, int NF>
 __device__ __forceinline__ void row_scan_warp_body(const PlanView& pv, const TIn* __restrict__ f, size_t f_pitch,
                                                    uint64_t* __restrict__ g, int32_t* status, int y, Wide<L>* tile) {
@@ -239,12 +241,12 @@ __device__ __forceinline__ void row_scan_warp_body(const PlanView& pv, const TIn
 }
 
 template <int L, typename TIn, int NF>
-__global__ void __launch_bounds__(32 * kRowWarps) row_scan_warp_kernel(const PlanView pv, const TIn* __restrict__ f,
-                                                                       size_t f_pitch, uint64_t* __restrict__ g,
-                                                                       int32_t* status) {
-  __shared__ Wide<L> s_tile[kRowWarps][32 * kRowVec];
+__global__ void __launch_bounds__(32 * kRowsPerCta) row_scan_warp_kernel(const PlanView pv, const TIn* __restrict__ f,
+                                                                         size_t f_pitch, uint64_t* __restrict__ g,
+                                                                         int32_t* status) {
+  __shared__ Wide<L> s_tile[kRowsPerCta][32 * kRowVec];
   const int warp = threadIdx.x >> 5;
-  const int y = blockIdx.x * kRowWarps + warp;
+  const int y = blockIdx.x * kRowsPerCta + warp;
   if (y >= pv.Gh) return;
   row_scan_warp_body<L, TIn, NF>(pv, f, f_pitch, g, status, y, s_tile[warp]);
 }
@@ -517,11 +519,12 @@ static cudaError_t launch_rows(const PlanView& pv, const void* f, size_t f_pitch
   const TIn* fin = (const TIn*)f;
   const int nf = pv.r[0];
   if (pv.Gw <= kRowWarpMaxCells) {  // a warp per row
-    const int blocks = (pv.Gh + kRowWarps - 1) / kRowWarps;
-    if (nf == 1) row_scan_warp_kernel<L, TIn, 1><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
-    else if (nf == 2) row_scan_warp_kernel<L, TIn, 2><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
-    else if (nf == 3) row_scan_warp_kernel<L, TIn, 3><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
-    else row_scan_warp_kernel<L, TIn, 4><<<blocks, threads, 0, st>>>(pv, fin, f_pitch, g, status);
+    const int blocks = (pv.Gh + kRowsPerCta - 1) / kRowsPerCta;
+    const int wt = 32 * kRowsPerCta;
+    if (nf == 1) row_scan_warp_kernel<L, TIn, 1><<<blocks, wt, 0, st>>>(pv, fin, f_pitch, g, status);
+    else if (nf == 2) row_scan_warp_kernel<L, TIn, 2><<<blocks, wt, 0, st>>>(pv, fin, f_pitch, g, status);
+    else if (nf == 3) row_scan_warp_kernel<L, TIn, 3><<<blocks, wt, 0, st>>>(pv, fin, f_pitch, g, status);
+    else row_scan_warp_kernel<L, TIn, 4><<<blocks, wt, 0, st>>>(pv, fin, f_pitch, g, status);
     return cudaGetLastError();
   }
   const int blocks = pv.Gh;  // one CTA per row
@@ -793,10 +796,10 @@ __global__ void __launch_bounds__(32 * kRowWarps) row_scan_batch_kernel(const __
 // The same over the rows of all jobs with a warp per row (every job's rows
 // short enough).
 template <int L, typename TIn, int NF>
-__global__ void __launch_bounds__(32 * kRowWarps) row_scan_batch_warp_kernel(const __grid_constant__ IntJobs jobs) {
-  __shared__ Wide<L> s_tile[kRowWarps][32 * kRowVec];
+__global__ void __launch_bounds__(32 * kRowsPerCta) row_scan_batch_warp_kernel(const __grid_constant__ IntJobs jobs) {
+  __shared__ Wide<L> s_tile[kRowsPerCta][32 * kRowVec];
   const int warp = threadIdx.x >> 5;
-  const long long b = (long long)blockIdx.x * kRowWarps + warp;
+  const long long b = (long long)blockIdx.x * kRowsPerCta + warp;
   if (b >= jobs.total) return;
   const IntJob& jb = jobs.job[find_int_job(jobs, b)];
   row_scan_warp_body<L, TIn, NF>(jb.pv, (const TIn*)jb.f, jb.f_pitch, jb.g, jb.status, (int)(b - jb.first),
@@ -873,8 +876,8 @@ static cudaError_t integrate_group(const IntIn* in, const int* idx, int m, uint3
   jobs.total = rows;
   if (rows >= (1ll << 31)) return cudaErrorInvalidValue;
   if (short_rows)
-    row_scan_batch_warp_kernel<L, TIn, NF><<<(unsigned)((rows + kRowWarps - 1) / kRowWarps), 32 * kRowWarps, 0, st>>>(
-        jobs);
+    row_scan_batch_warp_kernel<L, TIn, NF><<<(unsigned)((rows + kRowsPerCta - 1) / kRowsPerCta), 32 * kRowsPerCta, 0,
+                                              st>>>(jobs);
   else
     row_scan_batch_kernel<L, TIn, NF><<<(unsigned)rows, 32 * kRowWarps, 0, st>>>(jobs);
   cudaError_t e = cudaGetLastError();

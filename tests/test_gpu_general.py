@@ -57,6 +57,7 @@ CASES = [
     (2, 3, 0, (21, 45), 2, (1.0, 4.0), "f32"),
     (4, 1, 2, (26, 40), 3, (1.0, 5.0), "u8"),
     (2, 1, 2, (30, 41), 3, (1.0, 6.0), "f32"),
+    (2, 2, 0, (29, 37), 3, (1.0, 6.0), "f32big"),   # two limbs
 ]
 
 
@@ -65,12 +66,18 @@ def test_general_plan_bit_exact(directions, n, E, shape, q, rng_c, kind):
     rng = np.random.default_rng(70 + 7 * n + E)
     if kind == "u8":
         img, F, vb = rng.integers(0, 256, shape).astype(np.uint8), 0, 255.0
+    elif kind == "f32big":
+        # samples up to 2^43 (24-bit integers times 2^20, exact in binary32): the
+        # numerators need a second limb
+        img, F, vb = (rng.integers(-2**23, 2**23, shape) * 2.0**20).astype(np.float32), 16, 2.0**43
     else:
         img, F, vb = synthetic.image_f32_grid(rng, shape, 6.0, 3, 8), 8, 255.0
     sc = _steps(rng, shape, rng_c[0], rng_c[1], directions)
     cmax = rng_c[1]
     s, num, st, L = _run(img, sc, n, q, F, cmax, directions, E, vb)
     assert st == 0
+    if kind == "f32big":
+        assert L == 2
     C = oscales.scales_to_C("c4", sc, n, q, cmax)
     H, W = shape
     fi = (img.astype(np.float64) * (1 << F)).astype(np.int64)
