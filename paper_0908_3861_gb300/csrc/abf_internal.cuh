@@ -632,6 +632,7 @@ struct PlanView {
   const int2* stencil;            // generalised table: the R neighbours (dx, dy)
   const void* gtaps;              // generalised mesh: the taps grouped by FD weight
   double out_scale;               // generalised mesh: 2^(Q sum r - F) / D
+  int den_int;                    // generalised mesh: prod_k C_k^{r_k} fits 63 bits
   int ox, oy;                     // output pixel m sits at lattice point m + (ox, oy)
 };
 
@@ -679,7 +680,11 @@ __device__ __forceinline__ bool read_steps(int kind, float4 sc, int n, double cm
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       double uk = u[k] < 0.0 ? 0.0 : u[k];
-      double ck = __dsqrt_rn(__ddiv_rn(__dmul_rn(12.0, uk), (double)n));
+      // 12 u_k / n: for n = 1, 2 the quotient is the correctly rounded product
+      // with 1/n (exact), the same double as the division gives
+      const double t12 = __dmul_rn(12.0, uk);
+      const double q = n == 1 ? t12 : (n == 2 ? __dmul_rn(t12, 0.5) : __ddiv_rn(t12, (double)n));
+      double ck = __dsqrt_rn(q);
       if (ck < 1.0) ck = 1.0;
       if (ck > cmax) ck = cmax;
       c[k] = ck;

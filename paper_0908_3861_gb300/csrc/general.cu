@@ -110,10 +110,19 @@ __device__ __forceinline__ void gen_store(const PlanView& pv, void* s, size_t s_
     for (int i = 0; i < L; ++i) q[i] = S.w[i];
   }
   if (row) {
-    // s = S (2^(Q sum r - F) / D) / prod_k C_k^{r_k}
-    double den = 1.0;
-    for (int k = 0; k < 4; ++k)
-      for (int e = 0; e < pv.r[k]; ++e) den *= (double)C[k];
+    // s = S (2^(Q sum r - F) / D) / prod_k C_k^{r_k}; the product in 64-bit
+    // integers where it fits (one conversion instead of a binary64 product)
+    double den;
+    if (pv.den_int) {
+      uint64_t p = 1;
+      for (int k = 0; k < 4; ++k)
+        for (int e = 0; e < pv.r[k]; ++e) p *= (uint64_t)C[k];
+      den = (double)p;
+    } else {
+      den = 1.0;
+      for (int k = 0; k < 4; ++k)
+        for (int e = 0; e < pv.r[k]; ++e) den *= (double)C[k];
+    }
     const double v = (wto_double<L>(S) * pv.out_scale) / den;
     if (f64) reinterpret_cast<double*>(row)[x] = v;
     else reinterpret_cast<float*>(row)[x] = (float)v;
@@ -130,7 +139,7 @@ __device__ __forceinline__ void gen_apply_weight(Wide<L>& acc, const Wide<L>& pa
   else wadd<L>(acc, sc);
 }
 
-// Wide stencils (R > 32 neighbours): one warp per run of 32 pixels of a row,
+// Wide stencils (R > 64 neighbours): one warp per run of 32 pixels of a row,
 // as the plain form's generic path.  Lane i reads pixel x0 + i's steps; for
 // each pixel of the run the lanes tabulate its taps (grouped by FD weight) in
 // shared memory and then deal the (tap, neighbour) pairs of each group among
@@ -249,19 +258,20 @@ __device__ __forceinline__ void gen2_pixel(Wide<L>& acc, const PlanView& pv, con
   }
 }
 
-// Stencils of R <= G <= 32 neighbours (e.g. the 2 x 2 of N = 2, n = 2): the
-// warp owns a run of 32 pixels of a row and works in groups of G lanes, one
-// pixel per group, 32 / G neighbouring pixels at once; lane k of a group
-// takes neighbour k of every tap (its table weight is word k of the tap's
+// Stencils of up to 64 neighbours (e.g. the 2 x 2 of N = 2, n = 2): the warp
+// owns a run of 32 pixels of a row and works in groups of G lanes, one pixel
+// per group, 32 / G neighbouring pixels at once; lane k of a group takes
+// neighbour k (and k + 32 when R > 32) of every tap (its table weight is word k of the tap's
 // row, so a group reads one contiguous row piece), computes the tap positions
 // itself (no shared tap table) and the group sums its lanes by butterfly.
 // After each round the group leaders hand the numerators to the lanes that
 // own those pixels.
-template <int L, typename WT, int G, int NN>
+template <int L, typename WT, int G, int NN, int CANDS>
 __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
   static_assert(G == 4 || G == 16 || G == 32, "group of 4, 16 or 32 lanes");
+  static_assert(CANDS == 1 || (CANDS == 2 && G == 32 && NN == 0), "two neighbours per lane: whole-warp groups");
   constexpr int PPR = 32 / G;  // pixels per round
   __shared__ GenShared sh;
   gen_setup(pv, sh);
@@ -281,6 +291,8 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
   const int grp = lane / G, gl = lane % G;
   const bool has_d = gl < R;
   const int2 d = has_d ? sh.st[gl] : make_int2(0, 0);
+  const bool has_d2 = CANDS == 2 && gl + G < R;  // a second neighbour (R > 32)
+  const int2 d2 = has_d2 ? sh.st[gl + G] : make_int2(0, 0);
   const long long Gp = pv.Gp;
   Wide<L> mine;
   wzero<L>(mine);
@@ -308,11 +320,20 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
           const int j1 = u & 3, j2 = (u >> 2) & 3, j3 = (u >> 4) & 3, j4 = u >> 6;
           const int Yx = Y0x - 2 * (j1 * c0 + j2 * c1 - j4 * c3);
           const int Yy = Y0y - 2 * (j2 * c1 + j3 * c2 + j4 * c3);
-          const int k2 = (Yy >> P) + d.y;
-          if (k2 < 0) continue;  // rows below the box: g = 0
-          const int row = ((Yy & mask) << P) | (Yx & mask);
-          const Wide<L> gv = wload<L>(g + ((size_t)k2 * Gp + (size_t)((Yx >> P) + pv.left + d.x)) * L);
-          mac_weight<L, WT>(part, gv, __ldg(table + (size_t)row * R + gl));
+          const int py = Yy >> P, px = (Yx >> P) + pv.left;
+          const WT* trow = table + (size_t)(((Yy & mask) << P) | (Yx & mask)) * R;
+          const int k2 = py + d.y;
+          if (k2 >= 0) {  // rows below the box: g = 0
+            const Wide<L> gv = wload<L>(g + ((size_t)k2 * Gp + (size_t)(px + d.x)) * L);
+            mac_weight<L, WT>(part, gv, __ldg(trow + gl));
+          }
+          if constexpr (CANDS == 2) {
+            const int k2b = py + d2.y;
+            if (has_d2 && k2b >= 0) {
+              const Wide<L> gv = wload<L>(g + ((size_t)k2b * Gp + (size_t)(px + d2.x)) * L);
+              mac_weight<L, WT>(part, gv, __ldg(trow + gl + G));
+            }
+          }
         }
         gen_apply_weight<L>(acc, part, sh.t.gw[gi]);
       }
@@ -335,28 +356,32 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
 }
 
 // Lanes per pixel for a table of R neighbours: a group of 4 (the 2 x 2 stencil
-// of N = 2, n = 2), 16 (3 x 3 and 4 x 4) or the whole warp (up to 32), else 0
-// (the pair-dealt warp kernel).
-static int gen_group_lanes(int R) { return R <= 4 ? 4 : R <= 16 ? 16 : R <= 32 ? 32 : 0; }
+// of N = 2, n = 2), 16 (3 x 3 and 4 x 4) or the whole warp (up to 32 lanes with
+// one neighbour each, up to 64 with two), else 0 (the pair-dealt warp kernel).
+static int gen_group_lanes(int R) { return R <= 4 ? 4 : R <= 16 ? 16 : R <= 64 ? 32 : 0; }
 
 template <int L, typename WT, int NN>
 static void launch_gen_group(int G, dim3 grid, const PlanView& pv, const uint64_t* g, const float4* sc,
                              size_t scale_pitch, void* s, size_t s_pitch, uint64_t* num, size_t num_pitch,
                              int32_t* status, cudaStream_t st) {
   if (G == 4)
-    mesh_gen_group_kernel<L, WT, 4, NN><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                        num_pitch, status);
+    mesh_gen_group_kernel<L, WT, 4, NN, 1><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
+                                                                           num_pitch, status);
   else if (G == 16)
-    mesh_gen_group_kernel<L, WT, 16, NN><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                         num_pitch, status);
-  else
-    mesh_gen_group_kernel<L, WT, 32, NN><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                         num_pitch, status);
+    mesh_gen_group_kernel<L, WT, 16, NN, 1><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                            num, num_pitch, status);
+  else if (NN > 0 || pv.R <= 32)
+    mesh_gen_group_kernel<L, WT, 32, NN, 1><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                            num, num_pitch, status);
+  else if constexpr (NN == 0)
+    mesh_gen_group_kernel<L, WT, 32, 0, 2><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                           num, num_pitch, status);
 }
 
-// N = 2 (r = (n, 0, n, 0)) with 8-byte weights and at most two limbs takes the
-// unrolled tap loops of gen2_pixel; other plans with up to 32 neighbours the
-// run-time tap groups; wider stencils the pair-dealt warp kernel.
+// N = 2 (r = (n, 0, n, 0)) with up to 32 neighbours, 8-byte weights and at most
+// two limbs takes the unrolled tap loops of gen2_pixel; other plans with up to
+// 64 neighbours the run-time tap groups (two neighbours per lane above 32);
+// wider stencils the pair-dealt warp kernel.
 template <int L, typename WT>
 static void launch_gen_WT(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
@@ -368,7 +393,7 @@ static void launch_gen_WT(const PlanView& pv, const uint64_t* g, const void* sca
                                                            status);
     return;
   }
-  const bool n2 = pv.r[1] == 0 && pv.r[3] == 0 && pv.r[0] == pv.r[2] && pv.r[0] >= 1 && pv.r[0] <= 3;
+  const bool n2 = pv.r[1] == 0 && pv.r[3] == 0 && pv.r[0] == pv.r[2] && pv.r[0] >= 1 && pv.r[0] <= 3 && pv.R <= 32;
   if constexpr (L <= 2 && sizeof(WT) == 8) {
     if (n2) {
       if (pv.r[0] == 1) launch_gen_group<L, WT, 1>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
@@ -789,6 +814,7 @@ abf_status create_general_plan(const abf_desc* d, abf_plan p) {
   pv.log2_base = (float)(pv.log2D + std::log2(cbound) + d->in_frac_bits);
   pv.Dd = u128_d(tab.D);
   pv.out_scale = std::ldexp(1.0 / pv.Dd, Q * (r[0] + r[1] + r[2] + r[3]) - d->in_frac_bits);
+  pv.den_int = (r[0] + r[1] + r[2] + r[3]) * std::log2((double)Cmax + 1.0) < 63.0 ? 1 : 0;
   pv.table_bytes_per_w = tab.wbytes;
   pv.table = tab.ptr;
   pv.table_fold = nullptr;
