@@ -132,7 +132,7 @@ def _shape(args):
 MESH_DRAM_BYTES = 158931200 + 27586816
 # DRAM bytes (read + write) of the four integrate passes (row scan + v2, v3, v4
 # line scans) on the same workload, from one ncu capture of the current kernels
-INTEG_DRAM_BYTES = 640559872
+INTEG_DRAM_BYTES = 630252544
 
 
 def _algorithmic_macs(n):
