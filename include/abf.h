@@ -94,7 +94,7 @@ typedef struct {
   int32_t scale_kind;         /* abf_scale_kind                                       */
   int32_t q_bits;             /* Q: steps on the 2^-Q grid (1..9 for n = 1, else 1..8) */
   int32_t in_frac_bits;       /* F: f 2^F is an integer (exact form); 0 for u8/u16    */
-  int32_t flags;              /* reserved, 0                                          */
+  int32_t flags;              /* 0 or ABF_FLAG_DEBUG_BOUNDS                           */
   double max_scale;           /* upper bound on every step c_k (lattice units)        */
   double min_scale;           /* lower bound on c1 and c3 (>= 2^-Q); 0 means 1.0      */
   double value_bound;         /* upper bound on |f|; 0 means the dtype's range (u8,   *
@@ -397,7 +397,26 @@ abf_status abf_plan_denominator(abf_plan plan, uint32_t* d_words4);
 #define ABF_DEV_BAD_INPUT   8   /* f 2^F not an integer within value_bound (exact form)   */
 #define ABF_DEV_PRECISION  16   /* floating-point forms: a pixel's error bound exceeded the
                                    form's tolerance (the pixel is NaN)                     */
+#define ABF_DEV_BOUNDS     32   /* ABF_FLAG_DEBUG_BOUNDS: a tap's reads left the lattice box */
 abf_status abf_last_device_status(abf_plan plan, int32_t* code);
+
+/* Bounds checking of the adaptive step (no counterpart in the paper: a check
+ * of the lattice box the plan sizes from Sec. 7's reach of the taps).  A plan
+ * created with abf_desc.flags = ABF_FLAG_DEBUG_BOUNDS (exact form) runs
+ * abf_filter / abf_filter_numerator with checked kernels: before any read,
+ * every tap's lattice point plus the order's stencil box (generalised plans:
+ * each lane's neighbour at the extreme taps of the pixel) must lie inside the
+ * lattice box (columns 0 .. Gw - 1, rows up to Gh - 1; rows below 0 are zero
+ * by definition and never read).  Reads that would leave it are not made (the
+ * tap, or that lane's share of the pixel, adds nothing), the status word gets
+ * ABF_DEV_BOUNDS and the first such pixel (first in device order) is
+ * recorded.  abf_debug_bounds_violation returns that pixel as y W + x, or -1
+ * if none, and clears the record (synchronises the device).  Returns
+ * ABF_ERR_INVALID for a plan created without the flag.  Batched launches
+ * (abf_filter_batch, grouped serving) and plans without the flag run the
+ * unchecked kernels.  ABF_ERR_UNSUPPORTED for the floating-point forms.     */
+#define ABF_FLAG_DEBUG_BOUNDS 1
+abf_status abf_debug_bounds_violation(abf_plan plan, int64_t* pixel);
 
 const char* abf_status_str(abf_status s);
 

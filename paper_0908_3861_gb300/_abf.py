@@ -19,6 +19,8 @@ ABF_U8, ABF_U16, ABF_F32, ABF_F64 = 0, 1, 2, 3
 ABF_FORM_EXACT, ABF_FORM_PLAIN_F64, ABF_FORM_TILE_F32 = 0, 1, 2
 ABF_SCALES_C4, ABF_SCALES_A4, ABF_SCALES_ELLIPSE = 0, 1, 2
 ABF_DEV_BAD_SCALE, ABF_DEV_RANGE, ABF_DEV_TIMEOUT, ABF_DEV_BAD_INPUT, ABF_DEV_PRECISION = 1, 2, 4, 8, 16
+ABF_DEV_BOUNDS = 32
+ABF_FLAG_DEBUG_BOUNDS = 1
 
 SCALE_KINDS = {"c4": ABF_SCALES_C4, "a4": ABF_SCALES_A4, "ellipse": ABF_SCALES_ELLIPSE}
 FORMS = {"exact": ABF_FORM_EXACT, "plain_f64": ABF_FORM_PLAIN_F64, "tile_f32": ABF_FORM_TILE_F32}
@@ -92,6 +94,7 @@ def signatures():
         "abf_prepare_scales": ([vp, vp, sz, vp, sz, vp], st),
         "abf_plan_denominator": ([vp, P(ctypes.c_uint32)], st),
         "abf_last_device_status": ([vp, P(i32)], st),
+        "abf_debug_bounds_violation": ([vp, P(ctypes.c_int64)], st),
         "abf_measure_scales": ([P(abf_desc), vp, sz, P(ctypes.c_double), P(ctypes.c_double), vp], st),
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
@@ -222,6 +225,14 @@ def abf_last_device_status(plan):
     c = ctypes.c_int32()
     _check(lib().abf_last_device_status(plan, ctypes.byref(c)), "abf_last_device_status")
     return c.value
+
+
+def abf_debug_bounds_violation(plan):
+    """The first pixel (y W + x) whose taps would have read outside the lattice
+    box, or -1 (plans created with ABF_FLAG_DEBUG_BOUNDS; clears the record)."""
+    v = ctypes.c_int64()
+    _check(lib().abf_debug_bounds_violation(plan, ctypes.byref(v)), "abf_debug_bounds_violation")
+    return v.value
 
 
 def abf_measure_scales(desc, scales, scale_pitch, stream=None):

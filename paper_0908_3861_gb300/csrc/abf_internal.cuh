@@ -633,6 +633,7 @@ struct PlanView {
   const void* gtaps;              // generalised mesh: the taps grouped by FD weight
   double out_scale;               // generalised mesh: 2^(Q sum r - F) / D
   int den_int;                    // generalised mesh: prod_k C_k^{r_k} fits 63 bits
+  unsigned long long* dbg;        // ABF_FLAG_DEBUG_BOUNDS: first violating pixel + 1, else null
   int ox, oy;                     // output pixel m sits at lattice point m + (ox, oy)
 };
 
@@ -740,6 +741,19 @@ __device__ __forceinline__ void raise_status(int32_t* st, int32_t bits) {
   atomicOr(st, bits);
 }
 
+// ABF_FLAG_DEBUG_BOUNDS: whether the reads of a tap whose lattice point is box
+// column cx, row py, with stencil offsets dx in [dxlo, dxhi] and dy <= dyhi,
+// stay in the lattice box (rows below 0 are never read).  On a violation the
+// status gets ABF_DEV_BOUNDS and the first pixel is recorded; the caller
+// skips the tap.
+__device__ __forceinline__ bool dbg_tap_ok(const PlanView& pv, int32_t* status, int cx, int py, int dxlo, int dxhi,
+                                           int dyhi, int x, int y) {
+  if (cx + dxlo >= 0 && cx + dxhi < pv.Gw && py + dyhi < pv.Gh) return true;
+  raise_status(status, ABF_DEV_BOUNDS);
+  atomicCAS(pv.dbg, 0ull, (unsigned long long)y * (unsigned long long)pv.W + (unsigned long long)x + 1ull);
+  return false;
+}
+
 // Input element -> integer f 2^F; raises ABF_DEV_BAD_INPUT (and reads 0) when
 // a floating-point value is off the 2^-F grid or beyond the value bound
 // (bound_i = floor(value_bound 2^F)).  binary32 inputs are checked in binary32
@@ -804,6 +818,7 @@ struct abf_plan_s {
   size_t pf_tmp_bytes = 0;
   void* pf = nullptr;          // prefilter constants (host copy)
   void* d_gtaps = nullptr;     // generalised mesh: the taps grouped by FD weight
+  void* d_dbg = nullptr;       // ABF_FLAG_DEBUG_BOUNDS: the first violating pixel + 1
 };
 
 namespace abf {

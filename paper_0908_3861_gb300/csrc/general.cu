@@ -144,7 +144,7 @@ __device__ __forceinline__ void gen_apply_weight(Wide<L>& acc, const Wide<L>& pa
 // each pixel of the run the lanes tabulate its taps (grouped by FD weight) in
 // shared memory and then deal the (tap, neighbour) pairs of each group among
 // themselves.
-template <int L, typename WT>
+template <int L, typename WT, bool DBG>
 __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
         const int2 d = sh.st[cand];
         const int k2 = ti.y + d.y;
         if (k2 < 0) continue;  // rows below the box: g = 0
+        if (DBG && !dbg_tap_ok(pv, status, ti.x, ti.y, d.x, d.x, d.y, x0 + pp, y)) continue;
         const Wide<L> gv = wload<L>(g + ((size_t)k2 * (size_t)pv.Gp + (size_t)(ti.x + d.x)) * L);
         mac_weight<L, WT>(part, gv, __ldg(table + (size_t)ti.z * R + cand));
       }
@@ -213,6 +214,18 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_kernel(
     if (lane == pp) mine = acc;
   }
   gen_store<L>(pv, s, s_pitch, num, num_pitch, status, myx, y, ok, C, mine);
+}
+
+// Bounds checking for one lane and pixel: the taps y0 - sum_k j_k c_k v_k,
+// 0 <= j_k <= r_k, span columns from the all-v1-and-v2 corner to the all-v4
+// corner and rows up to y0 itself; with the lane's neighbour d added, that
+// span must lie in the lattice box (rows below 0 are never read).
+__device__ __forceinline__ bool gen_dbg_lane(const PlanView& pv, int32_t* status, int Y0x, int Y0y, int c0, int c1,
+                                             int c2, int c3, int2 d, int P, int x, int y) {
+  (void)c2;
+  const int xlo = ((Y0x - 2 * (pv.r[0] * c0 + pv.r[1] * c1)) >> P) + pv.left;
+  const int xhi = ((Y0x + 2 * pv.r[3] * c3) >> P) + pv.left;
+  return dbg_tap_ok(pv, status, xlo, Y0y >> P, d.x, d.x + (xhi - xlo), d.y, x, y);
 }
 
 // One pixel's share of a lane for N = 2, r = (NN, 0, NN, 0): the (NN + 1)^2
@@ -266,7 +279,7 @@ __device__ __forceinline__ void gen2_pixel(Wide<L>& acc, const PlanView& pv, con
 // itself (no shared tap table) and the group sums its lanes by butterfly.
 // After each round the group leaders hand the numerators to the lanes that
 // own those pixels.
-template <int L, typename WT, int G, int NN, int CANDS>
+template <int L, typename WT, int G, int NN, int CANDS, bool DBG>
 __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
@@ -308,7 +321,13 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
       const int ty = r1 * (c1 - one) + r2 * (c2 - one) + r3 * (c3 - one);
       const int Y0x = ((x0 + pp + pv.ox) << P) + tx;
       const int Y0y = ((y + pv.oy) << P) + ty;
-      if constexpr (NN > 0) {
+      // bounds checking: this lane's reads of the pixel (all taps, its
+      // neighbours) must stay in the box, else the lane reads nothing for it
+      const bool skip =
+          DBG && (!gen_dbg_lane(pv, status, Y0x, Y0y, c0, c1, c2, c3, d, P, x0 + pp, y) ||
+                     (CANDS == 2 && has_d2 && !gen_dbg_lane(pv, status, Y0x, Y0y, c0, c1, c2, c3, d2, P, x0 + pp, y)));
+      if (skip) {
+      } else if constexpr (NN > 0) {
         gen2_pixel<L, WT, NN>(acc, pv, g, table, R, gl, d, Y0x, Y0y, c0, c2, P, mask);
       } else {
       for (int gi = 0; gi < ng; ++gi) {
@@ -360,58 +379,62 @@ __global__ void __launch_bounds__(32 * kGenWarps) mesh_gen_group_kernel(
 // one neighbour each, up to 64 with two), else 0 (the pair-dealt warp kernel).
 static int gen_group_lanes(int R) { return R <= 4 ? 4 : R <= 16 ? 16 : R <= 64 ? 32 : 0; }
 
-template <int L, typename WT, int NN>
+template <int L, typename WT, int NN, bool DBG>
 static void launch_gen_group(int G, dim3 grid, const PlanView& pv, const uint64_t* g, const float4* sc,
                              size_t scale_pitch, void* s, size_t s_pitch, uint64_t* num, size_t num_pitch,
                              int32_t* status, cudaStream_t st) {
   if (G == 4)
-    mesh_gen_group_kernel<L, WT, 4, NN, 1><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num,
-                                                                           num_pitch, status);
+    mesh_gen_group_kernel<L, WT, 4, NN, 1, DBG><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                                num, num_pitch, status);
   else if (G == 16)
-    mesh_gen_group_kernel<L, WT, 16, NN, 1><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
-                                                                            num, num_pitch, status);
+    mesh_gen_group_kernel<L, WT, 16, NN, 1, DBG><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                                 num, num_pitch, status);
   else if (NN > 0 || pv.R <= 32)
-    mesh_gen_group_kernel<L, WT, 32, NN, 1><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
-                                                                            num, num_pitch, status);
+    mesh_gen_group_kernel<L, WT, 32, NN, 1, DBG><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                                 num, num_pitch, status);
   else if constexpr (NN == 0)
-    mesh_gen_group_kernel<L, WT, 32, 0, 2><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
-                                                                           num, num_pitch, status);
+    mesh_gen_group_kernel<L, WT, 32, 0, 2, DBG><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch,
+                                                                                num, num_pitch, status);
 }
 
 // N = 2 (r = (n, 0, n, 0)) with up to 32 neighbours, 8-byte weights and at most
 // two limbs takes the unrolled tap loops of gen2_pixel; other plans with up to
 // 64 neighbours the run-time tap groups (two neighbours per lane above 32);
 // wider stencils the pair-dealt warp kernel.
-template <int L, typename WT>
+template <int L, typename WT, bool DBG>
 static void launch_gen_WT(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
                           size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
   dim3 grid((unsigned)((pv.W + 31) / 32), (unsigned)((pv.H + kGenWarps - 1) / kGenWarps));
   const float4* sc = (const float4*)scales;
   const int G = gen_group_lanes(pv.R);
   if (G == 0) {
-    mesh_gen_kernel<L, WT><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch,
-                                                           status);
+    mesh_gen_kernel<L, WT, DBG><<<grid, 32 * kGenWarps, 0, st>>>(pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch,
+                                                                status);
     return;
   }
   const bool n2 = pv.r[1] == 0 && pv.r[3] == 0 && pv.r[0] == pv.r[2] && pv.r[0] >= 1 && pv.r[0] <= 3 && pv.R <= 32;
   if constexpr (L <= 2 && sizeof(WT) == 8) {
     if (n2) {
-      if (pv.r[0] == 1) launch_gen_group<L, WT, 1>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-      else if (pv.r[0] == 2) launch_gen_group<L, WT, 2>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-      else launch_gen_group<L, WT, 3>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+      if (pv.r[0] == 1) launch_gen_group<L, WT, 1, DBG>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+      else if (pv.r[0] == 2) launch_gen_group<L, WT, 2, DBG>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+      else launch_gen_group<L, WT, 3, DBG>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
       return;
     }
   }
-  launch_gen_group<L, WT, 0>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+  launch_gen_group<L, WT, 0, DBG>(G, grid, pv, g, sc, scale_pitch, s, s_pitch, num, num_pitch, status, st);
 }
 
 template <int L>
 static cudaError_t launch_gen_L(const PlanView& pv, const uint64_t* g, const void* scales, size_t scale_pitch, void* s,
                                 size_t s_pitch, uint64_t* num, size_t num_pitch, int32_t* status, cudaStream_t st) {
-  if (pv.table_bytes_per_w == 16)
-    launch_gen_WT<L, ulonglong2>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
-  else
-    launch_gen_WT<L, uint64_t>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+  const bool w16 = pv.table_bytes_per_w == 16;
+  if (pv.dbg) {
+    if (w16) launch_gen_WT<L, ulonglong2, true>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    else launch_gen_WT<L, uint64_t, true>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+  } else {
+    if (w16) launch_gen_WT<L, ulonglong2, false>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+    else launch_gen_WT<L, uint64_t, false>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, st);
+  }
   return cudaGetLastError();
 }
 

@@ -286,6 +286,26 @@ __device__ __forceinline__ void n2_pixel(Wide<L>& acc, const int4* taps, const u
   }
 }
 
+// Bounds checking of one pixel's tabulated taps (the fast paths' records:
+// x = g offset row * Gp + box column, y = table offset, z = lattice row): a
+// tap whose stencil box would leave the lattice box is pointed at the table's
+// zero row (zrow) and at the patch in the box corner, so it reads in bounds
+// and adds nothing.  Taps wholly below row 0 already read that way.
+template <int N>
+__device__ __forceinline__ void dbg_taps(const PlanView& pv, int32_t* status, int4* taps, int ntaps, int zrow,
+                                         int lane, int x, int y) {
+  constexpr int kDlo = Stencil<N>::kDmin, kDhi = Stencil<N>::kDmin + 3 * N - 1;
+  const int gp = (int)pv.Gp;
+  __syncwarp();
+  for (int slot = lane; slot < ntaps; slot += 32) {
+    const int4 t = taps[slot];
+    if (t.z + kDhi < 0) continue;  // below row 0: redirected already
+    const int cx = t.x - t.z * gp;  // box column of the tap's lattice point
+    if (!dbg_tap_ok(pv, status, cx, t.z, kDlo, kDhi, kDhi, x, y))
+      taps[slot] = make_int4(-kDlo * gp - kDlo, zrow, -kDlo, 0);
+  }
+}
+
 // Mesh for the run of 32 pixels (x0 .. x0+31, y) of one image; the whole warp
 // calls it.  taps: this warp's (n+1)^4-entry shared tap table; s_dx/s_dy: the
 // order-n stencil in shared memory.  FAST (n = 2, 3): taps carry plain g and
@@ -293,7 +313,7 @@ __device__ __forceinline__ void n2_pixel(Wide<L>& acc, const int4* taps, const u
 // n3_pixel); s_order is then the group-sorted tap order, s_off (n = 3) the
 // neighbours' g offsets dy Gp + dx, and g offsets must fit 32 bits and the
 // box have at least 3n rows.
-template <int N, int L, bool FAST = false>
+template <int N, int L, bool FAST = false, bool DBG = false>
 __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __restrict__ g,
                                          const float4* __restrict__ scales, size_t scale_pitch, void* __restrict__ s,
                                          size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch,
@@ -372,6 +392,7 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
         const int frow = below ? (half + 1) * (half + 2) / 2 : (Y * (Y + 1) >> 1) + X;
         taps[slot] = make_int4(xf, frow * R, py, below ? 0 : (fx | (fy << 1) | (sw << 2)));
       }
+      if constexpr (DBG) dbg_taps<N>(pv, status, taps, TAPS, (half + 1) * (half + 2) / 2 * R, lane, x0 + pp, y);
       const bool check = __any_sync(0xffffffffu, strad) != 0;
       __syncwarp();
       const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(pv.table_fold);
@@ -395,6 +416,7 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
         const int tf = (below ? (1 << (2 * P)) : r) * R;
         taps[slot] = make_int4(xf, tf, py, 0);
       }
+      if constexpr (DBG) dbg_taps<N>(pv, status, taps, TAPS, (1 << (2 * P)) * R, lane, x0 + pp, y);
       const bool check = __any_sync(0xffffffffu, strad) != 0;
       __syncwarp();
       const uint64_t* gl = g + ((ptrdiff_t)my_dy * rowpitch + my_dx) * L;
@@ -419,6 +441,13 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
         // n = 2: store the shift k of |w| = 2^k; otherwise |w|
         const int aw = w < 0 ? -w : w;
         taps[t] = make_int4(px + left, py, r, ((N == 2) ? (__ffs(aw) - 1) : aw) * (w < 0 ? -1 : 1) - (w < 0 ? 1 : 0));
+        // bounds checking: a tap whose reads would leave the box gets a row
+        // so far below 0 that none of its reads happen
+        if constexpr (DBG) {
+          constexpr int kDlo = Stencil<N>::kDmin, kDhi = Stencil<N>::kDmin + 3 * N - 1;
+          if (py + kDhi >= 0 && !dbg_tap_ok(pv, status, px + left, py, kDlo, kDhi, kDhi, x0 + pp, y))
+            taps[t].y = -(1 << 20);
+        }
       }
       __syncwarp();
       Wide<L> accn;
@@ -508,7 +537,7 @@ __device__ __forceinline__ void mesh_run(const PlanView& pv, const uint64_t* __r
 // launch parameter, 4 to 16, chosen by the plan's autotuner): neighbouring
 // rows have nearby taps, so their g patches are shared in L1.  Each warp's tap
 // table lives in dynamic shared memory.
-template <int N, int L, bool FAST>
+template <int N, int L, bool FAST, bool DBG = false>
 __device__ __forceinline__ void mesh_exact_body(const PlanView& pv, const uint64_t* __restrict__ g,
                                                 const float4* __restrict__ scales, size_t scale_pitch,
                                                 void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num,
@@ -533,25 +562,26 @@ __device__ __forceinline__ void mesh_exact_body(const PlanView& pv, const uint64
   const int y = band * rows + (threadIdx.x >> 5);
   if (y >= pv.H) return;
   const int x0 = (blockIdx.x - band * segs) * 32;
-  mesh_run<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
+  mesh_run<N, L, FAST, DBG>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status, y, x0,
                        s_tap + (threadIdx.x >> 5) * TAPS, s_dx, s_dy, s_order, s_off, s_perm);
 }
 
 // Orders 1, 2: CTAs of up to 16 rows, the compiler's register choice for
 // 512-thread blocks.  Order 3: up to 8 rows, three CTAs per SM (85 registers
 // for its wide accumulators).
-template <int N, int L, bool FAST>
+// DBG: the bounds-checked variant (plans with ABF_FLAG_DEBUG_BOUNDS).
+template <int N, int L, bool FAST, bool DBG>
 __global__ void __launch_bounds__(32 * kMeshWarpsMax) mesh_exact_kernel(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
-  mesh_exact_body<N, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status);
+  mesh_exact_body<N, L, FAST, DBG>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status);
 }
 
-template <int L, bool FAST>
+template <int L, bool FAST, bool DBG>
 __global__ void __launch_bounds__(32 * mesh_max_warps(3), mesh_min_ctas(3)) mesh_exact_kernel3(
     const PlanView pv, const uint64_t* __restrict__ g, const float4* __restrict__ scales, size_t scale_pitch,
     void* __restrict__ s, size_t s_pitch, uint64_t* __restrict__ num, size_t num_pitch, int32_t* status) {
-  mesh_exact_body<3, L, FAST>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status);
+  mesh_exact_body<3, L, FAST, DBG>(pv, g, scales, scale_pitch, s, s_pitch, num, num_pitch, status);
 }
 
 // ------------------------------------------------------------------- batches
@@ -788,9 +818,16 @@ static cudaError_t launch_mesh_NL(const PlanView& pv, const uint64_t* g, const v
     kernel<<<grid, block, smem, st>>>(pv, g, (const float4*)scales, scale_pitch, s, s_pitch, num, num_pitch, status);
     return cudaGetLastError();
   };
-  if constexpr (N == 3) return fast ? go(mesh_exact_kernel3<L, true>) : go(mesh_exact_kernel3<L, false>);
-  else if constexpr (N == 2) return fast ? go(mesh_exact_kernel<N, L, true>) : go(mesh_exact_kernel<N, L, false>);
-  else return go(mesh_exact_kernel<N, L, false>);
+  if (pv.dbg) {
+    if constexpr (N == 3) return fast ? go(mesh_exact_kernel3<L, true, true>) : go(mesh_exact_kernel3<L, false, true>);
+    else if constexpr (N == 2)
+      return fast ? go(mesh_exact_kernel<N, L, true, true>) : go(mesh_exact_kernel<N, L, false, true>);
+    else return go(mesh_exact_kernel<N, L, false, true>);
+  }
+  if constexpr (N == 3) return fast ? go(mesh_exact_kernel3<L, true, false>) : go(mesh_exact_kernel3<L, false, false>);
+  else if constexpr (N == 2)
+    return fast ? go(mesh_exact_kernel<N, L, true, false>) : go(mesh_exact_kernel<N, L, false, false>);
+  else return go(mesh_exact_kernel<N, L, false, false>);
 }
 
 template <int N>

@@ -506,6 +506,16 @@ const char* abf_status_str(abf_status s) {
   return "unknown status";
 }
 
+// ABF_FLAG_DEBUG_BOUNDS: the word that records the first pixel whose taps
+// would read outside the lattice box (the mesh kernels check when pv.dbg is set).
+static abf_status attach_debug_word(abf_plan p) {
+  if (!(p->desc.flags & ABF_FLAG_DEBUG_BOUNDS)) return ABF_OK;
+  if (cudaMalloc(&p->d_dbg, sizeof(unsigned long long)) != cudaSuccess) return ABF_ERR_OOM;
+  if (cudaMemset(p->d_dbg, 0, sizeof(unsigned long long)) != cudaSuccess) return ABF_ERR_CUDA;
+  p->pv.dbg = (unsigned long long*)p->d_dbg;
+  return ABF_OK;
+}
+
 abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (!d || !out) return ABF_ERR_INVALID;
   *out = nullptr;
@@ -540,6 +550,8 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (d->model_boxes < 0 || d->model_boxes > 6) return ABF_ERR_INVALID;
   const bool general = d->directions == 2 || d->model_boxes > 0;
   if (general && !exact) return ABF_ERR_UNSUPPORTED;
+  if (d->flags & ~ABF_FLAG_DEBUG_BOUNDS) return ABF_ERR_INVALID;
+  if ((d->flags & ABF_FLAG_DEBUG_BOUNDS) && !exact) return ABF_ERR_UNSUPPORTED;  // checks are in the exact mesh
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ABF_ERR_CUDA;
 
@@ -551,9 +563,11 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
     abf_status gs = abf::create_general_plan(d, p);
     if (gs == ABF_OK && cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) gs = ABF_ERR_OOM;
     if (gs == ABF_OK && cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) gs = ABF_ERR_CUDA;
+    if (gs == ABF_OK) gs = attach_debug_word(p);
     if (gs != ABF_OK) {
       abf::destroy_general_plan(p);
       if (p->d_status) cudaFree(p->d_status);
+      if (p->d_dbg) cudaFree(p->d_dbg);
       delete p;
       return gs;
     }
@@ -618,6 +632,12 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
     delete p;
     return ABF_ERR_CUDA;
   }
+  const abf_status ds = attach_debug_word(p);
+  if (ds != ABF_OK) {
+    cudaFree(p->d_status);
+    delete p;
+    return ds;
+  }
   *out = p;
   return ABF_OK;
 }
@@ -626,7 +646,17 @@ abf_status abf_plan_destroy(abf_plan p) {
   if (!p) return ABF_ERR_INVALID;
   if (p->general) abf::destroy_general_plan(p);
   if (p->d_status) cudaFree(p->d_status);
+  if (p->d_dbg) cudaFree(p->d_dbg);
   delete p;
+  return ABF_OK;
+}
+
+abf_status abf_debug_bounds_violation(abf_plan p, int64_t* pixel) {
+  if (!p || !pixel || !p->d_dbg) return ABF_ERR_INVALID;
+  unsigned long long v = 0;
+  if (cudaMemcpy(&v, p->d_dbg, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return ABF_ERR_CUDA;
+  if (cudaMemset(p->d_dbg, 0, sizeof(v)) != cudaSuccess) return ABF_ERR_CUDA;
+  *pixel = v ? (int64_t)(v - 1) : -1;
   return ABF_OK;
 }
 

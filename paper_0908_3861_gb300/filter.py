@@ -14,7 +14,9 @@ class AdaptiveFilter:
 
     def __init__(self, width, height, n, in_dtype, scale_kind="c4", q_bits=8, frac_bits=0, max_scale=8.0,
                  out="f64", form="exact", min_scale=0.0, value_bound=0.0, max_scale_product=0.0, device=None,
-                 directions=4, model_boxes=0):
+                 directions=4, model_boxes=0, debug_bounds=False):
+        """debug_bounds: check every tap's reads against the lattice box
+        (ABF_FLAG_DEBUG_BOUNDS; see bounds_violation)."""
         self.device = torch.device(device or "cuda")
         self.W, self.H, self.n = int(width), int(height), int(n)
         self.in_dtype = in_dtype
@@ -27,7 +29,7 @@ class AdaptiveFilter:
         d.scale_kind = C.SCALE_KINDS[scale_kind]
         d.q_bits = int(q_bits)
         d.in_frac_bits = int(frac_bits)
-        d.flags = 0
+        d.flags = C.ABF_FLAG_DEBUG_BOUNDS if debug_bounds else 0
         d.max_scale = float(max_scale)
         d.min_scale = float(min_scale)
         d.value_bound = float(value_bound)
@@ -120,6 +122,11 @@ class AdaptiveFilter:
 
     def device_status(self):
         return C.abf_last_device_status(self.plan)
+
+    def bounds_violation(self):
+        """First pixel index (y W + x) whose taps would have left the lattice
+        box, or -1; only for filters created with debug_bounds=True."""
+        return C.abf_debug_bounds_violation(self.plan)
 
 
 class Batch:

@@ -20,7 +20,7 @@ def to_device(arr, dev):
     return torch.from_numpy(np.ascontiguousarray(arr)).to(dev)
 
 
-def run_exact(w, dev="cuda:0", out="f64", max_scale_product=0.0, want=("s", "num", "C")):
+def run_exact(w, dev="cuda:0", out="f64", max_scale_product=0.0, want=("s", "num", "C"), debug_bounds=False):
     """Run abf_integrate + abf_filter (+ numerators, prepared scales) for a
     workload dict; returns numpy results and the filter object."""
     import torch
@@ -30,7 +30,7 @@ def run_exact(w, dev="cuda:0", out="f64", max_scale_product=0.0, want=("s", "num
     filt = AdaptiveFilter(W, H, w["n"], torch_dtype(img.dtype), scale_kind=w["scale_kind"], q_bits=w["q_bits"],
                           frac_bits=w["frac_bits"], max_scale=w["cmax"], out=out,
                           value_bound=w.get("value_bound", 0.0), max_scale_product=max_scale_product,
-                          min_scale=w.get("min_scale", 0.0), device=dev)
+                          min_scale=w.get("min_scale", 0.0), device=dev, debug_bounds=debug_bounds)
     f_t = to_device(img, dev)
     s_t = to_device(sc.astype(np.float32), dev)
     res = {}

@@ -309,3 +309,47 @@ def test_lookback_wait_times_out_then_the_context_recovers():
     res = gu.run_exact(w)
     assert res["status"] == 0
     _check_all_pixels(w, res)
+
+
+@pytest.mark.parametrize("n,shape,q,dtype,seed,lo", [c + (1.0,) for c in CASES] +
+                         [(1, (37, 70), 4, "u8", 11, 6.0), (2, (37, 70), 4, "f32", 12, 6.0),
+                          (3, (18, 70), 2, "f32", 13, 6.0)])
+def test_debug_bounds_checks_find_no_violation(n, shape, q, dtype, seed, lo):
+    """With ABF_FLAG_DEBUG_BOUNDS every tap of every pixel is checked against
+    the lattice box before it is read: the box the plan sizes from the taps'
+    reach holds at every pixel (also with every step at the plan's maximum,
+    lo = 6), and the checked plan gives the unchecked plan's numerators."""
+    w = _small_workload(n, shape, q, dtype, seed, lo=lo, hi=6.0)
+    a = gu.run_exact(w, want=("s", "num"))
+    b = gu.run_exact(w, want=("s", "num"), debug_bounds=True)
+    assert a["status"] == 0 and b["status"] == 0
+    assert b["filt"].bounds_violation() == -1
+    assert np.array_equal(a["num"], b["num"])
+    assert np.array_equal(a["s"], b["s"])
+
+
+def test_debug_bounds_full_size_2048_order2_ellipse():
+    """The bench workload (2048^2, order 2, ellipse fields, the plan sized for
+    the parameter range) with every tap checked: no pixel reads outside the
+    lattice box, and the output equals the unchecked plan's bit for bit."""
+    import torch
+    from paper_0908_3861_gb300 import AdaptiveFilter, ellipse_product_bound
+    w = synthetic.workload("c2")
+    img, sc = w["image"], w["scales"]
+    H, W = img.shape
+    dev = "cuda:0"
+    prod = ellipse_product_bound(w["sigma_max"], w["e_max"], 2, w["q_bits"], w["cmax"], device=dev)
+    outs = []
+    for dbg in (False, True):
+        f = AdaptiveFilter(W, H, 2, torch.float32, scale_kind="ellipse", q_bits=w["q_bits"],
+                           frac_bits=w["frac_bits"], max_scale=w["cmax"], out="f64",
+                           value_bound=w["value_bound"], max_scale_product=prod, device=dev, debug_bounds=dbg)
+        f.integrate(gu.to_device(img, dev))
+        outs.append(f.filter(gu.to_device(sc.astype(np.float32), dev)).cpu().numpy())
+        torch.cuda.synchronize()
+        assert f.device_status() == 0
+        if dbg:
+            assert f.bounds_violation() == -1
+        f.close()
+    assert np.array_equal(outs[0], outs[1])
+

@@ -33,13 +33,13 @@ def _steps(rng, shape, lo, hi, directions):
     return sc
 
 
-def _run(img, sc, n, q, F, cmax, directions, E, vb, want_num=True):
+def _run(img, sc, n, q, F, cmax, directions, E, vb, want_num=True, debug_bounds=False):
     import torch
     from paper_0908_3861_gb300 import AdaptiveFilter
     H, W = img.shape
     filt = AdaptiveFilter(W, H, n, gu.torch_dtype(img.dtype), scale_kind="c4", q_bits=q, frac_bits=F,
                           max_scale=cmax, out="f64", value_bound=vb, device="cuda:0", directions=directions,
-                          model_boxes=E)
+                          model_boxes=E, debug_bounds=debug_bounds)
     filt.integrate(gu.to_device(img, "cuda:0"))
     s_t = gu.to_device(sc, "cuda:0")
     s = filt.filter(s_t).cpu().numpy()
@@ -47,6 +47,8 @@ def _run(img, sc, n, q, F, cmax, directions, E, vb, want_num=True):
     torch.cuda.synchronize()
     st = filt.device_status()
     L = filt.limbs
+    if debug_bounds:
+        assert filt.bounds_violation() == -1
     filt.close()
     return s, num, st, L
 
@@ -128,3 +130,25 @@ def test_model_with_prefilter(directions, n, E, shape):
     sd = general.filter_direct(cx, ox, C, r, n1, q, 20, few)
     for (x, y), v in zip(few, sd):
         assert abs(Fr(s[y, x]) - v) <= Fr(1, 2) + Fr(1, 1 << 18)
+
+
+@pytest.mark.parametrize("directions,n,E,shape", [(2, 2, 0, (37, 70)), (2, 3, 0, (21, 45)), (4, 1, 2, (26, 40)),
+                                                  (4, 1, 4, (23, 39)), (4, 1, 6, (9, 35))])
+def test_general_debug_bounds_checks_find_no_violation(directions, n, E, shape):
+    """Generalised plans with every read checked against the lattice box (the
+    group kernels, the N = 2 unrolled taps, the pair-dealt kernel): steps at
+    the plan's maximum somewhere, no violation, and the unchecked plan's
+    numerators."""
+    rng = np.random.default_rng(120 + n + E)
+    img = rng.integers(0, 256, shape).astype(np.uint8)
+    sc = _steps(rng, shape, 1.0, 4.0, directions)
+    sc[0, 0, :] = 4.0      # the widest reach at two corners
+    sc[-1, -1, :] = 4.0
+    if directions == 2:
+        sc[..., 1] = sc[..., 3] = 1.0
+    a = _run(img, sc, n, 2, 0, 4.0, directions, E, 255.0)
+    b = _run(img, sc, n, 2, 0, 4.0, directions, E, 255.0, debug_bounds=True)
+    assert a[2] == 0 and b[2] == 0
+    assert np.array_equal(a[1], b[1])
+    assert np.array_equal(a[0], b[0])
+
