@@ -418,6 +418,28 @@ abf_status abf_last_device_status(abf_plan plan, int32_t* code);
 #define ABF_FLAG_DEBUG_BOUNDS 1
 abf_status abf_debug_bounds_violation(abf_plan plan, int64_t* pixel);
 
+/* Host-side fault injection (no counterpart in the paper; failure detection
+ * is tested without faulting a GPU).  Arms `count` faults of one kind,
+ * process-wide; count = 0 disarms it.
+ *   ABF_FAULT_ALLOC       the next `count` device allocations of plan
+ *                         creation (abf_plan_create: ABF_ERR_OOM, nothing
+ *                         leaked) and of server jobs (the job ends with
+ *                         ABF_ERR_OOM) fail;
+ *   ABF_FAULT_QUEUE_STALL while armed the server admits no queued job (as if
+ *                         their publication were withheld): abf_wait runs
+ *                         into its timeout; disarming lets the jobs run;
+ *   ABF_FAULT_BAD_DESC    the next `count` abf_plan_create calls (also those a
+ *                         server makes for its jobs) see an invalid
+ *                         descriptor: ABF_ERR_INVALID.
+ * The environment variable ABF_FAULT (read once, at the library's first
+ * plan or server call) arms the same: a comma-separated list of
+ * kind[:count] with kind alloc, queue_stall or bad_desc (count 1 if omitted).
+ * Returns ABF_ERR_INVALID for an unknown kind or a negative count.          */
+#define ABF_FAULT_ALLOC        1
+#define ABF_FAULT_QUEUE_STALL  2
+#define ABF_FAULT_BAD_DESC     3
+abf_status abf_debug_inject_fault(int32_t kind, int32_t count);
+
 const char* abf_status_str(abf_status s);
 
 /* Host-only: generate the ZP^{*n} weight table (the interpolation kernel of

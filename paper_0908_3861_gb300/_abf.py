@@ -21,6 +21,7 @@ ABF_SCALES_C4, ABF_SCALES_A4, ABF_SCALES_ELLIPSE = 0, 1, 2
 ABF_DEV_BAD_SCALE, ABF_DEV_RANGE, ABF_DEV_TIMEOUT, ABF_DEV_BAD_INPUT, ABF_DEV_PRECISION = 1, 2, 4, 8, 16
 ABF_DEV_BOUNDS = 32
 ABF_FLAG_DEBUG_BOUNDS = 1
+ABF_FAULT_ALLOC, ABF_FAULT_QUEUE_STALL, ABF_FAULT_BAD_DESC = 1, 2, 3
 
 SCALE_KINDS = {"c4": ABF_SCALES_C4, "a4": ABF_SCALES_A4, "ellipse": ABF_SCALES_ELLIPSE}
 FORMS = {"exact": ABF_FORM_EXACT, "plain_f64": ABF_FORM_PLAIN_F64, "tile_f32": ABF_FORM_TILE_F32}
@@ -95,6 +96,7 @@ def signatures():
         "abf_plan_denominator": ([vp, P(ctypes.c_uint32)], st),
         "abf_last_device_status": ([vp, P(i32)], st),
         "abf_debug_bounds_violation": ([vp, P(ctypes.c_int64)], st),
+        "abf_debug_inject_fault": ([i32, i32], st),
         "abf_measure_scales": ([P(abf_desc), vp, sz, P(ctypes.c_double), P(ctypes.c_double), vp], st),
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
@@ -233,6 +235,12 @@ def abf_debug_bounds_violation(plan):
     v = ctypes.c_int64()
     _check(lib().abf_debug_bounds_violation(plan, ctypes.byref(v)), "abf_debug_bounds_violation")
     return v.value
+
+
+def abf_debug_inject_fault(kind, count):
+    """Arm (count > 0) or disarm (0) a host-side fault: ABF_FAULT_ALLOC,
+    ABF_FAULT_QUEUE_STALL or ABF_FAULT_BAD_DESC."""
+    _check(lib().abf_debug_inject_fault(int(kind), int(count)), "abf_debug_inject_fault")
 
 
 def abf_measure_scales(desc, scales, scale_pitch, stream=None):

@@ -835,6 +835,10 @@ struct PrefilterView {
   long long bound;               // floor(value_bound 2^F)
 };
 abf_status prefilter2d_setup(int n1, double xmax, PrefilterView* pf, double* hnorm, int* tail);
+// Host-side fault injection (abf_debug_inject_fault, ABF_FAULT): take one
+// armed fault of a kind (true if one was armed), or test whether a kind is armed.
+bool fault_take(int kind);
+bool fault_active(int kind);
 cudaError_t run_prefilter_rows_raw(const PrefilterView& v, int count, int in_dtype, const void* f, size_t f_pitch,
                                    long long* c, long long c_pitch, int32_t* status, cudaStream_t st);
 

@@ -18,6 +18,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -27,6 +28,51 @@
 #include <vector>
 
 #include "abf_internal.cuh"
+
+// ------------------------------------------------------- fault injection
+
+namespace {
+std::atomic<int> g_fault[4];
+std::once_flag g_fault_env;
+
+// ABF_FAULT = kind[:count][,kind[:count]...]
+void fault_env() {
+  const char* e = std::getenv("ABF_FAULT");
+  if (!e) return;
+  std::string v(e);
+  size_t pos = 0;
+  while (pos <= v.size()) {
+    size_t end = v.find(',', pos);
+    if (end == std::string::npos) end = v.size();
+    std::string item = v.substr(pos, end - pos);
+    int count = 1;
+    const size_t colon = item.find(':');
+    if (colon != std::string::npos) {
+      count = std::atoi(item.c_str() + colon + 1);
+      item = item.substr(0, colon);
+    }
+    int kind = item == "alloc" ? ABF_FAULT_ALLOC : item == "queue_stall" ? ABF_FAULT_QUEUE_STALL
+                                                : item == "bad_desc" ? ABF_FAULT_BAD_DESC : 0;
+    if (kind && count >= 0) g_fault[kind].store(count);
+    pos = end + 1;
+  }
+}
+}  // namespace
+
+namespace abf {
+bool fault_take(int kind) {
+  std::call_once(g_fault_env, fault_env);
+  int v = g_fault[kind].load();
+  while (v > 0)
+    if (g_fault[kind].compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+bool fault_active(int kind) {
+  std::call_once(g_fault_env, fault_env);
+  return g_fault[kind].load() > 0;
+}
+}  // namespace abf
+
 
 namespace abf {
 cudaError_t run_integrate(const PlanView& pv, const void* f, size_t f_pitch, uint64_t* g, void* ws,
@@ -506,6 +552,13 @@ const char* abf_status_str(abf_status s) {
   return "unknown status";
 }
 
+abf_status abf_debug_inject_fault(int32_t kind, int32_t count) {
+  if (kind < ABF_FAULT_ALLOC || kind > ABF_FAULT_BAD_DESC || count < 0) return ABF_ERR_INVALID;
+  std::call_once(g_fault_env, fault_env);
+  g_fault[kind].store(count);
+  return ABF_OK;
+}
+
 // ABF_FLAG_DEBUG_BOUNDS: the word that records the first pixel whose taps
 // would read outside the lattice box (the mesh kernels check when pv.dbg is set).
 static abf_status attach_debug_word(abf_plan p) {
@@ -519,6 +572,7 @@ static abf_status attach_debug_word(abf_plan p) {
 abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   if (!d || !out) return ABF_ERR_INVALID;
   *out = nullptr;
+  if (abf::fault_take(ABF_FAULT_BAD_DESC)) return ABF_ERR_INVALID;
   const int n = d->order_n;
   if (d->width < 1 || d->height < 1 || n < 1 || n > 3) return ABF_ERR_INVALID;
   if (d->in_dtype < ABF_U8 || d->in_dtype > ABF_F64) return ABF_ERR_INVALID;
@@ -561,7 +615,8 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
   p->device = dev;
   if (general) {
     abf_status gs = abf::create_general_plan(d, p);
-    if (gs == ABF_OK && cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) gs = ABF_ERR_OOM;
+    if (gs == ABF_OK && (abf::fault_take(ABF_FAULT_ALLOC) || cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess))
+      gs = ABF_ERR_OOM;
     if (gs == ABF_OK && cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) gs = ABF_ERR_CUDA;
     if (gs == ABF_OK) gs = attach_debug_word(p);
     if (gs != ABF_OK) {
@@ -626,7 +681,10 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
     p->g_bytes = 0;
     p->ws_bytes = abf::tile_ws_bytes(pv, 2 * rb, &slots, &se, &o1, &o2, &o3, &o4);
   }
-  if (cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) { delete p; return ABF_ERR_OOM; }
+  if (abf::fault_take(ABF_FAULT_ALLOC) || cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) {
+    delete p;
+    return ABF_ERR_OOM;
+  }
   if (cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
     cudaFree(p->d_status);
     delete p;

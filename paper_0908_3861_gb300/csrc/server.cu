@@ -171,7 +171,7 @@ struct abf_server_s {
     ok(cudaEventCreate(&j->ev0));
     if (e == cudaSuccess) ok(cudaEventRecord(j->ev0, st));
     ok(cudaMemsetAsync(dst, 0, sizeof(int32_t), st));
-    ok(cudaMallocAsync(&j->d_sc, sb, st));
+    ok(abf::fault_take(ABF_FAULT_ALLOC) ? cudaErrorMemoryAllocation : cudaMallocAsync(&j->d_sc, sb, st));
     ok(cudaMallocAsync(&j->d_s, ob, st));
     if (e == cudaSuccess)
       ok(cudaMemcpy2DAsync(j->d_sc, (size_t)W * 16, j->req.h_scales, j->req.scale_pitch, (size_t)W * 16, H,
@@ -198,7 +198,7 @@ struct abf_server_s {
       if (e == cudaSuccess) ok(cudaEventRecord(j->ev_ready, st));
       if (e != cudaSuccess) {
         cudaGetLastError();
-        complete(j, ABF_ERR_CUDA);
+        complete(j, e == cudaErrorMemoryAllocation ? ABF_ERR_OOM : ABF_ERR_CUDA);
         return true;
       }
       *started = true;
@@ -229,7 +229,7 @@ struct abf_server_s {
     if (e == cudaSuccess) ok(cudaEventRecord(j->ev, st));
     if (e != cudaSuccess) {
       cudaGetLastError();
-      complete(j, ABF_ERR_CUDA);
+      complete(j, e == cudaErrorMemoryAllocation ? ABF_ERR_OOM : ABF_ERR_CUDA);
     }
   }
 
@@ -354,7 +354,7 @@ struct abf_server_s {
       // admissions, in arrival order; a job that does not fit lets later ones
       // try.  With grouping on, the jobs admitted in one round share one
       // batched launch of the adaptive step.
-      if (!paused) {
+      if (!paused && !abf::fault_active(ABF_FAULT_QUEUE_STALL)) {
         const bool grouping = (cfg.flags & ABF_SERVER_GROUP_MESH) != 0;
         std::vector<Job*> grp;
         for (auto it = queue.begin(); it != queue.end();) {

@@ -31,6 +31,18 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_fault_injection_arguments(lib):
+    """abf_debug_inject_fault takes the three kinds and a count >= 0 (host
+    only: arming and disarming touch no device)."""
+    from paper_0908_3861_gb300 import _abf
+    assert lib.abf_debug_inject_fault(0, 1) == _abf.ABF_ERR_INVALID
+    assert lib.abf_debug_inject_fault(4, 1) == _abf.ABF_ERR_INVALID
+    assert lib.abf_debug_inject_fault(_abf.ABF_FAULT_ALLOC, -1) == _abf.ABF_ERR_INVALID
+    for k in (_abf.ABF_FAULT_ALLOC, _abf.ABF_FAULT_QUEUE_STALL, _abf.ABF_FAULT_BAD_DESC):
+        assert lib.abf_debug_inject_fault(k, 3) == _abf.ABF_OK
+        assert lib.abf_debug_inject_fault(k, 0) == _abf.ABF_OK
+
+
 def test_status_strings(lib):
     from paper_0908_3861_gb300 import _abf
     assert _abf.abf_status_str(0) == "ok"

@@ -353,3 +353,36 @@ def test_debug_bounds_full_size_2048_order2_ellipse():
         f.close()
     assert np.array_equal(outs[0], outs[1])
 
+
+
+@pytest.mark.parametrize("n,shape,dtype", [(1, (300, 257), "u8"), (2, (257, 300), "f32"), (3, (130, 140), "u16")])
+def test_repeated_runs_are_bit_identical(n, shape, dtype):
+    """Race check without a sanitizer: ten integrate + filter runs of the same
+    plan on the same input (several bands per line pass, so the look-back
+    chains race each time) give bit-identical integrated images and
+    numerators; the first run's numerators also equal the oracle's at
+    sampled pixels."""
+    import torch
+    w = _small_workload(n, shape, 4 if n < 3 else 2, dtype, 90 + n)
+    res = gu.run_exact(w, want=("num", "g"))
+    filt = res["filt"]
+    f_t = gu.to_device(w["image"], "cuda:0")
+    s_t = gu.to_device(w["scales"].astype(np.float32), "cuda:0")
+    for _ in range(9):
+        filt.integrate(f_t)
+        g = filt.integrated().cpu().numpy().astype(np.uint64)
+        num = filt.numerators(s_t).cpu().numpy().astype(np.uint64)
+        torch.cuda.synchronize()
+        assert np.array_equal(g, res["g"])
+        assert np.array_equal(num, res["num"])
+    assert filt.device_status() == 0
+    rng = np.random.default_rng(7)
+    H, W = shape
+    pix = [(int(rng.integers(0, W)), int(rng.integers(0, H))) for _ in range(24)]
+    C_ref = gu.oracle_C(w)
+    S_ref, _ = paper.filter_pixels(gu.f_int(w), C_ref, n, w["q_bits"], w["frac_bits"], pix)
+    L = res["limbs"]
+    mod = 1 << (64 * L)
+    got = gu.wide_to_int(res["num"], L)
+    for (x, y), S in zip(pix, S_ref):
+        assert got[y * W + x] == int(S) % mod, (x, y)
