@@ -288,11 +288,18 @@ int32_t abf_batch_max_jobs(void);
  * (n, limbs, width, height) of its images; used by later abf_filter_batch
  * calls on batches of that composition).  Outputs are written as by
  * abf_filter / abf_filter_batch.  *warps_out = the choice; ms3 (optional):
- * the three times in ms.                                                     */
+ * the three times in ms.  Choices are also kept process-wide by key (GPU
+ * name, order, limbs, size, Q and scale kind for a plan; GPU name and the
+ * composition for a batch) and, when the environment variable
+ * ABF_TUNE_CACHE names a file, in that file (a flat JSON object
+ * {"key": rows}, read at the first lookup, rewritten after every tuning):
+ * abf_plan_create starts an exact plan from a kept choice for its key.
+ * abf_plan_rows reports a plan's current rows per CTA.                      */
 abf_status abf_plan_autotune(abf_plan plan, const void* d_g, const void* d_scales, size_t scale_pitch, void* d_s,
                              size_t s_pitch, cudaStream_t stream, int32_t* warps_out, float* ms3);
 abf_status abf_batch_autotune(const abf_job* jobs, int32_t njobs, void* d_ws, size_t ws_bytes, cudaStream_t stream,
                               int32_t* warps_out, float* ms3);
+abf_status abf_plan_rows(abf_plan plan, int32_t* rows);
 
 /* ------------------------------------------------------------------ serving
  * No counterpart in the paper: a serving interface around its two steps

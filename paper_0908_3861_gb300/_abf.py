@@ -97,6 +97,7 @@ def signatures():
         "abf_last_device_status": ([vp, P(i32)], st),
         "abf_debug_bounds_violation": ([vp, P(ctypes.c_int64)], st),
         "abf_debug_inject_fault": ([i32, i32], st),
+        "abf_plan_rows": ([vp, P(i32)], st),
         "abf_measure_scales": ([P(abf_desc), vp, sz, P(ctypes.c_double), P(ctypes.c_double), vp], st),
         "abf_weight_table_host": ([i32, i32, vp, sz, P(sz), P(i32), P(ctypes.c_uint32)], st),
         "abf_filter_batch": ([P(abf_job), i32, vp, sz, vp], st),
@@ -235,6 +236,13 @@ def abf_debug_bounds_violation(plan):
     v = ctypes.c_int64()
     _check(lib().abf_debug_bounds_violation(plan, ctypes.byref(v)), "abf_debug_bounds_violation")
     return v.value
+
+
+def abf_plan_rows(plan):
+    """Rows (warps) per CTA the plan's adaptive step launches with."""
+    r = ctypes.c_int32()
+    _check(lib().abf_plan_rows(plan, ctypes.byref(r)), "abf_plan_rows")
+    return r.value
 
 
 def abf_debug_inject_fault(kind, count):

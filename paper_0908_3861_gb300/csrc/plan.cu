@@ -15,6 +15,7 @@
 // of one fractional offset) sums to D exactly (partition of unity); the
 // generator checks that too.
 #include <algorithm>
+#include <cctype>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -534,6 +535,10 @@ abf_status abf::filter_with_status(abf_plan p, const void* d_g, const void* d_sc
 
 
 
+// The tuning cache (defined with the autotuner below).
+static int tune_lookup(const std::string& key, int dflt);
+static std::string plan_tune_key(abf_plan p);
+
 extern "C" {
 
 int32_t abf_version(void) { return 1; }
@@ -696,6 +701,7 @@ abf_status abf_plan_create(const abf_desc* d, abf_plan* out) {
     delete p;
     return ds;
   }
+  if (exact) p->mesh_warps = tune_lookup(plan_tune_key(p), p->mesh_warps);  // a tuning kept from earlier runs
   *out = p;
   return ABF_OK;
 }
@@ -801,10 +807,122 @@ int32_t abf_batch_max_jobs(void) { return abf::batch_max_jobs(); }
 
 }  // extern "C"
 
-// Batch tuning cache: the rows per CTA chosen for a batch composition (the
-// sorted (n, limbs, width, height) of its images), process-wide.
+// Tuning cache: the rows per CTA chosen for a plan (key "plan:<GPU>:n,L,W,H,Q,
+// scale kind") or a batch composition (key "batch:<GPU>:" + the sorted (n,
+// limbs, width, height) of its images), process-wide and, when the
+// environment variable ABF_TUNE_CACHE names a file, kept there as a flat JSON
+// object {"key": rows, ...}: read at the first lookup, rewritten (through a
+// temporary file and a rename) after every tuning.  A file that does not parse
+// is ignored.
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_batch_tuned;
+static std::map<std::string, int> g_tuned;
+static bool g_tune_loaded = false;
+
+static std::string gpu_name() {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n(prop.name);
+  for (char& c : n)
+    if (c == '"' || c == '\\' || c == ':') c = '_';
+  return n;
+}
+
+// Parses {"key": int, ...}; false (and nothing taken) on any other content.
+static bool parse_tune_json(const std::string& t, std::map<std::string, int>& out) {
+  std::map<std::string, int> m;
+  size_t i = 0;
+  auto ws = [&] { while (i < t.size() && std::isspace((unsigned char)t[i])) ++i; };
+  ws();
+  if (i >= t.size() || t[i] != '{') return false;
+  ++i;
+  ws();
+  if (i < t.size() && t[i] == '}') { out.swap(m); return true; }
+  for (;;) {
+    ws();
+    if (i >= t.size() || t[i] != '"') return false;
+    const size_t k0 = ++i;
+    while (i < t.size() && t[i] != '"') ++i;
+    if (i >= t.size()) return false;
+    const std::string key = t.substr(k0, i - k0);
+    ++i;
+    ws();
+    if (i >= t.size() || t[i] != ':') return false;
+    ++i;
+    ws();
+    const size_t v0 = i;
+    while (i < t.size() && std::isdigit((unsigned char)t[i])) ++i;
+    if (i == v0 || i - v0 > 6) return false;
+    m[key] = std::atoi(t.substr(v0, i - v0).c_str());
+    ws();
+    if (i < t.size() && t[i] == ',') { ++i; continue; }
+    if (i < t.size() && t[i] == '}') break;
+    return false;
+  }
+  out.swap(m);
+  return true;
+}
+
+// Call with g_tune_mu held.
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("ABF_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return;
+  std::string t;
+  char buf[4096];
+  size_t k;
+  while ((k = std::fread(buf, 1, sizeof buf, f)) > 0 && t.size() < (1u << 20)) t.append(buf, k);
+  std::fclose(f);
+  std::map<std::string, int> m;
+  if (parse_tune_json(t, m))
+    for (auto& kv : m)
+      if (kv.second == 4 || kv.second == 8 || kv.second == 16) g_tuned[kv.first] = kv.second;
+}
+
+static void tune_save_locked() {
+  const char* path = std::getenv("ABF_TUNE_CACHE");
+  if (!path || !*path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  std::fputs("{", f);
+  bool first = true;
+  for (auto& kv : g_tuned) {
+    std::fprintf(f, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+    first = false;
+  }
+  std::fputs("\n}\n", f);
+  const bool ok = std::fclose(f) == 0;
+  if (ok) std::rename(tmp.c_str(), path);
+  else std::remove(tmp.c_str());
+}
+
+static int tune_lookup(const std::string& key, int dflt) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tuned.find(key);
+  return it != g_tuned.end() ? it->second : dflt;
+}
+
+static void tune_store(const std::string& key, int rows) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  g_tuned[key] = rows;
+  tune_save_locked();
+}
+
+static std::string plan_tune_key(abf_plan p) {
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "plan:%s:%d,%d,%d,%d,%d,%d", gpu_name().c_str(), p->pv.n, p->pv.limbs, p->pv.W,
+                p->pv.H, p->pv.Q, p->pv.scale_kind);
+  return buf;
+}
 
 static abf_status batch_inputs(const abf_job* jobs, int32_t njobs, std::vector<abf::BatchIn>& in, std::string* key) {
   in.resize((size_t)njobs);
@@ -822,7 +940,7 @@ static abf_status batch_inputs(const abf_job* jobs, int32_t njobs, std::vector<a
   }
   if (key) {
     std::sort(sig.begin(), sig.end());
-    key->clear();
+    *key = "batch:" + gpu_name() + ":";
     for (auto& t : sig) {
       char buf[64];
       std::snprintf(buf, sizeof buf, "%d.%d.%d.%d;", std::get<0>(t), std::get<1>(t), std::get<2>(t), std::get<3>(t));
@@ -946,12 +1064,7 @@ abf_status abf_filter_batch(const abf_job* jobs, int32_t njobs, void* d_ws, size
   std::string key;
   abf_status s = batch_inputs(jobs, njobs, in, &key);
   if (s != ABF_OK) return s;
-  int warps = 8;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_batch_tuned.find(key);
-    if (it != g_batch_tuned.end()) warps = it->second;
-  }
+  const int warps = tune_lookup(key, 8);
   return batch_launch(in, d_ws, warps, st) == cudaSuccess ? ABF_OK : ABF_ERR_CUDA;
 }
 
@@ -971,7 +1084,14 @@ abf_status abf_plan_autotune(abf_plan p, const void* d_g, const void* d_scales, 
       st, &best, ms3);
   if (s != ABF_OK) return s;
   p->mesh_warps = best;
+  tune_store(plan_tune_key(p), best);
   if (warps_out) *warps_out = best;
+  return ABF_OK;
+}
+
+abf_status abf_plan_rows(abf_plan p, int32_t* rows) {
+  if (!p || !rows) return ABF_ERR_INVALID;
+  *rows = p->mesh_warps;
   return ABF_OK;
 }
 
@@ -985,10 +1105,7 @@ abf_status abf_batch_autotune(const abf_job* jobs, int32_t njobs, void* d_ws, si
   int best = 8;
   s = tune_warps([&](int w) { return batch_launch(in, d_ws, w, st); }, st, &best, ms3);
   if (s != ABF_OK) return s;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_batch_tuned[key] = best;
-  }
+  tune_store(key, best);
   if (warps_out) *warps_out = best;
   return ABF_OK;
 }

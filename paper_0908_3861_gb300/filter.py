@@ -123,6 +123,11 @@ class AdaptiveFilter:
     def device_status(self):
         return C.abf_last_device_status(self.plan)
 
+    def launch_rows(self):
+        """Rows (warps) per CTA of the adaptive step (8 by default; set by
+        autotune, or from a tuning kept under ABF_TUNE_CACHE)."""
+        return C.abf_plan_rows(self.plan)
+
     def bounds_violation(self):
         """First pixel index (y W + x) whose taps would have left the lattice
         box, or -1; only for filters created with debug_bounds=True."""
