@@ -386,3 +386,23 @@ def test_repeated_runs_are_bit_identical(n, shape, dtype):
     got = gu.wide_to_int(res["num"], L)
     for (x, y), S in zip(pix, S_ref):
         assert got[y * W + x] == int(S) % mod, (x, y)
+
+
+@pytest.mark.parametrize("n,q", [(1, 4), (2, 4), (3, 2)])
+def test_transpose_and_mirror_symmetries(n, q):
+    """The dihedral symmetries of v1..v4 on the device path: transposing the
+    image swaps a1 and a3, mirroring k1 swaps a2 and a4 (v2 = (1,1) mirrors to
+    (-1,1) = v4).  The numerators are exact, so they must agree bit for bit:
+    this also checks that the 3pi/4 pass' truncation at the box's right edge
+    (which the mirror moves to the 45 degree pass) does not reach them."""
+    w = _small_workload(n, (37, 53), q, "u8", 40 + n, lo=1.0, hi=5.0)
+    base = gu.run_exact(w, want=("num",))
+    img, sc = w["image"], w["scales"]
+    wt = dict(w, image=np.ascontiguousarray(img.T), scales=np.ascontiguousarray(sc.transpose(1, 0, 2)[..., [2, 1, 0, 3]]))
+    wm = dict(w, image=np.ascontiguousarray(img[:, ::-1]), scales=np.ascontiguousarray(sc[:, ::-1][..., [0, 3, 2, 1]]))
+    rt = gu.run_exact(wt, want=("num",))
+    rm = gu.run_exact(wm, want=("num",))
+    assert base["status"] == rt["status"] == rm["status"] == 0
+    assert base["limbs"] == rt["limbs"] == rm["limbs"]
+    assert np.array_equal(rt["num"], base["num"].transpose(1, 0, 2))
+    assert np.array_equal(rm["num"], base["num"][:, ::-1])
