@@ -818,16 +818,25 @@ static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tuned;
 static bool g_tune_loaded = false;
 
+// The current device's name (queried once per device: the property query is slow).
 static std::string gpu_name() {
+  static std::mutex mu;
+  static std::map<int, std::string> names;
   int dev = 0;
-  cudaDeviceProp prop{};
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return "unknown";
   }
-  std::string n(prop.name);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = names.find(dev);
+  if (it != names.end()) return it->second;
+  cudaDeviceProp prop{};
+  std::string n = "unknown";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) n = prop.name;
+  else cudaGetLastError();
   for (char& c : n)
     if (c == '"' || c == '\\' || c == ':') c = '_';
+  names[dev] = n;
   return n;
 }
 
