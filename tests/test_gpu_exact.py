@@ -406,3 +406,15 @@ def test_transpose_and_mirror_symmetries(n, q):
     assert base["limbs"] == rt["limbs"] == rm["limbs"]
     assert np.array_equal(rt["num"], base["num"].transpose(1, 0, 2))
     assert np.array_equal(rm["num"], base["num"][:, ::-1])
+
+
+@pytest.mark.parametrize("n,dtype", [(1, "u8"), (2, "f32"), (3, "u16")])
+def test_integrated_image_odd_size_several_bands(n, dtype):
+    """An odd size (257 x 129) whose lattice box spans several 64-row bands of
+    the line passes with a ragged last band, ragged groups of 32 lines and a
+    ragged last row chunk: the integrated image equals the oracle's exact
+    recursions at every cell where the GPU's is exact."""
+    w = _small_workload(n, (257, 129), 3 if n < 3 else 2, dtype, 60 + n)
+    res = gu.run_exact(w, want=("g",))
+    assert res["status"] == 0
+    _check_g(w, res)
